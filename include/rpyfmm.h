@@ -1,0 +1,279 @@
+/*
+ * rpyfmm.h -- C ABI of the GB300 RPY matvec library (librpyfmm.so).
+ *
+ * Operation (Sec. 1 of "RPYFMM: Parallel adaptive fast multipole method for
+ * Rotne-Prager-Yamakawa tensor in biomolecular hydrodynamics simulations"):
+ *
+ *     u_i = sum_j D_ij F_j,        i = 1..N,
+ *
+ * with the RPY tensor D: the self term kT/(6 pi eta a) I, the far branch
+ * (Eq. "rpy-far", r >= 2a) and the overlap branch (r < 2a; the standard form
+ * kT/(6 pi eta a)[(1 - 9r/(32a)) I + (3/(32a)) r(x)r / r], which the paper
+ * prints garbled).  Pairs in adjacent leaves are summed directly; all other
+ * pairs go through the four Laplace potentials of Sec. 2 (Eq. 2.8, with the
+ * dipole term read as -C2 grad L_C), evaluated by an adaptive FMM whose
+ * multipole-to-local step uses plane-wave (exponential) expansions along six
+ * directions (Sec. 1, Sec. 3.2 Fig. "op": M-to-I, I-to-I, I-to-L).
+ *
+ * Conventions for every entry point:
+ *  - Arrays marked "device" are CUDA device pointers owned by the caller;
+ *    arrays marked "host" are ordinary host memory owned by the caller.
+ *    Positions, forces and velocities are N x 3 row-major FP64 (x, y, z per
+ *    bead) in the caller's bead order.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; entry points that must read sizes
+ *    back (tree builds) synchronise that stream before returning.
+ *  - A tree handle owns all device workspace it needs; rpy_matvec allocates
+ *    nothing.  Handles are not thread-safe: one host thread per handle at a
+ *    time; different handles may be used concurrently on different streams.
+ *  - kT_over_eta is kT/eta; D is linear in it, D_ii = kT_over_eta/(6 pi a) I.
+ *  - Every function returns an rpy_status (0 = success).  Invalid arguments
+ *    are rejected before any device work.  Errors found on the device
+ *    during an asynchronous call are reported by the next call that
+ *    synchronises (rpy_tree_sync, rpy_tree_stats, a build).
+ *  - There is no CPU fallback: without a CUDA device every compute entry
+ *    point returns RPY_ERR_NODEVICE.
+ */
+#ifndef RPYFMM_H
+#define RPYFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rpy_tree_s *rpy_tree;
+
+typedef enum {
+    RPY_OK = 0,
+    RPY_ERR_INVALID = -1,    /* bad argument (n < 1, a <= 0, NULL pointer, ...) */
+    RPY_ERR_DIGITS = -2,     /* digits not in {3, 6} */
+    RPY_ERR_OOM = -3,        /* device allocation failed */
+    RPY_ERR_CUDA = -4,       /* a CUDA call failed; see rpy_last_cuda_error() */
+    RPY_ERR_TIMEOUT = -5,    /* a bounded device wait gave up */
+    RPY_ERR_NONFINITE = -6,  /* a position is NaN or infinite */
+    RPY_ERR_STATE = -7,      /* handle in the wrong state (freed, mismatched sizes) */
+    RPY_ERR_NODEVICE = -8,   /* no CUDA device visible */
+    RPY_ERR_INTERNAL = -9    /* internal capacity exceeded (reported, never silent) */
+} rpy_status;
+
+typedef enum {
+    RPY_FP64 = 0,            /* every stage in FP64 */
+    RPY_FP32 = 1             /* precision form: near field and translations in FP32 with
+                                compensated accumulation; bounding cube, Morton keys,
+                                r ~ 0 overlap pairs and the final per-bead sum in FP64 */
+} rpy_precision;
+
+/* Build parameters.  Zero fields take the defaults listed. */
+typedef struct {
+    int digits;       /* 3 or 6: relative-L2 accuracy setting (required) */
+    int precision;    /* rpy_precision; default RPY_FP64 */
+    int leaf_cap;     /* refinement limit: a box splits while it holds more beads
+                         (Sec. 4.2 "threshold"); 0 = default for the setting */
+    int order_p;      /* expansion order p; 0 = default for the setting */
+    int max_level;    /* deepest level allowed, 1..21; 0 = 21 */
+    int flags;        /* reserved, must be 0 */
+} rpy_build_params;
+
+/* Statistics of a built tree (host struct filled by rpy_tree_stats). */
+typedef struct {
+    int64_t n_beads;
+    int32_t n_systems;
+    int32_t n_boxes;
+    int32_t n_leaves;
+    int32_t depth;              /* deepest level present */
+    int32_t order_p;
+    int32_t exp_nodes;          /* lambda nodes s */
+    int32_t exp_terms;          /* sum_k M_k (plane waves per direction) */
+    int32_t leaf_cap;
+    int32_t digits;
+    int32_t precision;
+    int32_t max_leaf_count;     /* largest leaf (may exceed leaf_cap where the 2a rule stops refinement) */
+    int32_t leaves_over_cap;
+    int64_t u_pairs;            /* bead pairs summed directly (near field, incl. self) */
+    int64_t n_ulist, n_wlist, n_xlist, n_vpairs;
+    int64_t device_bytes;       /* device memory held by the handle */
+    double build_ms;            /* host-measured wall time of the last build */
+} rpy_stats;
+
+/*
+ * Build an adaptive octree over N beads and all interaction lists.
+ *   pos_dev   device, n x 3 FP64, caller order
+ *   n         number of beads, >= 1
+ *   a         bead radius, > 0 and finite
+ *   digits    3 or 6
+ *   leaf_cap  refinement limit, 0 = default (40 for 3 digits, 100 for 6)
+ *   precision rpy_precision
+ *   out       receives the handle (NULL on failure)
+ * Boxes split while they hold more than leaf_cap beads and their children
+ * would have side >= 2a, so every pair closer than 2a is summed directly.
+ * Synchronises `stream`.  Non-finite positions give RPY_ERR_NONFINITE.
+ */
+int rpy_tree_build(const double *pos_dev, int64_t n, double a, int digits, int leaf_cap,
+                   int precision, void *stream, rpy_tree *out);
+
+/*
+ * Build one tree over many independent systems (the batching form): system
+ * k owns beads [sys_offsets[k], sys_offsets[k+1]) of pos_dev and has radius
+ * a_host[k].  Systems do not interact.  Every later matvec treats all of
+ * them in the same launches.
+ *   pos_dev      device, sys_offsets[nsys] x 3 FP64
+ *   sys_offsets  host, nsys + 1 non-decreasing int64, sys_offsets[0] = 0,
+ *                every system non-empty
+ *   a_host       host, nsys radii
+ *   params       host, build parameters (digits required)
+ */
+int rpy_forest_build(const double *pos_dev, const int64_t *sys_offsets, int nsys, const double *a_host,
+                     const rpy_build_params *params, void *stream, rpy_tree *out);
+
+/*
+ * Rebuild the tree of `t` for new positions of the same beads (same N, same
+ * systems, same radii and parameters), reusing its device buffers where they
+ * fit.  Used between Brownian-dynamics steps.  Synchronises `stream`.
+ */
+int rpy_tree_update_positions(rpy_tree t, const double *pos_dev, void *stream);
+
+/*
+ * u = D F for every bead of the tree (the hot path).
+ *   f_dev        device, N x 3 FP64 forces, caller order
+ *   kT_over_eta  kT/eta, finite
+ *   u_dev        device, N x 3 FP64 velocities, caller order (overwritten)
+ * Asynchronous on `stream`; allocates nothing.  For a forest every system
+ * uses the same kT_over_eta; see rpy_forest_matvec.
+ */
+int rpy_matvec(rpy_tree t, const double *f_dev, double kT_over_eta, double *u_dev, void *stream);
+
+/* Forest matvec with a per-system kT/eta (host array of nsys values). */
+int rpy_forest_matvec(rpy_tree t, const double *f_dev, const double *kT_over_eta_host, double *u_dev,
+                      void *stream);
+
+/*
+ * Diagnostic split of rpy_matvec: parts = RPY_PART_NEAR (direct pairs of
+ * adjacent leaves, self term included), RPY_PART_FAR (everything else, via
+ * the FMM), or both.  u_dev receives the sum of the selected parts.
+ */
+enum { RPY_PART_NEAR = 1, RPY_PART_FAR = 2, RPY_PART_ALL = 3 };
+int rpy_matvec_parts(rpy_tree t, const double *f_dev, double kT_over_eta, double *u_dev, int parts,
+                     void *stream);
+
+/*
+ * One-shot form with the paper's argument list (positions, radius, forces,
+ * kT/eta, accuracy digits): builds a tree, applies it once, frees it.
+ * All arrays are device arrays.  Synchronises `stream`.
+ */
+int rpy_matvec_oneshot(const double *pos_dev, int64_t n, double a, const double *f_dev,
+                       double kT_over_eta, int digits, double *u_dev, void *stream);
+
+/*
+ * The same with HOST arrays: copies pos and f to the device, runs the
+ * one-shot matvec and copies u back, all on `stream` (synchronised before
+ * return).  Device scratch is allocated and freed inside.
+ */
+int rpy_matvec_host(const double *pos_host, int64_t n, double a, const double *f_host,
+                    double kT_over_eta, int digits, int precision, double *u_host, void *stream);
+
+/*
+ * Laplace far field of the tree (Sec. 2): for four charge sets q (device,
+ * N x 4 FP64, caller order) returns, at every bead, the FMM part of the
+ * potential, its gradient and its Hessian (device, N x 4 x 13 FP64:
+ * [phi, dx, dy, dz, Hxx, Hxy, Hxz, Hyx, Hyy, Hyz, Hzx, Hzy, Hzz]), i.e. the
+ * sum over all sources outside the bead's U list.  Used to test the
+ * expansions operator by operator against direct sums.
+ */
+int rpy_laplace_far(rpy_tree t, const double *q_dev, double *out_dev, void *stream);
+
+/*
+ * Copy one array of the tree to host memory for inspection and tests.
+ *   field      one of RPY_FIELD_*
+ *   host_dst   host buffer, may be NULL to query the size
+ *   capacity   bytes available at host_dst
+ *   bytes_out  receives the size of the field in bytes
+ * Synchronises `t`'s last stream.
+ */
+enum {
+    RPY_FIELD_PERM = 1,        /* int32[N]: sorted position -> caller index */
+    RPY_FIELD_KEYS = 2,        /* uint64[N]: Morton keys in sorted order */
+    RPY_FIELD_BOX_LEVEL = 3,   /* int32[nbox] */
+    RPY_FIELD_BOX_RANGE = 4,   /* int32[nbox][2]: sorted bead range [begin, end) */
+    RPY_FIELD_BOX_PARENT = 5,  /* int32[nbox], -1 for roots */
+    RPY_FIELD_BOX_CENTER = 6,  /* double[nbox][3] */
+    RPY_FIELD_BOX_LEAF = 7,    /* int32[nbox]: 1 if the box is a leaf */
+    RPY_FIELD_BOX_SYS = 8,     /* int32[nbox]: system of the box */
+    RPY_FIELD_BOX_SIDE = 9,    /* double[nbox] */
+    RPY_FIELD_LEAVES = 10,     /* int32[nleaf]: leaf box ids */
+    RPY_FIELD_U_OFF = 11,      /* int32[nleaf + 1]: CSR offsets of U lists (per leaf) */
+    RPY_FIELD_U_IDX = 12,      /* int32[]: source leaf boxes */
+    RPY_FIELD_W_OFF = 13,      /* int32[nleaf + 1]: W lists (per leaf) */
+    RPY_FIELD_W_IDX = 14,
+    RPY_FIELD_X_OFF = 15,      /* int32[nbox + 1]: X lists (per box) */
+    RPY_FIELD_X_IDX = 16,
+    RPY_FIELD_V_OFF = 17,      /* int32[nbox + 1]: V lists (per box), built on request */
+    RPY_FIELD_V_IDX = 18,
+    RPY_FIELD_CUBE = 19        /* double[nsys][4]: cube centre x, y, z, side */
+};
+int rpy_tree_export(rpy_tree t, int field, void *host_dst, int64_t capacity, int64_t *bytes_out);
+
+/* Fill *out with the statistics of t.  Synchronises t's last stream. */
+int rpy_tree_stats(rpy_tree t, rpy_stats *out);
+
+/* Wait for t's last stream and report any error recorded on the device. */
+int rpy_tree_sync(rpy_tree t);
+
+/*
+ * Estimate the device bytes a tree over n beads would hold (upper bound
+ * used for admission control by the serving loop).  Host only.
+ */
+int rpy_tree_footprint(int64_t n, int digits, int precision, int leaf_cap, int64_t *bytes);
+
+/* Release the handle and all its device memory.  NULL is ignored. */
+void rpy_tree_free(rpy_tree t);
+
+/* Static description of a status code. */
+const char *rpy_strerror(int status);
+
+/* Text of the last CUDA error seen by this thread (empty if none). */
+const char *rpy_last_cuda_error(void);
+
+/*
+ * Host-only inspection of the operator tables for expansion order p and a
+ * digit setting (no device needed): which = 1 M2M, 2 L2L (transposed real
+ * matrices per child octant), 3 / 4 frame rotations world->frame / frame->world,
+ * 5 M2X coefficients, 6 X2L coefficients, 7 stored plane waves (k, cos, sin,
+ * w/M), 8 shift factors, 9 merge-and-shift groups, 10 rotation block offsets,
+ * 11 quadrature (s, then lambda, w, M per node).  dst (host, may be NULL to
+ * query) receives *count doubles.
+ */
+int rpy_debug_table(int p, int digits, int which, double *dst, int64_t capacity, int64_t *count);
+
+/*
+ * Per-stage timing of later matvecs of t: when enabled, CUDA events are
+ * recorded on the call's stream between the stages of rpy_matvec.
+ * rpy_tree_stage_times writes the stage durations (ms) of the last matvec,
+ * in the order of RPY_STAGE_*, after synchronising; n = slots in ms_host.
+ */
+enum {
+    RPY_STAGE_GATHER = 0, RPY_STAGE_P2P, RPY_STAGE_P2M, RPY_STAGE_M2M, RPY_STAGE_M2X, RPY_STAGE_X2X,
+    RPY_STAGE_X2L, RPY_STAGE_P2L, RPY_STAGE_L2L, RPY_STAGE_EVAL, RPY_STAGE_COMBINE, RPY_NUM_STAGES
+};
+int rpy_tree_set_profiling(rpy_tree t, int enable);
+int rpy_tree_stage_times(rpy_tree t, double *ms_host, int n);
+
+/*
+ * Measured FMA throughput of the current device (FLOP/s, 2 per FMA) for
+ * RPY_FP64 or RPY_FP32: a short kernel of independent FMA chains on every
+ * SM, best of three timed runs.  Used as the ALU roofline denominator.
+ */
+int rpy_alu_peak(int precision, double *flops_per_s, void *stream);
+
+/* Number of kernels this library has launched in this process (all devices). */
+int64_t rpy_launch_count(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int rpy_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPYFMM_H */

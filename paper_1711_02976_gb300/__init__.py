@@ -1,0 +1,344 @@
+"""GB300 RPY matvec (u = D F with the Rotne-Prager-Yamakawa tensor) by an
+adaptive plane-wave FMM over the four Laplace potentials of the RPYFMM
+decomposition.
+
+This module is a thin ctypes binding of the C ABI in include/rpyfmm.h: every
+function has the C name, marshals torch tensors / numpy arrays into pointers
+and sizes, and raises RpyError on a non-zero status.  All computation happens
+in librpyfmm.so (CUDA, sm_103a); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "RpyError", "RpyStats", "BuildParams", "load", "rpy_tree_build", "rpy_forest_build",
+    "rpy_tree_update_positions", "rpy_matvec", "rpy_forest_matvec", "rpy_matvec_parts",
+    "rpy_matvec_oneshot", "rpy_matvec_host", "rpy_laplace_far", "rpy_tree_export", "rpy_tree_stats",
+    "rpy_tree_sync", "rpy_tree_footprint", "rpy_tree_free", "rpy_strerror", "rpy_last_cuda_error",
+    "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times", "rpy_launch_count",
+    "rpy_alu_peak", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
+    "RPY_PART_ALL", "EXPORTED_SYMBOLS",
+]
+
+RPY_FP64, RPY_FP32 = 0, 1
+RPY_PART_NEAR, RPY_PART_FAR, RPY_PART_ALL = 1, 2, 3
+FIELDS = {
+    "perm": (1, np.int32), "keys": (2, np.uint64), "box_level": (3, np.int32), "box_range": (4, np.int32),
+    "box_parent": (5, np.int32), "box_center": (6, np.float64), "box_leaf": (7, np.int32),
+    "box_sys": (8, np.int32), "box_side": (9, np.float64), "leaves": (10, np.int32), "u_off": (11, np.int32),
+    "u_idx": (12, np.int32), "w_off": (13, np.int32), "w_idx": (14, np.int32), "x_off": (15, np.int32),
+    "x_idx": (16, np.int32), "v_off": (17, np.int32), "v_idx": (18, np.int32), "cube": (19, np.float64),
+}
+EXPORTED_SYMBOLS = [
+    "rpy_tree_build", "rpy_forest_build", "rpy_tree_update_positions", "rpy_matvec", "rpy_forest_matvec",
+    "rpy_matvec_parts", "rpy_matvec_oneshot", "rpy_matvec_host", "rpy_laplace_far", "rpy_tree_export",
+    "rpy_tree_stats", "rpy_tree_sync", "rpy_tree_footprint", "rpy_tree_free", "rpy_strerror",
+    "rpy_last_cuda_error", "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times",
+    "rpy_launch_count", "rpy_alu_peak",
+]
+STAGES = ["gather", "p2p", "p2m", "m2m", "m2x", "x2x", "x2l", "p2l", "l2l", "eval", "combine"]
+
+
+class RpyError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        lib = load()
+        msg = lib.rpy_strerror(status).decode()
+        cu = lib.rpy_last_cuda_error().decode()
+        super().__init__(f"{what}: {msg} (status {status}){' [' + cu + ']' if cu else ''}")
+        self.status = status
+
+
+class BuildParams(ctypes.Structure):
+    _fields_ = [("digits", ctypes.c_int), ("precision", ctypes.c_int), ("leaf_cap", ctypes.c_int),
+                ("order_p", ctypes.c_int), ("max_level", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class RpyStats(ctypes.Structure):
+    _fields_ = [("n_beads", ctypes.c_int64), ("n_systems", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
+                ("n_leaves", ctypes.c_int32), ("depth", ctypes.c_int32), ("order_p", ctypes.c_int32),
+                ("exp_nodes", ctypes.c_int32), ("exp_terms", ctypes.c_int32), ("leaf_cap", ctypes.c_int32),
+                ("digits", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_leaf_count", ctypes.c_int32),
+                ("leaves_over_cap", ctypes.c_int32), ("u_pairs", ctypes.c_int64), ("n_ulist", ctypes.c_int64),
+                ("n_wlist", ctypes.c_int64), ("n_xlist", ctypes.c_int64), ("n_vpairs", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(build_if_missing: bool = True):
+    """Load librpyfmm.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"librpyfmm.so not found at {path}; run paper_1711_02976_gb300._build.build()")
+        lib = ctypes.CDLL(path)
+        vp, i64, d, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        sig = {
+            "rpy_tree_build": [vp, i64, d, i, i, i, vp, ctypes.POINTER(vp)],
+            "rpy_forest_build": [vp, vp, i, vp, ctypes.POINTER(BuildParams), vp, ctypes.POINTER(vp)],
+            "rpy_tree_update_positions": [vp, vp, vp],
+            "rpy_matvec": [vp, vp, d, vp, vp],
+            "rpy_forest_matvec": [vp, vp, vp, vp, vp],
+            "rpy_matvec_parts": [vp, vp, d, vp, i, vp],
+            "rpy_matvec_oneshot": [vp, i64, d, vp, d, i, vp, vp],
+            "rpy_matvec_host": [vp, i64, d, vp, d, i, i, vp, vp],
+            "rpy_laplace_far": [vp, vp, vp, vp],
+            "rpy_tree_export": [vp, i, vp, i64, ctypes.POINTER(i64)],
+            "rpy_tree_stats": [vp, ctypes.POINTER(RpyStats)],
+            "rpy_tree_sync": [vp],
+            "rpy_tree_footprint": [i64, i, i, i, ctypes.POINTER(i64)],
+            "rpy_tree_free": [vp],
+            "rpy_strerror": [i],
+            "rpy_last_cuda_error": [],
+            "rpy_version": [],
+            "rpy_debug_table": [i, i, i, vp, i64, ctypes.POINTER(i64)],
+            "rpy_tree_set_profiling": [vp, i],
+            "rpy_tree_stage_times": [vp, vp, i],
+            "rpy_launch_count": [],
+            "rpy_alu_peak": [i, ctypes.POINTER(d), vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.rpy_tree_free.restype = None
+        lib.rpy_launch_count.restype = ctypes.c_int64
+        lib.rpy_strerror.restype = ctypes.c_char_p
+        lib.rpy_last_cuda_error.restype = ctypes.c_char_p
+        _lib = lib
+        return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise RpyError(status, what)
+
+
+def _ptr(x) -> int:
+    """Device or host address of a torch tensor / numpy array (must be contiguous float64 etc.)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    return int(x)
+
+
+def _dev_f64(x, name):
+    if hasattr(x, "is_cuda"):
+        if not x.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        import torch
+        if x.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64")
+    return _ptr(x)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Tree:
+    """Owning wrapper of an rpy_tree handle (freed on close / garbage collection)."""
+
+    def __init__(self, handle: int, n: int, nsys: int):
+        self.handle = handle
+        self.n = n
+        self.nsys = nsys
+
+    def close(self):
+        if self.handle:
+            load().rpy_tree_free(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _h(tree):
+    return ctypes.c_void_p(tree.handle if isinstance(tree, Tree) else tree)
+
+
+def rpy_tree_build(pos, n, a, digits, leaf_cap=0, precision=RPY_FP64, stream=None) -> Tree:
+    lib = load()
+    out = ctypes.c_void_p()
+    _check(lib.rpy_tree_build(_dev_f64(pos, "pos"), int(n), float(a), int(digits), int(leaf_cap), int(precision),
+                              _stream(stream), ctypes.byref(out)), "rpy_tree_build")
+    return Tree(out.value, int(n), 1)
+
+
+def rpy_forest_build(pos, sys_offsets, a, digits, leaf_cap=0, precision=RPY_FP64, order_p=0, max_level=0,
+                     stream=None) -> Tree:
+    lib = load()
+    off = np.ascontiguousarray(sys_offsets, dtype=np.int64)
+    av = np.ascontiguousarray(a, dtype=np.float64)
+    prm = BuildParams(int(digits), int(precision), int(leaf_cap), int(order_p), int(max_level), 0)
+    out = ctypes.c_void_p()
+    _check(lib.rpy_forest_build(_dev_f64(pos, "pos"), off.ctypes.data, int(av.size), av.ctypes.data,
+                                ctypes.byref(prm), _stream(stream), ctypes.byref(out)), "rpy_forest_build")
+    return Tree(out.value, int(off[-1]), int(av.size))
+
+
+def rpy_tree_update_positions(tree, pos, stream=None):
+    _check(load().rpy_tree_update_positions(_h(tree), _dev_f64(pos, "pos"), _stream(stream)),
+           "rpy_tree_update_positions")
+
+
+def rpy_matvec(tree, f, kT_over_eta, u, stream=None):
+    _check(load().rpy_matvec(_h(tree), _dev_f64(f, "f"), float(kT_over_eta), _dev_f64(u, "u"), _stream(stream)),
+           "rpy_matvec")
+
+
+def rpy_forest_matvec(tree, f, kT_over_eta, u, stream=None):
+    s = np.ascontiguousarray(kT_over_eta, dtype=np.float64)
+    _check(load().rpy_forest_matvec(_h(tree), _dev_f64(f, "f"), s.ctypes.data, _dev_f64(u, "u"), _stream(stream)),
+           "rpy_forest_matvec")
+
+
+def rpy_matvec_parts(tree, f, kT_over_eta, u, parts, stream=None):
+    _check(load().rpy_matvec_parts(_h(tree), _dev_f64(f, "f"), float(kT_over_eta), _dev_f64(u, "u"), int(parts),
+                                   _stream(stream)), "rpy_matvec_parts")
+
+
+def rpy_matvec_oneshot(pos, n, a, f, kT_over_eta, digits, u, stream=None):
+    _check(load().rpy_matvec_oneshot(_dev_f64(pos, "pos"), int(n), float(a), _dev_f64(f, "f"), float(kT_over_eta),
+                                     int(digits), _dev_f64(u, "u"), _stream(stream)), "rpy_matvec_oneshot")
+
+
+def rpy_matvec_host(pos, a, f, kT_over_eta, digits, u, precision=RPY_FP64, stream=None):
+    """Host arrays in and out (numpy float64, N x 3, C-contiguous; u is written in place)."""
+    for name, arr in (("pos", pos), ("f", f), ("u", u)):
+        if not isinstance(arr, np.ndarray) or arr.dtype != np.float64 or not arr.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name} must be a C-contiguous float64 numpy array")
+    n = pos.shape[0]
+    _check(load().rpy_matvec_host(_ptr(pos), int(n), float(a), _ptr(f), float(kT_over_eta), int(digits),
+                                  int(precision), _ptr(u), _stream(stream)), "rpy_matvec_host")
+
+
+def rpy_laplace_far(tree, q, out, stream=None):
+    _check(load().rpy_laplace_far(_h(tree), _dev_f64(q, "q"), _dev_f64(out, "out"), _stream(stream)),
+           "rpy_laplace_far")
+
+
+def rpy_tree_export(tree, field: str) -> np.ndarray:
+    lib = load()
+    code, dt = FIELDS[field]
+    nbytes = ctypes.c_int64()
+    _check(lib.rpy_tree_export(_h(tree), code, None, 0, ctypes.byref(nbytes)), "rpy_tree_export")
+    out = np.zeros(nbytes.value // np.dtype(dt).itemsize, dtype=dt)
+    _check(lib.rpy_tree_export(_h(tree), code, out.ctypes.data, nbytes.value, ctypes.byref(nbytes)),
+           "rpy_tree_export")
+    if field in ("box_range",):
+        out = out.reshape(-1, 2)
+    elif field == "box_center":
+        out = out.reshape(-1, 3)
+    elif field == "cube":
+        out = out.reshape(-1, 4)
+    return out
+
+
+def rpy_tree_stats(tree) -> dict:
+    st = RpyStats()
+    _check(load().rpy_tree_stats(_h(tree), ctypes.byref(st)), "rpy_tree_stats")
+    return st.as_dict()
+
+
+def rpy_tree_sync(tree):
+    _check(load().rpy_tree_sync(_h(tree)), "rpy_tree_sync")
+
+
+def rpy_tree_footprint(n, digits, precision=RPY_FP64, leaf_cap=0) -> int:
+    b = ctypes.c_int64()
+    _check(load().rpy_tree_footprint(int(n), int(digits), int(precision), int(leaf_cap), ctypes.byref(b)),
+           "rpy_tree_footprint")
+    return b.value
+
+
+def rpy_tree_free(tree):
+    if isinstance(tree, Tree):
+        tree.close()
+    else:
+        load().rpy_tree_free(ctypes.c_void_p(tree))
+
+
+def rpy_strerror(status: int) -> str:
+    return load().rpy_strerror(int(status)).decode()
+
+
+def rpy_last_cuda_error() -> str:
+    return load().rpy_last_cuda_error().decode()
+
+
+def rpy_version() -> int:
+    return load().rpy_version()
+
+
+def rpy_debug_table(p: int, digits: int, which: int) -> np.ndarray:
+    lib = load()
+    cnt = ctypes.c_int64()
+    _check(lib.rpy_debug_table(int(p), int(digits), int(which), None, 0, ctypes.byref(cnt)), "rpy_debug_table")
+    out = np.zeros(cnt.value)
+    _check(lib.rpy_debug_table(int(p), int(digits), int(which), out.ctypes.data, cnt.value, ctypes.byref(cnt)),
+           "rpy_debug_table")
+    return out
+
+
+def rpy_tree_set_profiling(tree, enable=True):
+    _check(load().rpy_tree_set_profiling(_h(tree), int(bool(enable))), "rpy_tree_set_profiling")
+
+
+def rpy_tree_stage_times(tree) -> dict:
+    ms = np.zeros(len(STAGES))
+    _check(load().rpy_tree_stage_times(_h(tree), ms.ctypes.data, len(STAGES)), "rpy_tree_stage_times")
+    return dict(zip(STAGES, ms.tolist()))
+
+
+def rpy_launch_count() -> int:
+    return int(load().rpy_launch_count())
+
+
+def rpy_alu_peak(precision=RPY_FP64, stream=None) -> float:
+    v = ctypes.c_double()
+    _check(load().rpy_alu_peak(int(precision), ctypes.byref(v), _stream(stream)), "rpy_alu_peak")
+    return v.value

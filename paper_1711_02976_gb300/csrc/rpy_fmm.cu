@@ -1,0 +1,808 @@
+// Far field of the RPY matvec: the four Laplace potentials of Sec. 2 through
+// an adaptive FMM whose multipole-to-local step runs on plane-wave
+// (exponential) expansions (M-to-I, I-to-I, I-to-L of Fig. "op").
+//
+// Charge sets (Sec. 2): q_1..q_3 = F^1..F^3, q_4 = F . (r - c0) with c0 the
+// centre of the system's bounding cube (Eq. 2.8 holds for any common origin).
+//
+// Kernels, in launch order:
+//   k_p2m      S->M   leaves: M_n^m = sum_j q_j conj(y_n^m(eta_j))
+//   k_m2m      M->M   dense per-octant operator, level by level upward
+//   k_m2x      M->I   rotate into the frame of each axis, outgoing plane waves
+//                     W_kj = (w_k/M_k) sum_{n,m} M_n^m i^|m| lambda_k^n e^{i m a_kj} / sqrt((n-|m|)!(n+|m|)!)
+//   k_x2x      I->I   merge-and-shift: per parent and direction, sources are
+//                     shifted to the parent centre and summed per group of
+//                     targets they serve, then shifted once to each child
+//   k_x2l      I->L   L_n^m = i^|m| sum_k (-lambda_k)^n / sqrt(...) sum_j I_kj e^{-i m a_kj},
+//                     rotated back to the world frame
+//   k_p2l      S->L   X list
+//   k_l2l      L->L   level by level downward
+//   k_far_eval L->T, M->T   L2P for the leaf and M2P for its W list, with the
+//                     gradients and Hessians of Theorems 1-2 formed as
+//                     derivative expansions per box, combined by Eq. (2.8):
+//                     u = C1 [L1 L2 L3] - C1 sum_k x_k grad L_k + C1 grad L4 - C2 grad L_C.
+#include <cmath>
+#include <cstdio>
+
+#include "rpy_harmonics.h"
+
+namespace rpy {
+
+constexpr double kPi = 3.14159265358979323846;
+
+__device__ __forceinline__ int deg_of(int idx) {
+    int n = int((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
+    while (tri(n + 1, 0) <= idx) ++n;
+    while (tri(n, 0) > idx) --n;
+    return n;
+}
+
+// ---------------------------------------------------------------- harmonics per warp lane
+// Lane m (m <= P) fills column m of y (or z) for one point.
+template <typename T, bool IRREG>
+__device__ void warp_harmonics(T x, T y, T z, int P, const T *ra, const T *rb, const T *cm, cpx<T> *out) {
+    int m = threadIdx.x & 31;
+    if (m > P) return;
+    T r2 = x * x + y * y + z * z;
+    T ir2 = IRREG ? T(1) / r2 : T(0);
+    cpx<T> w = IRREG ? mk(x * ir2, y * ir2) : mk(x, y);
+    cpx<T> d = IRREG ? mk<T>(sqrt(ir2), 0) : mk<T>(1, 0);
+    for (int k = 0; k < m; ++k) d = w * d;
+    d = cm[m] * d;
+    out[tri(m, m)] = d;
+    cpx<T> p2 = mk<T>(0, 0), p1 = d;
+    for (int n = m + 1; n <= P; ++n) {
+        int i = tri(n, m);
+        cpx<T> c;
+        if (IRREG)
+            c = mk((ra[i] * z * p1.x - rb[i] * p2.x) * ir2, (ra[i] * z * p1.y - rb[i] * p2.y) * ir2);
+        else
+            c = mk(ra[i] * z * p1.x - rb[i] * r2 * p2.x, ra[i] * z * p1.y - rb[i] * r2 * p2.y);
+        out[i] = c;
+        p2 = p1;
+        p1 = c;
+    }
+}
+
+// Streaming per-thread evaluation of NE real fields f_q = sum_{n<=P,m} w_m Re(E_q[n,m] h_n^m(v)).
+template <typename T, int NE, bool IRREG>
+__device__ void eval_fields(T x, T y, T z, int P, const cpx<T> *E, int stride, const T *ra, const T *rb,
+                            const T *rc, T *acc) {
+    T r2 = x * x + y * y + z * z;
+    T ir2 = IRREG ? T(1) / r2 : T(0);
+    cpx<T> w = IRREG ? mk(x * ir2, y * ir2) : mk(x, y);
+    cpx<T> diag = IRREG ? mk<T>(sqrt(ir2), 0) : mk<T>(1, 0);
+    for (int m = 0; m <= P; ++m) {
+        if (m > 0) diag = rc[m] * (w * diag);
+        T wm = m ? T(2) : T(1);
+        cpx<T> p2 = mk<T>(0, 0), p1 = diag;
+        {
+            int i = tri(m, m);
+            cpx<T> hw = mk(wm * diag.x, wm * diag.y);
+#pragma unroll
+            for (int q = 0; q < NE; ++q) acc[q] += E[q * stride + i].x * hw.x - E[q * stride + i].y * hw.y;
+        }
+        for (int n = m + 1; n <= P; ++n) {
+            int i = tri(n, m);
+            cpx<T> c;
+            if (IRREG)
+                c = mk((ra[i] * z * p1.x - rb[i] * p2.x) * ir2, (ra[i] * z * p1.y - rb[i] * p2.y) * ir2);
+            else
+                c = mk(ra[i] * z * p1.x - rb[i] * r2 * p2.x, ra[i] * z * p1.y - rb[i] * r2 * p2.y);
+            cpx<T> hw = mk(wm * c.x, wm * c.y);
+#pragma unroll
+            for (int q = 0; q < NE; ++q) acc[q] += E[q * stride + i].x * hw.x - E[q * stride + i].y * hw.y;
+            p2 = p1;
+            p1 = c;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- derivative expansions
+// Real-field derivative expansions (ladder relations of Sec. 2, Theorems 1-2),
+// computed by the whole CTA.  src: degree ps coefficients.  dst: x, y, z
+// derivatives, each zero-padded to stride.
+template <typename T>
+__device__ void d_local(const cpx<T> *src, int ps, cpx<T> *dx, cpx<T> *dy, cpx<T> *dz, int stride, int P) {
+    // degree k <= ps-1 from L_{k+1}
+    for (int i = threadIdx.x; i < ncoef(P); i += blockDim.x) {
+        int k = deg_of(i), m = i - tri(k, 0);
+        cpx<T> X = mk<T>(0, 0), Y = X, Z = X;
+        if (k <= ps - 1) {
+            Z = T(sqrt(T((k + 1 + m) * (k + 1 - m)))) * src[tri(k + 1, m)];
+            cpx<T> Pv = m >= 1 ? T(sqrt(T((k - m + 1) * (k - m + 2)))) * src[tri(k + 1, m - 1)]
+                               : T(-sqrt(T((k + 1) * (k + 2)))) * conj(src[tri(k + 1, 1)]);
+            cpx<T> Qv = T(-sqrt(T((k + m + 1) * (k + m + 2)))) * src[tri(k + 1, m + 1)];
+            X = mk(T(0.5) * (Pv.x + Qv.x), T(0.5) * (Pv.y + Qv.y));
+            Y = mk(T(0.5) * (Pv.y - Qv.y), T(-0.5) * (Pv.x - Qv.x));
+        }
+        dx[i] = X;
+        dy[i] = Y;
+        dz[i] = Z;
+    }
+}
+
+template <typename T>
+__device__ void d_multipole(const cpx<T> *src, int ps, cpx<T> *dx, cpx<T> *dy, cpx<T> *dz, int stride, int P) {
+    // degree k <= ps+1 from M_{k-1}
+    for (int i = threadIdx.x; i < ncoef(P); i += blockDim.x) {
+        int k = deg_of(i), m = i - tri(k, 0);
+        cpx<T> X = mk<T>(0, 0), Y = X, Z = X;
+        if (k >= 1 && k <= ps + 1) {
+            if (m <= k - 1) Z = T(-sqrt(T((k + m) * (k - m)))) * src[tri(k - 1, m)];
+            cpx<T> Pv = mk<T>(0, 0), Qv = mk<T>(0, 0);
+            if (m >= 1) Pv = T(sqrt(T((k + m) * (k + m - 1)))) * src[tri(k - 1, m - 1)];
+            else if (k >= 2) Pv = T(-sqrt(T(k * (k - 1)))) * conj(src[tri(k - 1, 1)]);
+            if (m + 1 <= k - 1) Qv = T(-sqrt(T((k - m) * (k - m - 1)))) * src[tri(k - 1, m + 1)];
+            X = mk(T(0.5) * (Pv.x + Qv.x), T(0.5) * (Pv.y + Qv.y));
+            Y = mk(T(0.5) * (Pv.y - Qv.y), T(-0.5) * (Pv.x - Qv.x));
+        }
+        dx[i] = X;
+        dy[i] = Y;
+        dz[i] = Z;
+    }
+}
+
+// ---------------------------------------------------------------- table access
+template <typename T>
+struct Rec {
+    const T *a, *b, *c, *cm;
+};
+
+template <typename T>
+__device__ Rec<T> load_rec(const DevTables<T> &D, T *sm) {
+    int P = D.p + 2;
+    int nc = ncoef(P);
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        sm[i] = D.rec_a[i];
+        sm[nc + i] = D.rec_b[i];
+    }
+    for (int i = threadIdx.x; i <= P; i += blockDim.x) {
+        sm[2 * nc + i] = D.rec_c[i];
+        sm[2 * nc + P + 1 + i] = D.rec_cm[i];
+    }
+    Rec<T> r{sm, sm + nc, sm + 2 * nc, sm + 2 * nc + P + 1};
+    return r;
+}
+
+template <typename T>
+__host__ __device__ inline int rec_floats(int p) {
+    return 2 * ncoef(p + 2) + 2 * (p + 3);
+}
+
+
+// ---------------------------------------------------------------- P2M / P2L
+
+constexpr int kChunkB = 16;
+
+// MODE 0: P2M over the leaf's own beads (multipole about its centre)
+// MODE 1: P2L over the beads of every box in X(b) (local about b's centre)
+template <typename T, int MODE>
+__global__ void k_p2x(int b0, int nb, DevTables<T> D, const int *beg, const int *end, const double *ctr,
+                      const double *side, const int *lvl, const int *leaf, const int *bsys, const int *xoff,
+                      const int *xidx, const double *pos, const double *fs, const double *lapq, int64_t n,
+                      SysConst sc, cpx<T> *out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int b = b0 + blockIdx.x;
+    if (b >= b0 + nb) return;
+    if (lvl[b] < 2) return;
+    if (MODE == 0 && !leaf[b]) return;
+    int nsrc = MODE == 0 ? 1 : xoff[b + 1] - xoff[b];
+    if (nsrc == 0) return;
+    const int p = D.p, nc = ncoef(p);
+    T *smr = reinterpret_cast<T *>(smem_raw);
+    Rec<T> R = load_rec(D, smr);
+    cpx<T> *ybuf = reinterpret_cast<cpx<T> *>(smr + ((rec_floats<T>(p) + 1) & ~1));
+    cpx<T> *acc = ybuf + kChunkB * nc;
+    T *q = reinterpret_cast<T *>(acc + kSets * nc);
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) acc[i] = mk<T>(0, 0);
+    int sy = bsys[b];
+    double c0x = sc.cube[4 * sy], c0y = sc.cube[4 * sy + 1], c0z = sc.cube[4 * sy + 2];
+    double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
+    double ih = 1.0 / side[b];
+    int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    __syncthreads();
+    for (int si = 0; si < nsrc; ++si) {
+        int src = MODE == 0 ? b : xidx[xoff[b] + si];
+        int j0 = beg[src], j1 = end[src];
+        for (int jc = j0; jc < j1; jc += kChunkB) {
+            int cnt = min(kChunkB, j1 - jc);
+            for (int t = warp; t < cnt; t += nwarp) {
+                int j = jc + t;
+                T ex = T((pos[j] - cx) * ih), ey = T((pos[n + j] - cy) * ih), ez = T((pos[2 * n + j] - cz) * ih);
+                warp_harmonics<T, MODE == 1>(ex, ey, ez, p, R.a, R.b, R.cm, ybuf + t * nc);
+            }
+            for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+                int j = jc + t;
+                if (lapq) {
+                    for (int k = 0; k < kSets; ++k) q[4 * t + k] = T(lapq[4 * j + k]);
+                } else {
+                    double fx = fs[j], fy = fs[n + j], fz = fs[2 * n + j];
+                    q[4 * t] = T(fx);
+                    q[4 * t + 1] = T(fy);
+                    q[4 * t + 2] = T(fz);
+                    q[4 * t + 3] = T(fx * (pos[j] - c0x) + fy * (pos[n + j] - c0y) + fz * (pos[2 * n + j] - c0z));
+                }
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
+                int k = e / nc, i = e - k * nc;
+                cpx<T> a = acc[e];
+                for (int t = 0; t < cnt; ++t) {
+                    cpx<T> yv = ybuf[t * nc + i];
+                    T qq = q[4 * t + k];
+                    a.x += qq * yv.x;
+                    a.y -= qq * yv.y;   // conj
+                }
+                acc[e] = a;
+            }
+            __syncthreads();
+        }
+    }
+    cpx<T> *o = out + size_t(b) * kSets * nc;
+    for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
+        if (MODE == 0) o[e] = acc[e];
+        else o[e] += acc[e];
+    }
+}
+
+// ---------------------------------------------------------------- M2M / L2L
+
+// M2M: parent M = sum over children of T_o [child M]; output degree n uses inputs of degree <= n.
+template <typename T>
+__global__ void k_m2m(int b0, int nb, DevTables<T> D, const int *leaf, const int *child, cpx<T> *M) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int b = b0 + blockIdx.x;
+    if (leaf[b]) return;
+    const int nc = ncoef(D.p), Dd = 2 * nc;
+    T *X = reinterpret_cast<T *>(smem_raw);
+    int r = threadIdx.x;
+    int kmax = r < Dd ? 2 * ncoef(deg_of(r >> 1)) : 0;
+    T acc[kSets] = {0, 0, 0, 0};
+    for (int o = 0; o < 8; ++o) {
+        int c = child[8 * b + o];
+        if (c < 0) continue;
+        const T *src = reinterpret_cast<const T *>(M + size_t(c) * kSets * nc);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kSets * Dd; i += blockDim.x) X[i] = src[i];
+        __syncthreads();
+        if (r < Dd) {
+            const T *Tt = D.m2m_t + size_t(o) * Dd * Dd;
+            for (int k = 0; k < kmax; ++k) {
+                T t = Tt[size_t(k) * Dd + r];
+#pragma unroll
+                for (int s = 0; s < kSets; ++s) acc[s] += t * X[s * Dd + k];
+            }
+        }
+    }
+    if (r < Dd) {
+        T *dst = reinterpret_cast<T *>(M + size_t(b) * kSets * nc);
+        for (int s = 0; s < kSets; ++s) dst[s * Dd + r] = acc[s];
+    }
+}
+
+// L2L: child L += S_o [parent L]; output degree k uses inputs of degree >= k.
+template <typename T>
+__global__ void k_l2l(int b0, int nb, DevTables<T> D, const int *par, const int *cell, cpx<T> *L) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int b = b0 + blockIdx.x;
+    int P = par[b];
+    const int nc = ncoef(D.p), Dd = 2 * nc;
+    T *X = reinterpret_cast<T *>(smem_raw);
+    const T *src = reinterpret_cast<const T *>(L + size_t(P) * kSets * nc);
+    for (int i = threadIdx.x; i < kSets * Dd; i += blockDim.x) X[i] = src[i];
+    __syncthreads();
+    int r = threadIdx.x;
+    if (r >= Dd) return;
+    int o = (cell[3 * b] & 1) | ((cell[3 * b + 1] & 1) << 1) | ((cell[3 * b + 2] & 1) << 2);
+    int kdeg = deg_of(r >> 1);
+    int k0 = 2 * tri(kdeg, 0);
+    const T *St = D.l2l_t + size_t(o) * Dd * Dd;
+    T acc[kSets] = {0, 0, 0, 0};
+    for (int k = k0; k < Dd; ++k) {
+        T t = St[size_t(k) * Dd + r];
+#pragma unroll
+        for (int s = 0; s < kSets; ++s) acc[s] += t * X[s * Dd + k];
+    }
+    T *dst = reinterpret_cast<T *>(L + size_t(b) * kSets * nc);
+    for (int s = 0; s < kSets; ++s) dst[s * Dd + r] += acc[s];
+}
+
+// ---------------------------------------------------------------- rotations
+// dst[s] = R src[s] per degree block (real 2-layout, block size 2(n+1)).
+template <typename T>
+__device__ void rotate_sets(const T *rot, const int *roff, int p, const cpx<T> *src, cpx<T> *dst) {
+    const int nc = ncoef(p);
+    int tot = kSets * 2 * nc;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        int s = e / (2 * nc), r = e - s * 2 * nc;
+        int n = deg_of(r >> 1);
+        int B = 2 * (n + 1);
+        int lo = r - 2 * tri(n, 0);
+        const T *row = rot + roff[n] + lo * B;
+        const T *in = reinterpret_cast<const T *>(src + s * nc) + 2 * tri(n, 0);
+        T a = 0;
+        for (int c = 0; c < B; ++c) a += row[c] * in[c];
+        reinterpret_cast<T *>(dst + s * nc)[r] = a;
+    }
+}
+
+// ---------------------------------------------------------------- M2X
+template <typename T>
+__global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *Xo) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int b = b0 + blockIdx.x;
+    const int p = D.p, nc = ncoef(p), s = D.s, S = D.S, P1 = p + 1;
+    cpx<T> *Mw = reinterpret_cast<cpx<T> *>(smem_raw);
+    cpx<T> *Mf = Mw + kSets * nc;
+    cpx<T> *AE = Mf + kSets * nc;
+    cpx<T> *AO = AE + kSets * s * P1;
+    const cpx<T> *src = M + size_t(b) * kSets * nc;
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Mw[i] = src[i];
+    __syncthreads();
+    for (int f = 0; f < 3; ++f) {
+        const cpx<T> *Mu = Mw;
+        if (f > 0) {
+            rotate_sets(D.rot_fwd + size_t(f - 1) * D.rot_len, D.rot_off, p, Mw, Mf);
+            __syncthreads();
+            Mu = Mf;
+        }
+        // A_k^m split by parity of n + m
+        for (int e = threadIdx.x; e < kSets * s * P1; e += blockDim.x) {
+            int st = e / (s * P1), rem = e - st * s * P1, k = rem / P1, m = rem - k * P1;
+            cpx<T> ev = mk<T>(0, 0), od = mk<T>(0, 0);
+            const T *cc = D.m2x_c + size_t(k) * nc;
+            for (int n = m; n <= p; ++n) {
+                int i = tri(n, m);
+                cpx<T> v = cc[i] * Mu[st * nc + i];
+                if ((n + m) & 1) od += v; else ev += v;
+            }
+            AE[e] = ev;
+            AO[e] = od;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kSets * S; e += blockDim.x) {
+            int st = e / S, j = e - st * S;
+            int k = D.e_k[j];
+            cpx<T> ph = mk(D.e_cos[j], D.e_sin[j]);
+            const cpx<T> *ae = AE + (st * s + k) * P1;
+            const cpx<T> *ao = AO + (st * s + k) * P1;
+            T rp = ae[0].x + ao[0].x, rm = ae[0].x - ao[0].x, ip = 0, im = 0;
+            cpx<T> z = mk<T>(1, 0);
+            for (int m = 1; m <= p; ++m) {
+                z = z * ph;
+                T se = ae[m].x * z.x - ae[m].y * z.y;   // Re(AE e^{i m a})
+                T so = ao[m].x * z.x - ao[m].y * z.y;
+                T vp = 2 * (se + so), vm = 2 * (se - so);
+                switch (m & 3) {
+                    case 0: rp += vp; rm += vm; break;
+                    case 1: ip += vp; im += vm; break;
+                    case 2: rp -= vp; rm -= vm; break;
+                    default: ip -= vp; im -= vm; break;
+                }
+            }
+            T wm = D.e_wm[j];
+            size_t base = size_t(b) * kDirs * kSets * S;
+            Xo[base + size_t(2 * f) * kSets * S + st * S + j] = mk(wm * rp, wm * ip);
+            Xo[base + size_t(2 * f + 1) * kSets * S + st * S + j] = mk(wm * rm, wm * im);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- X2X merge-and-shift
+template <typename T>
+__global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const int *child, const int *leaf,
+                      const cpx<T> *Xo, cpx<T> *Xi) {
+    __shared__ int src[216];
+    int P = parents[blockIdx.x];
+    int d = blockIdx.y;
+    const int S = D.S;
+    for (int sl = threadIdx.x; sl < 216; sl += blockDim.x) {
+        int q = sl >> 3, o = sl & 7;
+        int Q = coll[27 * P + q];
+        src[sl] = (Q >= 0 && !leaf[Q]) ? child[8 * Q + o] : -1;
+    }
+    __syncthreads();
+    int ng = D.grp_n[d];
+    const int *goff = D.grp_off + d * (kGroupMax + 1);
+    const int *gmask = D.grp_mask + d * kGroupMax;
+    const int *slots = D.slot_list + d * 216;
+    int ch[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) ch[t] = child[8 * P + t];
+    for (int e = threadIdx.x; e < kSets * S; e += blockDim.x) {
+        int j = e % S;
+        cpx<T> acc[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc[t] = mk<T>(0, 0);
+        for (int g = 0; g < ng; ++g) {
+            cpx<T> ga = mk<T>(0, 0);
+            for (int z = goff[g]; z < goff[g + 1]; ++z) {
+                int ent = slots[z];
+                int sb = src[ent & 255];
+                if (sb < 0) continue;
+                cpx<T> x = Xo[(size_t(sb) * kDirs + d) * kSets * S + e];
+                ga += x * D.shift[size_t(ent >> 8) * S + j];
+            }
+            int mask = gmask[g];
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                if ((mask >> t) & 1) acc[t] += ga;
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (ch[t] < 0) continue;
+            cpx<T> sh = D.shift[size_t(D.child_shift[d * 8 + t]) * S + j];
+            Xi[(size_t(ch[t]) * kDirs + d) * kSets * S + e] = acc[t] * sh;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- X2L
+template <typename T>
+__global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *L) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int b = b0 + blockIdx.x;
+    const int p = D.p, nc = ncoef(p), s = D.s, S = D.S, P1 = p + 1;
+    cpx<T> *I = reinterpret_cast<cpx<T> *>(smem_raw);
+    cpx<T> *Bk = I + kSets * S;
+    cpx<T> *Lf = Bk + kSets * s * P1;
+    cpx<T> *Lw = Lf + kSets * nc;
+    cpx<T> *Lr = Lw + kSets * nc;
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] = mk<T>(0, 0);
+    for (int f = 0; f < 3; ++f) {
+        for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lf[i] = mk<T>(0, 0);
+        for (int sg = 0; sg < 2; ++sg) {
+            int d = 2 * f + sg;
+            __syncthreads();
+            const cpx<T> *src = Xi + (size_t(b) * kDirs + d) * kSets * S;
+            for (int i = threadIdx.x; i < kSets * S; i += blockDim.x) I[i] = src[i];
+            __syncthreads();
+            // b_k^m = sum_{j < M_k/2} (I_j + (-1)^m conj I_j) e^{-i m a_j}
+            for (int e = threadIdx.x; e < kSets * s * P1; e += blockDim.x) {
+                int st = e / (s * P1), rem = e - st * s * P1, k = rem / P1, m = rem - k * P1;
+                int j0 = D.k_start[k], j1 = D.k_start[k + 1];
+                int Mk = 2 * (j1 - j0);
+                const cpx<T> *rt = D.roots + 2 * j0;
+                cpx<T> a = mk<T>(0, 0);
+                for (int j = j0; j < j1; ++j) {
+                    cpx<T> w = I[st * S + j];
+                    cpx<T> u = (m & 1) ? mk<T>(0, 2 * w.y) : mk<T>(2 * w.x, 0);   // w + (-1)^m conj w
+                    cpx<T> r = rt[(m * (j - j0)) % Mk];
+                    a += u * conj(r);
+                }
+                Bk[e] = a;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
+                int st = e / nc, i = e - st * nc;
+                int n = deg_of(i), m = i - tri(n, 0);
+                cpx<T> a = mk<T>(0, 0);
+                for (int k = 0; k < s; ++k) a += D.x2l_c[size_t(k) * nc + i] * Bk[(st * s + k) * P1 + m];
+                a = mul_ipow(a, m);
+                if (sg == 1 && ((n + m) & 1)) a = mk(-a.x, -a.y);
+                Lf[e] += a;
+            }
+        }
+        __syncthreads();
+        if (f == 0) {
+            for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lf[i];
+        } else {
+            rotate_sets(D.rot_bwd + size_t(f - 1) * D.rot_len, D.rot_off, p, Lf, Lr);
+            __syncthreads();
+            for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lr[i];
+        }
+        __syncthreads();
+    }
+    cpx<T> *dst = L + size_t(b) * kSets * nc;
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) dst[i] += Lw[i];
+}
+
+// ---------------------------------------------------------------- far-field evaluation
+constexpr int kNE = 18;
+
+// Build the 18 evaluation expansions of Eq. (2.8) from 4 source expansions.
+// IRREG = multipole source (degrees grow by one per derivative), else local.
+template <typename T, bool IRREG>
+__device__ void build_eval_set(const cpx<T> *src, int p, int P, cpx<T> *EV, cpx<T> *tmp, double cbx, double cby,
+                               double cbz) {
+    const int st = ncoef(P);
+    // 0..2 values
+    for (int i = threadIdx.x; i < 3 * st; i += blockDim.x) {
+        int k = i / st, c = i - k * st;
+        EV[k * st + c] = c < ncoef(p) ? src[k * ncoef(p) + c] : mk<T>(0, 0);
+    }
+    // 3..11 gradients of sets 0..2 (index 3 + 3k + a), tmp[0..2] gradient of set 3
+    for (int k = 0; k < 4; ++k) {
+        cpx<T> *gx = k < 3 ? EV + (3 + 3 * k) * st : tmp;
+        if (IRREG) d_multipole(src + k * ncoef(p), p, gx, gx + st, gx + 2 * st, st, P);
+        else d_local(src + k * ncoef(p), p, gx, gx + st, gx + 2 * st, st, P);
+    }
+    __syncthreads();
+    // 12..14: G4'_a = dL4_a - sum_k cb_k dL_k,a ; tmp[3] = L_C = dxL1 + dyL2 + dzL3
+    T cb[3] = {T(cbx), T(cby), T(cbz)};
+    for (int i = threadIdx.x; i < st; i += blockDim.x) {
+        for (int a = 0; a < 3; ++a) {
+            cpx<T> g = tmp[a * st + i];
+            for (int k = 0; k < 3; ++k) {
+                cpx<T> v = EV[(3 + 3 * k + a) * st + i];
+                g.x -= cb[k] * v.x;
+                g.y -= cb[k] * v.y;
+            }
+            EV[(12 + a) * st + i] = g;
+        }
+        cpx<T> lc = EV[(3 + 0) * st + i] + EV[(3 + 3 + 1) * st + i] + EV[(3 + 6 + 2) * st + i];
+        tmp[3 * st + i] = lc;
+    }
+    __syncthreads();
+    int pl = IRREG ? p + 1 : p - 1;
+    if (IRREG) d_multipole(tmp + 3 * st, pl, EV + 15 * st, EV + 16 * st, EV + 17 * st, st, P);
+    else d_local(tmp + 3 * st, pl, EV + 15 * st, EV + 16 * st, EV + 17 * st, st, P);
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void k_far_eval(const int *leaves, DevTables<T> D, const int *beg, const int *end, const double *ctr,
+                           const double *side, const int *lvl, const int *bsys, const int *woff, const int *widx,
+                           const double *pos, int64_t n, SysConst sc, const cpx<T> *L, const cpx<T> *M,
+                           double *ufar) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int li = blockIdx.x;
+    int b = leaves[li];
+    const int p = D.p, nc = ncoef(p), P = p + 2, st = ncoef(P);
+    T *smr = reinterpret_cast<T *>(smem_raw);
+    Rec<T> R = load_rec(D, smr);
+    cpx<T> *EV = reinterpret_cast<cpx<T> *>(smr + ((rec_floats<T>(p) + 1) & ~1));
+    cpx<T> *tmp = EV + kNE * st;
+    cpx<T> *srcs = tmp + 4 * st;
+    int sy = bsys[b];
+    double a = sc.a[sy], sv = sc.s[sy];
+    double C1 = sv / (8.0 * kPi), C2 = sv * a * a / (12.0 * kPi);
+    double c0x = sc.cube[4 * sy], c0y = sc.cube[4 * sy + 1], c0z = sc.cube[4 * sy + 2];
+    double cbx = ctr[3 * b], cby = ctr[3 * b + 1], cbz = ctr[3 * b + 2];
+    double hb = side[b];
+    int j0 = beg[b], j1 = end[b];
+    int nw = woff[li + 1] - woff[li];
+    bool has_local = lvl[b] >= 2;
+    for (int jc = j0; jc < j1; jc += blockDim.x) {
+        int j = jc + threadIdx.x;
+        bool act = j < j1;
+        double x = act ? pos[j] : cbx, y = act ? pos[n + j] : cby, z = act ? pos[2 * n + j] : cbz;
+        double u[3] = {0, 0, 0};
+        for (int w = -1; w < nw; ++w) {
+            if (w < 0 && !has_local) continue;
+            int C = w < 0 ? b : widx[woff[li] + w];
+            const cpx<T> *E = w < 0 ? L + size_t(C) * kSets * nc : M + size_t(C) * kSets * nc;
+            __syncthreads();
+            for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) srcs[i] = E[i];
+            __syncthreads();
+            if (w < 0) build_eval_set<T, false>(srcs, p, P, EV, tmp, cbx - c0x, cby - c0y, cbz - c0z);
+            else build_eval_set<T, true>(srcs, p, P, EV, tmp, cbx - c0x, cby - c0y, cbz - c0z);
+            double h = side[C];
+            double ih = 1.0 / h;
+            T acc[kNE];
+#pragma unroll
+            for (int q = 0; q < kNE; ++q) acc[q] = 0;
+            T vx = T((x - ctr[3 * C]) * ih), vy = T((y - ctr[3 * C + 1]) * ih), vz = T((z - ctr[3 * C + 2]) * ih);
+            if (w < 0) eval_fields<T, kNE, false>(vx, vy, vz, p, EV, st, R.a, R.b, R.c, acc);
+            else eval_fields<T, kNE, true>(vx, vy, vz, P, EV, st, R.a, R.b, R.c, acc);
+            double xi[3] = {(x - cbx) * ih, (y - cby) * ih, (z - cbz) * ih};
+            for (int d = 0; d < 3; ++d) {
+                double v = double(acc[d]);
+                for (int k = 0; k < 3; ++k) v -= xi[k] * double(acc[3 + 3 * k + d]);
+                u[d] += C1 * ih * v + C1 * ih * ih * double(acc[12 + d]) - C2 * ih * ih * ih * double(acc[15 + d]);
+            }
+        }
+        if (act)
+            for (int d = 0; d < 3; ++d) ufar[3 * size_t(j) + d] = u[d];
+    }
+}
+
+// Laplace diagnostic: potential, gradient and Hessian of each set from L2P and M2P.
+template <typename T, bool IRREG>
+__device__ void build_lap_set(const cpx<T> *src, int p, int P, cpx<T> *EV, cpx<T> *tmp) {
+    const int st = ncoef(P);
+    for (int i = threadIdx.x; i < st; i += blockDim.x) EV[i] = i < ncoef(p) ? src[i] : mk<T>(0, 0);
+    if (IRREG) d_multipole(src, p, EV + st, EV + 2 * st, EV + 3 * st, st, P);
+    else d_local(src, p, EV + st, EV + 2 * st, EV + 3 * st, st, P);
+    __syncthreads();
+    int pd = IRREG ? p + 1 : p - 1;
+    // Hessian rows: d/dx of (x, y, z) derivatives -> 4..6, d/dy -> 7..9, d/dz -> 10..12
+    for (int a = 0; a < 3; ++a) {
+        if (IRREG) d_multipole(EV + (1 + a) * st, pd, tmp, tmp + st, tmp + 2 * st, st, P);
+        else d_local(EV + (1 + a) * st, pd, tmp, tmp + st, tmp + 2 * st, st, P);
+        __syncthreads();
+        for (int i = threadIdx.x; i < st; i += blockDim.x)
+            for (int c = 0; c < 3; ++c) EV[(4 + 3 * a + c) * st + i] = tmp[c * st + i];
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void k_lap_eval(const int *leaves, DevTables<T> D, const int *beg, const int *end, const double *ctr,
+                           const double *side, const int *lvl, const int *woff, const int *widx, const double *pos,
+                           int64_t n, const cpx<T> *L, const cpx<T> *M, double *out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int li = blockIdx.x;
+    int b = leaves[li];
+    const int p = D.p, nc = ncoef(p), P = p + 2, st = ncoef(P);
+    T *smr = reinterpret_cast<T *>(smem_raw);
+    Rec<T> R = load_rec(D, smr);   // recurrence tables cover degree p + 2
+    cpx<T> *EV = reinterpret_cast<cpx<T> *>(smr + ((rec_floats<T>(p) + 1) & ~1));
+    cpx<T> *tmp = EV + 13 * st;
+    cpx<T> *srcs = tmp + 3 * st;
+    double cbx = ctr[3 * b], cby = ctr[3 * b + 1], cbz = ctr[3 * b + 2];
+    int j0 = beg[b], j1 = end[b];
+    int nw = woff[li + 1] - woff[li];
+    bool has_local = lvl[b] >= 2;
+    for (int jc = j0; jc < j1; jc += blockDim.x) {
+        int j = jc + threadIdx.x;
+        bool act = j < j1;
+        double x = act ? pos[j] : cbx, y = act ? pos[n + j] : cby, z = act ? pos[2 * n + j] : cbz;
+        double res[kSets][13];
+        for (int k = 0; k < kSets; ++k)
+            for (int c = 0; c < 13; ++c) res[k][c] = 0;
+        for (int w = -1; w < nw; ++w) {
+            if (w < 0 && !has_local) continue;
+            int C = w < 0 ? b : widx[woff[li] + w];
+            const cpx<T> *E = w < 0 ? L + size_t(C) * kSets * nc : M + size_t(C) * kSets * nc;
+            double h = side[C], ih = 1.0 / h;
+            T vx = T((x - ctr[3 * C]) * ih), vy = T((y - ctr[3 * C + 1]) * ih), vz = T((z - ctr[3 * C + 2]) * ih);
+            for (int k = 0; k < kSets; ++k) {
+                __syncthreads();
+                for (int i = threadIdx.x; i < nc; i += blockDim.x) srcs[i] = E[k * nc + i];
+                __syncthreads();
+                if (w < 0) build_lap_set<T, false>(srcs, p, P, EV, tmp);
+                else build_lap_set<T, true>(srcs, p, P, EV, tmp);
+                T acc[13];
+#pragma unroll
+                for (int q = 0; q < 13; ++q) acc[q] = 0;
+                if (w < 0) eval_fields<T, 13, false>(vx, vy, vz, p, EV, st, R.a, R.b, R.c, acc);
+                else eval_fields<T, 13, true>(vx, vy, vz, P, EV, st, R.a, R.b, R.c, acc);
+                res[k][0] += ih * double(acc[0]);
+                for (int c = 1; c < 4; ++c) res[k][c] += ih * ih * double(acc[c]);
+                for (int c = 4; c < 13; ++c) res[k][c] += ih * ih * ih * double(acc[c]);
+            }
+        }
+        if (act)
+            for (int k = 0; k < kSets; ++k)
+                for (int c = 0; c < 13; ++c) out[(size_t(j) * kSets + k) * 13 + c] = res[k][c];
+    }
+}
+
+// ---------------------------------------------------------------- driver
+
+template <typename T>
+static size_t smem_p2x(int p) {
+    int nc = ncoef(p);
+    return sizeof(T) * ((rec_floats<T>(p) + 1) & ~1) + sizeof(cpx<T>) * (kChunkB * nc + kSets * nc) +
+           sizeof(T) * 4 * kChunkB + 64;
+}
+template <typename T>
+static size_t smem_m2x(int p, int s) {
+    int nc = ncoef(p);
+    return sizeof(cpx<T>) * (2 * kSets * nc + 2 * kSets * s * (p + 1));
+}
+template <typename T>
+static size_t smem_x2l(int p, int s, int S) {
+    int nc = ncoef(p);
+    return sizeof(cpx<T>) * (kSets * S + kSets * s * (p + 1) + 3 * kSets * nc);
+}
+template <typename T>
+static size_t smem_far(int p) {
+    int st = ncoef(p + 2);
+    return sizeof(T) * ((rec_floats<T>(p) + 1) & ~1) + sizeof(cpx<T>) * (kNE * st + 4 * st + kSets * ncoef(p)) + 64;
+}
+template <typename T>
+static size_t smem_lap(int p) {
+    int st = ncoef(p + 2);
+    return sizeof(T) * ((rec_floats<T>(p) + 1) & ~1) + sizeof(cpx<T>) * (13 * st + 3 * st + ncoef(p)) + 64;
+}
+
+template <typename K>
+static int set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) RPY_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+    return RPY_OK;
+}
+
+template <typename T>
+int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *lapq, double *ufar, double *lapout,
+              const SysConst &sc, cudaStream_t st) {
+    const int p = D.p, nc = ncoef(p);
+    cpx<T> *M = static_cast<cpx<T> *>(t.M), *L = static_cast<cpx<T> *>(t.L);
+    cpx<T> *Xo = static_cast<cpx<T> *>(t.Xo), *Xi = static_cast<cpx<T> *>(t.Xi);
+    int nbx = t.nbox;
+    RPY_CHECK(cudaMemsetAsync(L, 0, sizeof(cpx<T>) * size_t(nbx) * kSets * nc, st));
+    if (t.nlevels <= 2) {
+        // no box at level >= 2: nothing is far
+        if (ufar) RPY_CHECK(cudaMemsetAsync(ufar, 0, sizeof(double) * 3 * size_t(t.n), st));
+        if (lapout) RPY_CHECK(cudaMemsetAsync(lapout, 0, sizeof(double) * 52 * size_t(t.n), st));
+        return RPY_OK;
+    }
+    int b2 = t.level_off[2];
+    int n2 = nbx - b2;
+    // upward pass
+    size_t sp = smem_p2x<T>(p);
+    RPY_TRY(set_smem(k_p2x<T, 0>, sp));
+    RPY_TRY(set_smem(k_p2x<T, 1>, sp));
+    k_p2x<T, 0><<<n2, 128, sp, st>>>(b2, n2, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level, t.b_leaf,
+                                     t.b_sys, t.x_off, t.x_idx, t.pos, fs, lapq, t.n, sc, M);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
+    int Dd = 2 * nc;
+    int thr = ((Dd + 31) / 32) * 32;
+    size_t sm2 = sizeof(T) * kSets * Dd;
+    prof_mark(t, RPY_STAGE_M2M, st);
+    RPY_TRY(set_smem(k_m2m<T>, sm2));
+    RPY_TRY(set_smem(k_l2l<T>, sm2));
+    for (int l = t.nlevels - 2; l >= 2; --l) {
+        int lb = t.level_off[l], ln = t.level_off[l + 1] - lb;
+        if (ln > 0) {
+            k_m2m<T><<<ln, thr, sm2, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
+            RPY_LAUNCHED(1);
+        }
+    }
+    RPY_CHECK(cudaGetLastError());
+    // plane-wave M2L
+    prof_mark(t, RPY_STAGE_M2X, st);
+    size_t smx = smem_m2x<T>(p, D.s);
+    RPY_TRY(set_smem(k_m2x<T>, smx));
+    k_m2x<T><<<n2, 256, smx, st>>>(b2, n2, D, M, Xo);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
+    prof_mark(t, RPY_STAGE_X2X, st);
+    if (t.n_x2x_par > 0) {
+        dim3 g(t.n_x2x_par, kDirs);
+        k_x2x<T><<<g, 256, 0, st>>>(t.x2x_par, D, t.b_coll, t.b_child, t.b_leaf, Xo, Xi);
+        RPY_LAUNCHED(1);
+        RPY_CHECK(cudaGetLastError());
+    }
+    prof_mark(t, RPY_STAGE_X2L, st);
+    size_t sxl = smem_x2l<T>(p, D.s, D.S);
+    RPY_TRY(set_smem(k_x2l<T>, sxl));
+    k_x2l<T><<<n2, 256, sxl, st>>>(b2, n2, D, Xi, L);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
+    // X list
+    prof_mark(t, RPY_STAGE_P2L, st);
+    k_p2x<T, 1><<<n2, 128, sp, st>>>(b2, n2, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level, t.b_leaf,
+                                     t.b_sys, t.x_off, t.x_idx, t.pos, fs, lapq, t.n, sc, L);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
+    // downward pass
+    prof_mark(t, RPY_STAGE_L2L, st);
+    for (int l = 3; l < t.nlevels; ++l) {
+        int lb = t.level_off[l], ln = t.level_off[l + 1] - lb;
+        if (ln > 0) {
+            k_l2l<T><<<ln, thr, sm2, st>>>(lb, ln, D, t.b_parent, t.b_cell, L);
+            RPY_LAUNCHED(1);
+        }
+    }
+    RPY_CHECK(cudaGetLastError());
+    prof_mark(t, RPY_STAGE_EVAL, st);
+    if (ufar) {
+        size_t sf = smem_far<T>(p);
+        RPY_TRY(set_smem(k_far_eval<T>, sf));
+        k_far_eval<T><<<t.nleaf, 128, sf, st>>>(t.leaves, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level,
+                                                t.b_sys, t.w_off, t.w_idx, t.pos, t.n, sc, L, M, ufar);
+        RPY_LAUNCHED(1);
+        RPY_CHECK(cudaGetLastError());
+    }
+    if (lapout) {
+        size_t sl = smem_lap<T>(p);
+        RPY_TRY(set_smem(k_lap_eval<T>, sl));
+        k_lap_eval<T><<<t.nleaf, 128, sl, st>>>(t.leaves, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level,
+                                                t.w_off, t.w_idx, t.pos, t.n, L, M, lapout);
+        RPY_LAUNCHED(1);
+        RPY_CHECK(cudaGetLastError());
+    }
+    return RPY_OK;
+}
+
+template int run_far_t<double>(Tree &, const DevTables<double> &, const double *, const double *, double *, double *,
+                               const SysConst &, cudaStream_t);
+template int run_far_t<float>(Tree &, const DevTables<float> &, const double *, const double *, double *, double *,
+                              const SysConst &, cudaStream_t);
+
+}  // namespace rpy

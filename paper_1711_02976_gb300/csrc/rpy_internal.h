@@ -1,0 +1,239 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/rpyfmm.h"
+
+#define RPY_HD __host__ __device__ __forceinline__
+
+namespace rpy {
+
+// ---------------------------------------------------------------- status
+
+// Device-side error flags (bitwise OR into DevStatus::flags).
+enum : unsigned {
+    DEVERR_NONFINITE = 1u,     // a position was NaN/inf
+    DEVERR_STACK = 2u,         // list-builder traversal stack overflow
+    DEVERR_CAPACITY = 4u,      // a fixed-size device table overflowed
+};
+
+struct CudaError {
+    cudaError_t err;
+    const char *what;
+};
+
+void set_last_cuda_error(const char *what, cudaError_t e);
+int check_cuda(const char *what, cudaError_t e);   // returns RPY_OK or RPY_ERR_CUDA/OOM
+
+#define RPY_CHECK(call)                                                   \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return rpy::check_cuda(#call, e_);         \
+    } while (0)
+
+#define RPY_TRY(expr)                                                     \
+    do {                                                                  \
+        int s_ = (expr);                                                  \
+        if (s_ != RPY_OK) return s_;                                      \
+    } while (0)
+
+// ---------------------------------------------------------------- complex
+
+template <typename T>
+struct alignas(2 * sizeof(T)) cpx {
+    T x, y;
+};
+
+template <typename T> RPY_HD cpx<T> mk(T a, T b) { cpx<T> r; r.x = a; r.y = b; return r; }
+template <typename T> RPY_HD cpx<T> operator+(cpx<T> a, cpx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T> RPY_HD cpx<T> operator-(cpx<T> a, cpx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T> RPY_HD cpx<T> operator*(cpx<T> a, cpx<T> b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename T> RPY_HD cpx<T> operator*(T s, cpx<T> a) { return mk(s * a.x, s * a.y); }
+template <typename T> RPY_HD cpx<T> conj(cpx<T> a) { return mk(a.x, -a.y); }
+template <typename T> RPY_HD void operator+=(cpx<T> &a, cpx<T> b) { a.x += b.x; a.y += b.y; }
+// multiply by i^k
+template <typename T> RPY_HD cpx<T> mul_ipow(cpx<T> a, int k) {
+    switch (k & 3) {
+        case 0: return a;
+        case 1: return mk(-a.y, a.x);
+        case 2: return mk(-a.x, -a.y);
+        default: return mk(a.y, -a.x);
+    }
+}
+
+// index of coefficient (n, m), 0 <= m <= n, in triangular storage
+RPY_HD int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+RPY_HD int ncoef(int p) { return (p + 1) * (p + 2) / 2; }
+
+// ---------------------------------------------------------------- settings
+
+constexpr int kSets = 4;          // Laplace charge sets L1..L4 (Sec. 2)
+constexpr int kDirs = 6;          // +z -z +x -x +y -y plane-wave directions
+constexpr int kMaxP = 29;         // largest supported expansion order (p + 2 < 32 warp lanes)
+constexpr int kMaxLevel = 21;
+
+struct ExpQuad {                  // plane-wave quadrature (box units)
+    int s = 0;                    // lambda nodes
+    std::vector<double> lambda, weight;
+    std::vector<int> m;           // trapezoid counts (even)
+    int terms() const { int t = 0; for (int v : m) t += v; return t; }
+    int half() const { return terms() / 2; }
+};
+
+const ExpQuad &exp_quadrature(int digits);
+int default_order(int digits);
+int default_leaf_cap(int digits);
+
+// Operator tables of one (p, digits) setting, uploaded once per device.
+struct OpTables {
+    int p = 0, nc = 0, digits = 0, s = 0, S = 0;   // S = stored plane waves (half of sum M_k)
+    // host copies (double) ----------------------------------------------
+    std::vector<double> m2m_t;    // [8][D][D] transposed real M2M (D = 2 nc), column = output
+    std::vector<double> l2l_t;    // [8][D][D] transposed real L2L
+    std::vector<double> rot_fwd;  // [2 frames][sum_n (2n+1)^2] real blocks world -> frame (x, y)
+    std::vector<double> rot_bwd;  // [2 frames][...] frame -> world
+    std::vector<int> rot_off;     // [p+1] offset of degree-n block
+    std::vector<double> m2x_c;    // [s][nc]  lambda_k^n / sqrt((n-m)!(n+m)!)
+    std::vector<double> x2l_c;    // [s][nc]  (-lambda_k)^n / sqrt((n-m)!(n+m)!)
+    std::vector<int> e_k;         // [S] node of stored plane wave e
+    std::vector<double> e_cos, e_sin, e_wm;   // [S] cos a, sin a, w_k / M_k
+    std::vector<int> k_start;     // [s+1] first stored e of node k
+    std::vector<double> shift;    // [216][S][2] e^{-lambda dz + i lambda (dx cos a + dy sin a)}
+    // merge-and-shift groups per direction
+    std::vector<int> grp_off;     // [6][G_MAX+1] start of group g in slot list (per direction)
+    std::vector<int> grp_n;       // [6] number of groups
+    std::vector<int> grp_mask;    // [6][G_MAX] child mask of group
+    std::vector<int> slot_list;   // [6][216] (slot | (shift index << 8)) by group
+    std::vector<int> child_shift; // [6][8] shift index parent centre -> child centre
+    std::vector<double> roots;    // [2S][2] e^{2 pi i r / M_k}, r < M_k, node k at 2 k_start[k]
+    std::vector<double> rec_a, rec_b, rec_c, rec_cm;   // harmonic recurrences to degree p + 2
+};
+constexpr int kGroupMax = 32;
+
+int build_tables(int p, int digits, OpTables &t);   // host computation, no CUDA
+
+// device copies
+template <typename T>
+struct DevTables {
+    int p, nc, s, S, rot_len;
+    const T *m2m_t, *l2l_t, *rot_fwd, *rot_bwd;
+    const int *rot_off;
+    const T *rec_a, *rec_b, *rec_c, *rec_cm;
+    const cpx<T> *roots;
+    const T *m2x_c, *x2l_c;
+    const int *e_k, *k_start;
+    const T *e_cos, *e_sin, *e_wm;
+    const cpx<T> *shift;
+    const int *grp_off, *grp_n, *grp_mask, *slot_list, *child_shift;
+};
+
+// ---------------------------------------------------------------- tree
+
+struct Tree {
+    int device = 0;
+    cudaStream_t last_stream = nullptr;
+    int64_t n = 0;
+    int nsys = 0;
+    rpy_build_params params{};
+    int p = 0;
+    std::vector<int64_t> sys_off_h;   // host copy, nsys+1
+    std::vector<double> a_h;          // host copy, nsys
+    // systems (device)
+    int64_t *sys_off = nullptr;
+    double *sys_a = nullptr;
+    double *sys_cube = nullptr;       // [nsys][4]: centre x, y, z, side
+    // beads (device, sorted order)
+    int *perm = nullptr;              // sorted -> caller
+    uint64_t *keys = nullptr;
+    double *pos = nullptr;            // SoA [3][n]
+    int *bead_sys = nullptr;
+    // boxes (device)
+    int nbox = 0, nbox_cap = 0, nlevels = 0;
+    std::vector<int> level_off;       // host, nlevels+1
+    int *b_level = nullptr, *b_begin = nullptr, *b_end = nullptr, *b_parent = nullptr;
+    int *b_child = nullptr;           // [nbox][8]
+    int *b_coll = nullptr;            // [nbox][27]
+    int *b_cell = nullptr;            // [nbox][3]
+    int *b_sys = nullptr, *b_leaf = nullptr, *b_leafid = nullptr;
+    double *b_center = nullptr;       // [nbox][3]
+    double *b_side = nullptr;
+    int nleaf = 0;
+    int *leaves = nullptr;
+    // lists (device CSR)
+    int *u_off = nullptr, *u_idx = nullptr;
+    int *w_off = nullptr, *w_idx = nullptr;
+    int *x_off = nullptr, *x_idx = nullptr;
+    int64_t n_u = 0, n_w = 0, n_x = 0, u_pairs = 0;
+    int max_leaf_count = 0, leaves_over_cap = 0;
+    // level-2+ boxes with children (X2X parents), and boxes at level >= 2
+    int n_x2x_par = 0, *x2x_par = nullptr;
+    // expansions and matvec workspace
+    void *M = nullptr, *L = nullptr, *Xo = nullptr, *Xi = nullptr;
+    double *fs = nullptr;             // sorted forces SoA [3][n]
+    double *u_near = nullptr, *u_far = nullptr;   // sorted [n][3]
+    double *lap_q = nullptr;          // [n][4] sorted charges for the Laplace debug path
+    double *sys_s = nullptr;          // [nsys] kT/eta of the last matvec
+    std::vector<double> sys_s_h;
+    unsigned *dev_status = nullptr;
+    int64_t device_bytes = 0;
+    double build_ms = 0;
+    // debug V lists (built on request)
+    int *v_off = nullptr, *v_idx = nullptr;
+    int64_t n_v = 0;
+    // tables
+    OpTables tabs;
+    void *dtabs_mem = nullptr;        // one device block holding all tables
+    DevTables<double> dt64{};
+    DevTables<float> dt32{};
+    // scratch for builds
+    std::vector<void *> allocs;       // every cudaMalloc of the handle
+    // per-stage profiling (events recorded between stages when enabled)
+    bool prof = false;
+    cudaEvent_t ev[16] = {};
+    bool ev_used[16] = {};
+};
+
+// stage markers: record event k on st when profiling is on
+void prof_mark(Tree &t, int k, cudaStream_t st);
+
+// count of kernel launches issued by the library
+void note_launches(int n);
+#define RPY_LAUNCHED(n) rpy::note_launches(n)
+
+int tree_build(Tree &t, const double *pos_dev, cudaStream_t st);
+int tree_alloc_workspace(Tree &t, cudaStream_t st);
+int tree_upload_tables(Tree &t, cudaStream_t st);
+int tree_build_vlists(Tree &t, cudaStream_t st);
+void tree_release(Tree &t);
+int dev_alloc(Tree &t, void **p, size_t bytes);
+
+// per-system constants seen by the kernels
+struct SysConst {
+    const double *cube;   // [nsys][4]
+    const double *a;      // [nsys]
+    const double *s;      // [nsys] kT/eta
+};
+
+template <typename T>
+int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *lapq, double *ufar, double *lapout,
+              const SysConst &sc, cudaStream_t st);
+int run_p2p(Tree &t, const double *fs, double *unear, const SysConst &sc, cudaStream_t st);
+const char *last_cuda_error_text();
+
+// matvec stages (rpy_fmm.cu / rpy_p2p.cu)
+int run_matvec(Tree &t, const double *f_dev, const double *s_per_sys_host, double *u_dev, int parts,
+               cudaStream_t st);
+int run_laplace_far(Tree &t, const double *q_dev, double *out_dev, cudaStream_t st);
+
+// generic device helpers (rpy_tree.cu)
+int exclusive_scan_i32(const int *in, int *out, int n, int *total_host, void *tmp, size_t tmp_bytes,
+                       cudaStream_t st);
+size_t scan_tmp_bytes(int n);
+
+}  // namespace rpy

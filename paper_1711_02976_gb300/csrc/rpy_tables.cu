@@ -1,0 +1,400 @@
+// Host construction of the FMM operator tables for one (p, digits) setting.
+//
+// All expansions are stored in box units: for a box of side h and centre c,
+//   multipole  phi(x) = (1/h) sum_{n,m} M_n^m z_n^m((x - c)/h),
+//   local      phi(x) = (1/h) sum_{n,m} L_n^m y_n^m((x - c)/h),
+// so every operator below is independent of the level (Sec. 2 expansion
+// forms; the scaling is this library's choice).
+//
+// Tables:
+//   M2M / L2L   dense real matrices per child octant, built from the
+//               addition theorem of regular solid harmonics
+//               R_n^m(u + v) = sum_{k,l} R_k^l(u) R_{n-k}^{m-l}(v),
+//               R_n^m = r^n P_n^m e^{i m phi} / (n+m)!, which in the paper's
+//               normalisation reads y_n^m(u+v) = sum G_{nm,kl}(v) y_k^l(u).
+//   rotations   Y_n^m(A w) = sum_m' K_{m m'} Y_n^m'(w) for the two coordinate
+//               frames whose z axis is world x or world y, computed by exact
+//               quadrature on the sphere.
+//   plane waves the quadrature of gen_exp_quadrature.py; M2X coefficients
+//               lambda^n / sqrt((n-m)!(n+m)!), X2L coefficients
+//               (-lambda)^n / sqrt((n-m)!(n+m)!), and the diagonal shift
+//               factors e^{-lambda dz + i lambda (dx cos a + dy sin a)}.
+//   groups      merge-and-shift bookkeeping: which children of a parent's
+//               colleagues feed which children of the parent, per direction.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+
+#include "exp_quadrature.h"
+#include "rpy_harmonics.h"
+
+namespace rpy {
+
+using cd = std::complex<double>;
+
+static std::vector<double> g_fact;   // n! for n <= 4 kMaxP + 8
+
+static double fact(int n) {
+    if (g_fact.empty()) {
+        g_fact.resize(4 * kMaxP + 9);
+        g_fact[0] = 1.0;
+        for (size_t i = 1; i < g_fact.size(); ++i) g_fact[i] = g_fact[i - 1] * double(i);
+    }
+    return g_fact[n];
+}
+
+static double Nnm(int n, int m) {   // sqrt((n+|m|)!(n-|m|)!)
+    int am = m < 0 ? -m : m;
+    return std::sqrt(fact(n + am) * fact(n - am));
+}
+
+static double sgn_m(int m) { return (m >= 0 || ((-m) % 2 == 0)) ? 1.0 : -1.0; }
+
+// y_n^m(v) for all n <= p, m in [-n, n] (complex, full range).
+static void regular_full(const double v[3], int p, std::vector<cd> &out) {
+    HarmRec h = harm_rec(p);
+    std::vector<cpx<double>> tmp(ncoef(p));
+    regular_all<double>(v[0], v[1], v[2], p, h.a.data(), h.b.data(), h.c.data(), tmp.data());
+    out.assign((p + 1) * (p + 1), cd(0, 0));
+    for (int n = 0; n <= p; ++n)
+        for (int m = 0; m <= n; ++m) {
+            cd y(tmp[tri(n, m)].x, tmp[tri(n, m)].y);
+            out[n * n + n + m] = y;
+            out[n * n + n - m] = std::conj(y);
+        }
+}
+
+// G_{nm,kl}(v): y_n^m(u + v) = sum_{k<=n,l} G y_k^l(u).
+struct AddTheorem {
+    int p;
+    std::vector<cd> yv;   // y_j^q(v), full
+    AddTheorem(int p_, const double v[3]) : p(p_) { regular_full(v, p_, yv); }
+    cd R(int j, int q) const {   // R_j^q(v) = y_j^q / (s_q N_j^q)
+        if (q > j || -q > j) return cd(0, 0);
+        return yv[j * j + j + q] / (sgn_m(q) * Nnm(j, q));
+    }
+    cd G(int n, int m, int k, int l) const {
+        if (k > n) return cd(0, 0);
+        return (sgn_m(m) * Nnm(n, m) / (sgn_m(l) * Nnm(k, l))) * R(n - k, m - l);
+    }
+};
+
+// Accumulate coefficient c * X^{(k,l)} into output (n, m>=0), real 2-layout.
+// X^{(k,l)} = X_k^|l| for l >= 0, conj(X_k^|l|) for l < 0.
+static void add_real(std::vector<double> &Tt, int D, int out_n, int out_m, int in_k, int in_l, cd c) {
+    int ro = 2 * tri(out_n, out_m);
+    int ci = 2 * tri(in_k, in_l < 0 ? -in_l : in_l);
+    double cr = c.real(), cim = c.imag();
+    double s = in_l < 0 ? -1.0 : 1.0;
+    // out_re += cr xr - s ci xi ; out_im += ci xr + s cr xi   (stored transposed [in][out])
+    Tt[size_t(ci) * D + ro] += cr;
+    Tt[size_t(ci + 1) * D + ro] += -s * cim;
+    Tt[size_t(ci) * D + ro + 1] += cim;
+    Tt[size_t(ci + 1) * D + ro + 1] += s * cr;
+}
+
+static void octant_delta(int o, double d[3]) {
+    for (int a = 0; a < 3; ++a) d[a] = ((o >> a) & 1) ? 0.25 : -0.25;
+}
+
+static void build_m2m(int p, std::vector<double> &out) {
+    int nc = ncoef(p), D = 2 * nc;
+    out.assign(size_t(8) * D * D, 0.0);
+    for (int o = 0; o < 8; ++o) {
+        double d[3];
+        octant_delta(o, d);
+        AddTheorem at(p, d);
+        std::vector<double> Tt(size_t(D) * D, 0.0);
+        // M^p_n^m = sum_{k<=n,l} conj(G_{nm,kl}(d)) 2^{-k} M^c_k^l
+        for (int n = 0; n <= p; ++n)
+            for (int m = 0; m <= n; ++m)
+                for (int k = 0; k <= n; ++k)
+                    for (int l = -k; l <= k; ++l) {
+                        cd g = at.G(n, m, k, l);
+                        if (g == cd(0, 0)) continue;
+                        add_real(Tt, D, n, m, k, l, std::conj(g) * std::ldexp(1.0, -k));
+                    }
+        std::memcpy(&out[size_t(o) * D * D], Tt.data(), sizeof(double) * D * D);
+    }
+}
+
+static void build_l2l(int p, std::vector<double> &out) {
+    int nc = ncoef(p), D = 2 * nc;
+    out.assign(size_t(8) * D * D, 0.0);
+    for (int o = 0; o < 8; ++o) {
+        double d[3];
+        octant_delta(o, d);
+        AddTheorem at(p, d);
+        std::vector<double> Tt(size_t(D) * D, 0.0);
+        // L^c_k^l = 2^{-k-1} sum_{n>=k, m} L^p_n^m G_{nm,kl}(d)
+        for (int k = 0; k <= p; ++k)
+            for (int l = 0; l <= k; ++l)
+                for (int n = k; n <= p; ++n)
+                    for (int m = -n; m <= n; ++m) {
+                        cd g = at.G(n, m, k, l);
+                        if (g == cd(0, 0)) continue;
+                        add_real(Tt, D, k, l, n, m, g * std::ldexp(1.0, -k - 1));
+                    }
+        std::memcpy(&out[size_t(o) * D * D], Tt.data(), sizeof(double) * D * D);
+    }
+}
+
+// Gauss-Legendre nodes on [-1, 1] (Newton on P_n).
+static void legendre_pd(int n, double z, double &p, double &dp) {
+    double p0 = 1.0, p1 = 0.0;
+    for (int j = 1; j <= n; ++j) {
+        double p2 = p1;
+        p1 = p0;
+        p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+    }
+    p = p0;
+    dp = n * (z * p0 - p1) / (z * z - 1.0);
+}
+
+static void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), p = 0.0, dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            legendre_pd(n, z, p, dp);
+            double dz = p / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        legendre_pd(n, z, p, dp);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// K_{m m'} with Y_n^m(A w) = sum_{m'} K_{m m'} Y_n^{m'}(w), all m, m' in [-n, n].
+static std::vector<cd> rotmat(const double A[9], int n) {
+    int dim = 2 * n + 1;
+    std::vector<cd> K(size_t(dim) * dim, cd(0, 0));
+    std::vector<double> gx, gw;
+    gauss_legendre(n + 1, gx, gw);
+    int nphi = 2 * n + 2;
+    std::vector<cd> ya, yw;
+    for (size_t i = 0; i < gx.size(); ++i) {
+        double ct = gx[i], st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+        for (int j = 0; j < nphi; ++j) {
+            double ph = 2.0 * M_PI * j / nphi;
+            double w[3] = {st * std::cos(ph), st * std::sin(ph), ct};
+            double aw[3] = {A[0] * w[0] + A[1] * w[1] + A[2] * w[2], A[3] * w[0] + A[4] * w[1] + A[5] * w[2],
+                            A[6] * w[0] + A[7] * w[1] + A[8] * w[2]};
+            regular_full(aw, n, ya);
+            regular_full(w, n, yw);
+            double wt = gw[i] * 2.0 * M_PI / nphi * (2.0 * n + 1.0) / (4.0 * M_PI);
+            for (int m = -n; m <= n; ++m)
+                for (int mp = -n; mp <= n; ++mp)
+                    K[size_t(m + n) * dim + (mp + n)] += wt * ya[n * n + n + m] * std::conj(yw[n * n + n + mp]);
+        }
+    }
+    return K;
+}
+
+// Frame matrices (rows = frame axes in world coordinates).
+static const double kQx[9] = {0, 1, 0, 0, 0, 1, 1, 0, 0};   // x'=y, y'=z, z'=x
+static const double kQy[9] = {0, 0, 1, 1, 0, 0, 0, 1, 0};   // x'=z, y'=x, z'=y
+
+static void transpose3(const double A[9], double B[9]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) B[3 * i + j] = A[3 * j + i];
+}
+
+// Real per-degree blocks, layout [off_n + out*(2(n+1)) + in], 2-real local index 2m+part.
+static void build_rotations(int p, std::vector<double> &fwd, std::vector<double> &bwd, std::vector<int> &off) {
+    off.resize(p + 2);
+    off[0] = 0;
+    for (int n = 0; n <= p; ++n) off[n + 1] = off[n] + 4 * (n + 1) * (n + 1);
+    fwd.assign(size_t(2) * off[p + 1], 0.0);
+    bwd.assign(size_t(2) * off[p + 1], 0.0);
+    for (int f = 0; f < 2; ++f) {
+        const double *Q = f == 0 ? kQx : kQy;
+        double Qt[9];
+        transpose3(Q, Qt);
+        for (int n = 0; n <= p; ++n) {
+            int B = 2 * (n + 1), dim = 2 * n + 1;
+            std::vector<cd> D = rotmat(Qt, n);   // forward: M'_{m'} = sum_m M_m D_{m m'}
+            std::vector<cd> K = rotmat(Q, n);    // backward: L_m = sum_{m'} L'_{m'} K_{m' m}
+            double *F = &fwd[size_t(f) * off[p + 1] + off[n]];
+            double *Bk = &bwd[size_t(f) * off[p + 1] + off[n]];
+            for (int mo = 0; mo <= n; ++mo)
+                for (int mi = -n; mi <= n; ++mi) {
+                    cd cf = D[size_t(mi + n) * dim + (mo + n)];
+                    cd cb = K[size_t(mi + n) * dim + (mo + n)];
+                    int ro = 2 * mo, ci = 2 * (mi < 0 ? -mi : mi);
+                    double s = mi < 0 ? -1.0 : 1.0;
+                    F[ro * B + ci] += cf.real();
+                    F[ro * B + ci + 1] += -s * cf.imag();
+                    F[(ro + 1) * B + ci] += cf.imag();
+                    F[(ro + 1) * B + ci + 1] += s * cf.real();
+                    Bk[ro * B + ci] += cb.real();
+                    Bk[ro * B + ci + 1] += -s * cb.imag();
+                    Bk[(ro + 1) * B + ci] += cb.imag();
+                    Bk[(ro + 1) * B + ci + 1] += s * cb.real();
+                }
+            // clean round-off of exact zeros / ones
+            for (int i = 0; i < B * B; ++i) {
+                if (std::fabs(F[i]) < 1e-15) F[i] = 0.0;
+                if (std::fabs(Bk[i]) < 1e-15) Bk[i] = 0.0;
+            }
+        }
+    }
+}
+
+// signed-permutation frame matrices P_d for the six directions
+static void frame_matrix(int d, int P[9]) {
+    static const int Pz[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    static const int Px[9] = {0, 1, 0, 0, 0, 1, 1, 0, 0};
+    static const int Py[9] = {0, 0, 1, 1, 0, 0, 0, 1, 0};
+    const int *B = d < 2 ? Pz : (d < 4 ? Px : Py);
+    for (int i = 0; i < 9; ++i) P[i] = B[i];
+    if (d & 1)
+        for (int j = 0; j < 3; ++j) P[6 + j] = -P[6 + j];
+}
+
+// direction of a (target - source) centre offset in child units, or -1 if adjacent
+static int classify(const int D2[3]) {   // D2 = 2 * offset (integers)
+    if (D2[2] >= 4) return 0;
+    if (D2[2] <= -4) return 1;
+    if (D2[1] >= 4) return 4;
+    if (D2[1] <= -4) return 5;
+    if (D2[0] >= 4) return 2;
+    if (D2[0] <= -4) return 3;
+    return -1;
+}
+
+static int shift_index(const int v2[3]) {   // v2 = 2 * half-integer offset in [-5, 5]
+    int ix = (v2[0] + 5) / 2, iy = (v2[1] + 5) / 2, iz = (v2[2] + 5) / 2;
+    return ix + 6 * iy + 36 * iz;
+}
+
+static void build_groups(OpTables &t) {
+    t.grp_off.assign(kDirs * (kGroupMax + 1), 0);
+    t.grp_n.assign(kDirs, 0);
+    t.grp_mask.assign(kDirs * kGroupMax, 0);
+    t.slot_list.assign(kDirs * 216, -1);
+    t.child_shift.assign(kDirs * 8, 0);
+    for (int d = 0; d < kDirs; ++d) {
+        int P[9];
+        frame_matrix(d, P);
+        std::map<int, std::vector<int>> by_mask;
+        for (int q = 0; q < 27; ++q) {
+            int dq[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
+            for (int o = 0; o < 8; ++o) {
+                int s2[3];   // 2 * source centre relative to parent centre, child units
+                for (int a = 0; a < 3; ++a) s2[a] = 4 * dq[a] + (((o >> a) & 1) ? 1 : -1);
+                int mask = 0;
+                for (int tt = 0; tt < 8; ++tt) {
+                    int D2[3];
+                    for (int a = 0; a < 3; ++a) D2[a] = (((tt >> a) & 1) ? 1 : -1) - s2[a];
+                    if (classify(D2) == d) mask |= 1 << tt;
+                }
+                if (!mask) continue;
+                int v2[3];   // frame offset parent - source = P (-s)
+                for (int i = 0; i < 3; ++i) v2[i] = -(P[3 * i] * s2[0] + P[3 * i + 1] * s2[1] + P[3 * i + 2] * s2[2]);
+                by_mask[mask].push_back((q * 8 + o) | (shift_index(v2) << 8));
+            }
+        }
+        int g = 0, pos = 0;
+        for (auto &kv : by_mask) {
+            t.grp_mask[d * kGroupMax + g] = kv.first;
+            t.grp_off[d * (kGroupMax + 1) + g] = pos;
+            for (int e : kv.second) t.slot_list[d * 216 + pos++] = e;
+            ++g;
+        }
+        t.grp_off[d * (kGroupMax + 1) + g] = pos;
+        t.grp_n[d] = g;
+        for (int tt = 0; tt < 8; ++tt) {
+            int c2[3];
+            for (int a = 0; a < 3; ++a) c2[a] = ((tt >> a) & 1) ? 1 : -1;
+            int v2[3];
+            for (int i = 0; i < 3; ++i) v2[i] = P[3 * i] * c2[0] + P[3 * i + 1] * c2[1] + P[3 * i + 2] * c2[2];
+            t.child_shift[d * 8 + tt] = shift_index(v2);
+        }
+    }
+}
+
+const ExpQuad &exp_quadrature(int digits) {
+    static ExpQuad q3, q6;
+    if (q3.s == 0) {
+        q3.s = RPY_EXPQ_D3_S;
+        q3.lambda.assign(rpy_expq_d3_lambda, rpy_expq_d3_lambda + q3.s);
+        q3.weight.assign(rpy_expq_d3_weight, rpy_expq_d3_weight + q3.s);
+        q3.m.assign(rpy_expq_d3_m, rpy_expq_d3_m + q3.s);
+        q6.s = RPY_EXPQ_D6_S;
+        q6.lambda.assign(rpy_expq_d6_lambda, rpy_expq_d6_lambda + q6.s);
+        q6.weight.assign(rpy_expq_d6_weight, rpy_expq_d6_weight + q6.s);
+        q6.m.assign(rpy_expq_d6_m, rpy_expq_d6_m + q6.s);
+    }
+    return digits <= 3 ? q3 : q6;
+}
+
+int default_order(int digits) { return digits <= 3 ? 10 : 20; }
+int default_leaf_cap(int digits) { return digits <= 3 ? 40 : 100; }
+
+int build_tables(int p, int digits, OpTables &t) {
+    if (p < 2 || p > kMaxP) return RPY_ERR_INVALID;
+    const ExpQuad &q = exp_quadrature(digits);
+    t.p = p;
+    t.nc = ncoef(p);
+    t.digits = digits;
+    t.s = q.s;
+    t.S = q.half();
+    build_m2m(p, t.m2m_t);
+    build_l2l(p, t.l2l_t);
+    build_rotations(p, t.rot_fwd, t.rot_bwd, t.rot_off);
+    t.m2x_c.assign(size_t(q.s) * t.nc, 0.0);
+    t.x2l_c.assign(size_t(q.s) * t.nc, 0.0);
+    for (int k = 0; k < q.s; ++k)
+        for (int n = 0; n <= p; ++n)
+            for (int m = 0; m <= n; ++m) {
+                double inv = 1.0 / Nnm(n, m);
+                t.m2x_c[size_t(k) * t.nc + tri(n, m)] = std::pow(q.lambda[k], n) * inv;
+                t.x2l_c[size_t(k) * t.nc + tri(n, m)] = std::pow(-q.lambda[k], n) * inv;
+            }
+    t.e_k.clear(); t.e_cos.clear(); t.e_sin.clear(); t.e_wm.clear();
+    t.k_start.assign(q.s + 1, 0);
+    for (int k = 0; k < q.s; ++k) {
+        t.k_start[k] = int(t.e_k.size());
+        for (int j = 0; j < q.m[k] / 2; ++j) {
+            double al = 2.0 * M_PI * j / q.m[k];
+            t.e_k.push_back(k);
+            t.e_cos.push_back(std::cos(al));
+            t.e_sin.push_back(std::sin(al));
+            t.e_wm.push_back(q.weight[k] / q.m[k]);
+        }
+    }
+    t.k_start[q.s] = int(t.e_k.size());
+    t.shift.assign(size_t(216) * t.S * 2, 0.0);
+    for (int off = 0; off < 216; ++off) {
+        double dx = (off % 6) - 2.5, dy = ((off / 6) % 6) - 2.5, dz = (off / 36) - 2.5;
+        for (int e = 0; e < t.S; ++e) {
+            double lam = q.lambda[t.e_k[e]];
+            double mag = std::exp(-lam * dz);
+            double ph = lam * (dx * t.e_cos[e] + dy * t.e_sin[e]);
+            t.shift[(size_t(off) * t.S + e) * 2] = mag * std::cos(ph);
+            t.shift[(size_t(off) * t.S + e) * 2 + 1] = mag * std::sin(ph);
+        }
+    }
+    build_groups(t);
+    t.roots.assign(size_t(2) * t.S * 2, 0.0);
+    for (int k = 0; k < q.s; ++k)
+        for (int r = 0; r < q.m[k]; ++r) {
+            size_t idx = size_t(2) * t.k_start[k] + r;
+            t.roots[2 * idx] = std::cos(2.0 * M_PI * r / q.m[k]);
+            t.roots[2 * idx + 1] = std::sin(2.0 * M_PI * r / q.m[k]);
+        }
+    HarmRec h = harm_rec(p);
+    t.rec_a = h.a;
+    t.rec_b = h.b;
+    t.rec_c = h.c;
+    t.rec_cm.assign(h.c.size(), 1.0);
+    for (size_t m = 1; m < h.c.size(); ++m) t.rec_cm[m] = t.rec_cm[m - 1] * h.c[m];
+    return RPY_OK;
+}
+
+}  // namespace rpy

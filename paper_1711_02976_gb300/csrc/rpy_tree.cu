@@ -1,0 +1,903 @@
+// Device tree construction: bounding cube, Morton keys, LSD radix sort,
+// level-synchronous adaptive octree, colleagues and the U / V / W / X lists
+// of the adaptive FMM.
+//
+// The paper fixes only that the octree is adaptive with a refinement limit
+// ("threshold", Sec. 4.2: the maximum number of beads in a childless box).
+// Here a box splits while it holds more than leaf_cap beads AND its children
+// would still have side >= 2a (so every pair closer than 2a - where the
+// Laplace split of Sec. 2 does not hold - stays in the direct near field)
+// AND it is above the deepest level.
+//
+// Lists (adaptive FMM): for a leaf B, U(B) = all leaves adjacent to B
+// (including B), W(B) = boxes not adjacent to B whose parent is adjacent to
+// B and which descend from a colleague of B; X(B) = {C : B in W(C)};
+// V(B) = children of the parent's colleagues that are not adjacent to B.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "rpy_internal.h"
+
+namespace rpy {
+
+// ---------------------------------------------------------------- errors
+
+static thread_local std::string g_last_err;
+
+void set_last_cuda_error(const char *what, cudaError_t e) {
+    g_last_err = std::string(what) + ": " + cudaGetErrorString(e);
+}
+
+int check_cuda(const char *what, cudaError_t e) {
+    if (e == cudaSuccess) return RPY_OK;
+    set_last_cuda_error(what, e);
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) return RPY_ERR_OOM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return RPY_ERR_NODEVICE;
+    return RPY_ERR_CUDA;
+}
+
+const char *last_cuda_error_text() { return g_last_err.c_str(); }
+
+int dev_alloc(Tree &t, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return check_cuda("cudaMalloc", e);
+    }
+    t.allocs.push_back(*p);
+    t.device_bytes += int64_t(bytes);
+    return RPY_OK;
+}
+
+static void dev_free(Tree &t, void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < t.allocs.size(); ++i)
+        if (t.allocs[i] == p) {
+            t.allocs.erase(t.allocs.begin() + i);
+            break;
+        }
+    cudaFree(p);
+}
+
+void tree_release(Tree &t) {
+    for (void *p : t.allocs) cudaFree(p);
+    t.allocs.clear();
+    t.device_bytes = 0;
+}
+
+// ---------------------------------------------------------------- scan
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *total) {
+    __shared__ int warp_sums[32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        int s = lane < nw ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int before = warp ? warp_sums[warp - 1] : 0;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void k_scan_tile(const int *in, int *out, int n, int *tile_sums) {
+    int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0;
+        s += v[i];
+    }
+    int total;
+    int ex = block_exclusive_scan(s, &total);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = ex;
+        ex += v[i];
+    }
+    if (threadIdx.x == 0 && tile_sums) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_add(int *out, int n, const int *tile_off) {
+    int base = blockIdx.x * kScanTile;
+    int add = tile_off[blockIdx.x];
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x)
+        if (base + i < n) out[base + i] += add;
+}
+
+size_t scan_tmp_bytes(int n) {
+    size_t b = 0;
+    while (n > kScanTile) {
+        n = (n + kScanTile - 1) / kScanTile;
+        b += 2 * size_t(n) * sizeof(int) + 256;
+    }
+    return b + 256;
+}
+
+static void scan_rec(const int *in, int *out, int n, char *tmp, cudaStream_t st) {
+    int tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles <= 1) {
+        k_scan_tile<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+        RPY_LAUNCHED(1);
+        return;
+    }
+    int *sums = reinterpret_cast<int *>(tmp);
+    int *offs = sums + tiles;
+    char *next = tmp + ((2 * size_t(tiles) * sizeof(int) + 255) / 256) * 256;
+    k_scan_tile<<<tiles, kScanThreads, 0, st>>>(in, out, n, sums);
+    RPY_LAUNCHED(1);
+    scan_rec(sums, offs, tiles, next, st);
+    k_scan_add<<<tiles, kScanThreads, 0, st>>>(out, n, offs);
+    RPY_LAUNCHED(1);
+}
+
+// out[i] = sum_{j<i} in[j]; if total_host, *total_host = sum of all (synchronises st).
+int exclusive_scan_i32(const int *in, int *out, int n, int *total_host, void *tmp, size_t tmp_bytes,
+                       cudaStream_t st) {
+    if (n <= 0) {
+        if (total_host) *total_host = 0;
+        return RPY_OK;
+    }
+    if (tmp_bytes < scan_tmp_bytes(n)) return RPY_ERR_INTERNAL;
+    scan_rec(in, out, n, static_cast<char *>(tmp), st);
+    RPY_CHECK(cudaGetLastError());
+    if (total_host) {
+        int a = 0, b = 0;
+        RPY_CHECK(cudaMemcpyAsync(&a, out + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RPY_CHECK(cudaMemcpyAsync(&b, in + n - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RPY_CHECK(cudaStreamSynchronize(st));
+        *total_host = a + b;
+    }
+    return RPY_OK;
+}
+
+// ---------------------------------------------------------------- radix sort
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;   // 4096
+constexpr int kSortWarps = kSortThreads / 32;
+
+__global__ void k_radix_hist(const uint64_t *keys, int n, int shift, int *counts, int ntiles) {
+    __shared__ int h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kSortTile;
+    for (int i = threadIdx.x; i < kSortTile; i += blockDim.x)
+        if (base + i < n) atomicAdd(&h[(keys[base + i] >> shift) & 255], 1);
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) counts[d * ntiles + blockIdx.x] = h[d];
+}
+
+// Stable scatter: ranks inside the tile follow the input order (warp by warp,
+// 32-item rounds in order), tiles are laid out in input order by the scan.
+__global__ void k_radix_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout, int n,
+                                int shift, const int *offs, int ntiles) {
+    __shared__ int wh[kSortWarps][257];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kSortWarps * 257; i += blockDim.x) (&wh[0][0])[i] = 0;
+    __syncthreads();
+    uint64_t k[kSortItems];
+    uint32_t v[kSortItems];
+    int rk[kSortItems], dg[kSortItems];
+    int base = blockIdx.x * kSortTile + warp * (kSortItems * 32);
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int i = base + r * 32 + lane;
+        bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0ull;
+        int d = valid ? int((key >> shift) & 255) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int leader = __ffs(peers) - 1;
+        int pre = __popc(peers & ((1u << lane) - 1u));
+        int b = 0;
+        if (lane == leader) {
+            b = wh[warp][d];
+            wh[warp][d] = b + __popc(peers);
+        }
+        b = __shfl_sync(0xffffffffu, b, leader);
+        __syncwarp();
+        k[r] = key;
+        v[r] = valid ? vin[i] : 0u;
+        dg[r] = d;
+        rk[r] = b + pre;
+    }
+    __syncthreads();
+    __shared__ int wb[kSortWarps][256];
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+        int s = 0;
+        for (int w = 0; w < kSortWarps; ++w) {
+            wb[w][d] = s;
+            s += wh[w][d];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        if (dg[r] < 256) {
+            int pos = offs[dg[r] * ntiles + blockIdx.x] + wb[warp][dg[r]] + rk[r];
+            kout[pos] = k[r];
+            vout[pos] = v[r];
+        }
+    }
+}
+
+// Sort (keys, vals) by bits [0, bits) stably.  Result ends in (k0, v0).
+static int radix_sort(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int n, int bits, int *counts,
+                      void *scan_tmp, size_t scan_bytes, cudaStream_t st) {
+    int ntiles = (n + kSortTile - 1) / kSortTile;
+    int passes = (bits + 7) / 8;
+    for (int pss = 0; pss < passes; ++pss) {
+        int shift = 8 * pss;
+        k_radix_hist<<<ntiles, kSortThreads, 0, st>>>(k0, n, shift, counts, ntiles);
+        RPY_LAUNCHED(1);
+        RPY_TRY(exclusive_scan_i32(counts, counts, 256 * ntiles, nullptr, scan_tmp, scan_bytes, st));
+        k_radix_scatter<<<ntiles, kSortThreads, 0, st>>>(k0, v0, k1, v1, n, shift, counts, ntiles);
+        RPY_LAUNCHED(1);
+        RPY_CHECK(cudaGetLastError());
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+    }
+    if (passes & 1) {   // result is in the second buffer: copy back
+        RPY_CHECK(cudaMemcpyAsync(k1, k0, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
+        RPY_CHECK(cudaMemcpyAsync(v1, v0, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+    }
+    return RPY_OK;
+}
+
+// ---------------------------------------------------------------- cube, keys
+
+constexpr int kChunk = 8192;
+
+// chunk c covers beads [cb[c], ce[c]) of system cs[c]
+__global__ void k_bbox_partial(const double *pos, const int64_t *cb, const int64_t *ce, double *part,
+                               unsigned *status) {
+    __shared__ double red[6][256];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    for (int64_t i = cb[blockIdx.x] + threadIdx.x; i < ce[blockIdx.x]; i += blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            double v = pos[3 * i + a];
+            if (!isfinite(v)) bad = true;
+            lo[a] = fmin(lo[a], v);
+            hi[a] = fmax(hi[a], v);
+        }
+    if (bad) atomicOr(status, DEVERR_NONFINITE);
+    for (int a = 0; a < 3; ++a) {
+        red[a][threadIdx.x] = lo[a];
+        red[3 + a][threadIdx.x] = hi[a];
+    }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int a = 0; a < 3; ++a) {
+                red[a][threadIdx.x] = fmin(red[a][threadIdx.x], red[a][threadIdx.x + s]);
+                red[3 + a][threadIdx.x] = fmax(red[3 + a][threadIdx.x], red[3 + a][threadIdx.x + s]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) part[6 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// cube of system s: centre = (lo+hi)/2, side = max extent (exact IEEE ops, no contraction)
+__global__ void k_bbox_final(const double *part, const int *sys_chunk_off, int nsys, double *cube) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int c = sys_chunk_off[s]; c < sys_chunk_off[s + 1]; ++c)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], part[6 * c + a]);
+            hi[a] = fmax(hi[a], part[6 * c + 3 + a]);
+        }
+    double side = 0.0;
+    for (int a = 0; a < 3; ++a) side = fmax(side, __dsub_rn(hi[a], lo[a]));
+    for (int a = 0; a < 3; ++a) cube[4 * s + a] = __dmul_rn(0.5, __dadd_rn(lo[a], hi[a]));
+    cube[4 * s + 3] = side;
+}
+
+__device__ __forceinline__ int sys_of(const int64_t *off, int nsys, int64_t i) {
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+// q = min(2^21-1, floor((x - origin)/side * 2^21)), origin = centre - side/2,
+// every step a single correctly rounded operation (no FMA contraction).
+__global__ void k_morton(const double *pos, int64_t n, const int64_t *off, int nsys, const double *cube,
+                         uint64_t *keys, uint64_t *keys_copy, uint32_t *idx, uint64_t *sysk) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = sys_of(off, nsys, i);
+    double side = cube[4 * s + 3];
+    uint64_t q[3];
+    for (int a = 0; a < 3; ++a) {
+        if (side == 0.0) { q[a] = 0; continue; }
+        double origin = __dsub_rn(cube[4 * s + a], __dmul_rn(0.5, side));
+        double t = __ddiv_rn(__dsub_rn(pos[3 * i + a], origin), side);
+        t = __dmul_rn(t, 2097152.0);
+        double fl = floor(t);
+        fl = fl < 0.0 ? 0.0 : fl;
+        fl = fl > 2097151.0 ? 2097151.0 : fl;
+        q[a] = uint64_t(fl);
+    }
+    uint64_t key = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+    keys[i] = key;
+    keys_copy[i] = key;
+    idx[i] = uint32_t(i);
+    if (sysk) sysk[i] = uint64_t(s);
+}
+
+__global__ void k_gather_sorted(const double *pos, int64_t n, const uint32_t *perm, const uint64_t *keys_caller,
+                                const int64_t *off, int nsys, double *pos_s, uint64_t *keys_s, int *perm_i,
+                                int *bead_sys) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t j = perm[i];
+    pos_s[i] = pos[3 * int64_t(j)];
+    pos_s[n + i] = pos[3 * int64_t(j) + 1];
+    pos_s[2 * n + i] = pos[3 * int64_t(j) + 2];
+    keys_s[i] = keys_caller[j];
+    perm_i[i] = int(j);
+    bead_sys[i] = sys_of(off, nsys, int64_t(j));
+}
+
+__global__ void k_sysk_from_perm(const uint32_t *vals, int64_t n, const int64_t *off, int nsys, uint64_t *sysk) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    sysk[i] = uint64_t(sys_of(off, nsys, int64_t(vals[i])));
+}
+
+// ---------------------------------------------------------------- octree
+
+__global__ void k_roots(int nsys, const int64_t *off, const double *cube, int *lvl, int *beg, int *end, int *par,
+                        int *child, int *coll, int *cell, int *bsys, int *leaf, double *ctr, double *side) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    lvl[s] = 0;
+    beg[s] = int(off[s]);
+    end[s] = int(off[s + 1]);
+    par[s] = -1;
+    for (int o = 0; o < 8; ++o) child[8 * s + o] = -1;
+    for (int q = 0; q < 27; ++q) coll[27 * s + q] = -1;
+    coll[27 * s + 13] = s;
+    for (int a = 0; a < 3; ++a) {
+        cell[3 * s + a] = 0;
+        ctr[3 * s + a] = cube[4 * s + a];
+    }
+    side[s] = cube[4 * s + 3];
+    bsys[s] = s;
+    leaf[s] = 1;
+}
+
+__global__ void k_split_count(int b0, int nb, int level, int cap, int max_level, const int *beg, const int *end,
+                              const double *side, const int *bsys, const double *sys_a, const uint64_t *keys,
+                              int *bounds, int *nchild) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > nb) return;
+    if (i == nb) { nchild[i] = 0; return; }
+    int b = b0 + i;
+    int lo = beg[b], hi = end[b];
+    double a = sys_a[bsys[b]];
+    bool split = (hi - lo) > cap && 0.5 * side[b] >= 2.0 * a && level < max_level;
+    int cnt = 0;
+    if (split) {
+        int sh = 60 - 3 * level;
+        bounds[9 * i] = lo;
+        for (int o = 1; o < 8; ++o) {
+            int l = lo, h = hi;   // first index with digit >= o
+            while (l < h) {
+                int mid = (l + h) >> 1;
+                if (int((keys[mid] >> sh) & 7ull) < o) l = mid + 1; else h = mid;
+            }
+            bounds[9 * i + o] = l;
+        }
+        bounds[9 * i + 8] = hi;
+        for (int o = 0; o < 8; ++o) cnt += bounds[9 * i + o + 1] > bounds[9 * i + o];
+    }
+    nchild[i] = cnt;
+}
+
+__global__ void k_make_children(int b0, int nb, int level, int first_new, const int *bounds, const int *nchild,
+                                const int *cbase, int *lvl, int *beg, int *end, int *par, int *child, int *coll,
+                                int *cell, int *bsys, int *leaf, double *ctr, double *side) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    int b = b0 + i;
+    if (nchild[i] == 0) return;
+    leaf[b] = 0;
+    int c = first_new + cbase[i];
+    double hs = 0.5 * side[b];
+    for (int o = 0; o < 8; ++o) {
+        int lo = bounds[9 * i + o], hi = bounds[9 * i + o + 1];
+        if (hi <= lo) { child[8 * b + o] = -1; continue; }
+        child[8 * b + o] = c;
+        lvl[c] = level + 1;
+        beg[c] = lo;
+        end[c] = hi;
+        par[c] = b;
+        for (int k = 0; k < 8; ++k) child[8 * c + k] = -1;
+        for (int q = 0; q < 27; ++q) coll[27 * c + q] = -1;
+        for (int a = 0; a < 3; ++a) {
+            int bit = (o >> a) & 1;
+            cell[3 * c + a] = 2 * cell[3 * b + a] + bit;
+            ctr[3 * c + a] = ctr[3 * b + a] + (bit ? 0.5 : -0.5) * hs;
+        }
+        side[c] = hs;
+        bsys[c] = bsys[b];
+        leaf[c] = 1;
+        ++c;
+    }
+}
+
+__device__ __forceinline__ bool boxes_adjacent(int la, const int *ca, int lb, const int *cb) {
+    // closed boxes touch or overlap
+    if (la > lb) {
+        int t = la; la = lb; lb = t;
+        const int *tc = ca; ca = cb; cb = tc;
+    }
+    int sh = lb - la;
+    for (int a = 0; a < 3; ++a) {
+        long lo = long(ca[a]) << sh, hi = long(ca[a] + 1) << sh;
+        if (long(cb[a]) + 1 < lo || long(cb[a]) > hi) return false;
+    }
+    return true;
+}
+
+__global__ void k_colleagues(int b0, int nb, const int *par, const int *child, int *coll, const int *cell) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    int b = b0 + i;
+    int p = par[b];
+    for (int q = 0; q < 27; ++q) {
+        int Q = coll[27 * p + q];
+        if (Q < 0) continue;
+        for (int o = 0; o < 8; ++o) {
+            int c = child[8 * Q + o];
+            if (c < 0) continue;
+            int d[3];
+            bool ok = true;
+            for (int a = 0; a < 3; ++a) {
+                d[a] = cell[3 * c + a] - cell[3 * b + a];
+                if (d[a] < -1 || d[a] > 1) ok = false;
+            }
+            if (ok) coll[27 * b + (d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1)] = c;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- lists
+
+struct ListArgs {
+    const int *lvl, *par, *child, *coll, *cell, *leaf, *leafid, *beg, *end;
+    int *ucnt, *wcnt, *xcnt;            // count pass
+    const int *uoff, *woff, *xoff;      // fill pass
+    int *uidx, *widx, *xidx;
+    unsigned *status;
+};
+
+constexpr int kStack = 96;
+
+template <bool FILL>
+__global__ void k_lists(int nbox, ListArgs A) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    int lb = A.lvl[b];
+    const int *cb = A.cell + 3 * b;
+    // X list: leaf colleagues of ancestors, adjacent to the parent, not to b
+    int nx = 0, xo = FILL ? A.xoff[b] : 0;
+    int P = A.par[b];
+    if (P >= 0) {
+        for (int anc = P; anc >= 0; anc = A.par[anc]) {
+            for (int q = 0; q < 27; ++q) {
+                int c = A.coll[27 * anc + q];
+                if (c < 0 || c == anc || !A.leaf[c]) continue;
+                int lc = A.lvl[c];
+                if (boxes_adjacent(lc, A.cell + 3 * c, lb, cb)) continue;
+                if (!boxes_adjacent(lc, A.cell + 3 * c, A.lvl[P], A.cell + 3 * P)) continue;
+                if (FILL) A.xidx[xo + nx] = c;
+                ++nx;
+            }
+        }
+    }
+    if (!FILL) A.xcnt[b] = nx;
+    if (!A.leaf[b]) return;
+    int li = A.leafid[b];
+    int nu = 0, nw = 0;
+    int uo = FILL ? A.uoff[li] : 0, wo = FILL ? A.woff[li] : 0;
+    // (a) same-level leaf colleagues, b included
+    for (int q = 0; q < 27; ++q) {
+        int c = A.coll[27 * b + q];
+        if (c >= 0 && A.leaf[c]) {
+            if (FILL) A.uidx[uo + nu] = c;
+            ++nu;
+        }
+    }
+    // (b) coarser leaves adjacent to b: leaf colleagues of ancestors
+    for (int anc = P; anc >= 0; anc = A.par[anc]) {
+        for (int q = 0; q < 27; ++q) {
+            int c = A.coll[27 * anc + q];
+            if (c < 0 || c == anc || !A.leaf[c]) continue;
+            if (!boxes_adjacent(A.lvl[c], A.cell + 3 * c, lb, cb)) continue;
+            if (FILL) A.uidx[uo + nu] = c;
+            ++nu;
+        }
+    }
+    // (c) finer: descend into non-leaf colleagues
+    int stack[kStack];
+    int sp = 0;
+    for (int q = 0; q < 27; ++q) {
+        int c = A.coll[27 * b + q];
+        if (c >= 0 && !A.leaf[c]) stack[sp++] = c;
+    }
+    while (sp > 0) {
+        int c = stack[--sp];
+        for (int o = 0; o < 8; ++o) {
+            int ch = A.child[8 * c + o];
+            if (ch < 0) continue;
+            if (boxes_adjacent(A.lvl[ch], A.cell + 3 * ch, lb, cb)) {
+                if (A.leaf[ch]) {
+                    if (FILL) A.uidx[uo + nu] = ch;
+                    ++nu;
+                } else if (sp < kStack) {
+                    stack[sp++] = ch;
+                } else {
+                    atomicOr(A.status, DEVERR_STACK);
+                }
+            } else {
+                if (FILL) A.widx[wo + nw] = ch;
+                ++nw;
+            }
+        }
+    }
+    if (!FILL) {
+        A.ucnt[li] = nu;
+        A.wcnt[li] = nw;
+    }
+}
+
+template <bool FILL>
+__global__ void k_vlists(int b0, int nbox, const int *lvl, const int *par, const int *child, const int *coll,
+                         const int *cell, const int *leaf, int *vcnt, const int *voff, int *vidx) {
+    int b = b0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    int P = par[b];
+    int nv = 0, vo = FILL ? voff[b] : 0;
+    if (P >= 0 && lvl[b] >= 2) {
+        for (int q = 0; q < 27; ++q) {
+            int Q = coll[27 * P + q];
+            if (Q < 0 || leaf[Q]) continue;
+            for (int o = 0; o < 8; ++o) {
+                int c = child[8 * Q + o];
+                if (c < 0) continue;
+                if (boxes_adjacent(lvl[c], cell + 3 * c, lvl[b], cell + 3 * b)) continue;
+                if (FILL) vidx[vo + nv] = c;
+                ++nv;
+            }
+        }
+    }
+    if (!FILL) vcnt[b] = nv;
+}
+
+__global__ void k_flag_compact(int n, const int *flag, const int *pos, int *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) out[pos[i]] = i;
+}
+
+__global__ void k_leafid(int n, const int *leaf, const int *pos, int *leafid) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) leafid[i] = leaf[i] ? pos[i] : -1;
+}
+
+__global__ void k_x2x_flag(int b0, int nbox, const int *leaf, int *flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nbox) flag[i] = (i >= b0 && !leaf[i]) ? 1 : 0;
+}
+
+__global__ void k_leaf_stats(int nleaf, const int *leaves, const int *beg, const int *end, const int *uoff,
+                             const int *uidx, int cap, unsigned long long *pairs, int *maxcnt, int *over) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nleaf) return;
+    int b = leaves[i];
+    int nb = end[b] - beg[b];
+    unsigned long long s = 0;
+    for (int k = uoff[i]; k < uoff[i + 1]; ++k) s += unsigned(end[uidx[k]] - beg[uidx[k]]);
+    atomicAdd(pairs, s * unsigned(nb));
+    atomicMax(maxcnt, nb);
+    if (nb > cap) atomicAdd(over, 1);
+}
+
+// ---------------------------------------------------------------- build driver
+
+static int grow_boxes(Tree &t, int need, cudaStream_t st) {
+    if (need <= t.nbox_cap) return RPY_OK;
+    int cap = std::max(need, t.nbox_cap * 2);
+    cap = std::max(cap, 1024);
+    struct F { void **p; size_t es; int per; };
+    F fields[] = {{(void **)&t.b_level, 4, 1}, {(void **)&t.b_begin, 4, 1}, {(void **)&t.b_end, 4, 1},
+                  {(void **)&t.b_parent, 4, 1}, {(void **)&t.b_child, 4, 8}, {(void **)&t.b_coll, 4, 27},
+                  {(void **)&t.b_cell, 4, 3}, {(void **)&t.b_sys, 4, 1}, {(void **)&t.b_leaf, 4, 1},
+                  {(void **)&t.b_center, 8, 3}, {(void **)&t.b_side, 8, 1}};
+    for (auto &f : fields) {
+        void *np = nullptr;
+        RPY_TRY(dev_alloc(t, &np, f.es * f.per * size_t(cap)));
+        if (*f.p) {
+            RPY_CHECK(cudaMemcpyAsync(np, *f.p, f.es * f.per * size_t(t.nbox), cudaMemcpyDeviceToDevice, st));
+            t.device_bytes -= int64_t(f.es * f.per * size_t(t.nbox_cap));
+            dev_free(t, *f.p);
+        }
+        *f.p = np;
+    }
+    t.nbox_cap = cap;
+    return RPY_OK;
+}
+
+static inline int nblk(int64_t n, int b) { return int((n + b - 1) / b); }
+
+int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
+    const int64_t n = t.n;
+    const int nsys = t.nsys;
+    // -- per-system chunk table for the bounding cubes
+    std::vector<int64_t> cb, ce;
+    std::vector<int> sco(nsys + 1, 0);
+    for (int s = 0; s < nsys; ++s) {
+        sco[s] = int(cb.size());
+        for (int64_t i = t.sys_off_h[s]; i < t.sys_off_h[s + 1]; i += kChunk) {
+            cb.push_back(i);
+            ce.push_back(std::min(i + kChunk, t.sys_off_h[s + 1]));
+        }
+    }
+    sco[nsys] = int(cb.size());
+    int nch = int(cb.size());
+    // scratch for the build (freed at the end)
+    Tree scratch;
+    int64_t *d_cb, *d_ce;
+    int *d_sco;
+    double *d_part;
+    RPY_TRY(dev_alloc(scratch, (void **)&d_cb, sizeof(int64_t) * nch));
+    RPY_TRY(dev_alloc(scratch, (void **)&d_ce, sizeof(int64_t) * nch));
+    RPY_TRY(dev_alloc(scratch, (void **)&d_sco, sizeof(int) * (nsys + 1)));
+    RPY_TRY(dev_alloc(scratch, (void **)&d_part, sizeof(double) * 6 * nch));
+    RPY_CHECK(cudaMemcpyAsync(d_cb, cb.data(), sizeof(int64_t) * nch, cudaMemcpyHostToDevice, st));
+    RPY_CHECK(cudaMemcpyAsync(d_ce, ce.data(), sizeof(int64_t) * nch, cudaMemcpyHostToDevice, st));
+    RPY_CHECK(cudaMemcpyAsync(d_sco, sco.data(), sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice, st));
+    RPY_CHECK(cudaMemsetAsync(t.dev_status, 0, sizeof(unsigned), st));
+    k_bbox_partial<<<nch, 256, 0, st>>>(pos_dev, d_cb, d_ce, d_part, t.dev_status);
+    RPY_LAUNCHED(1);
+    k_bbox_final<<<nblk(nsys, 128), 128, 0, st>>>(d_part, d_sco, nsys, t.sys_cube);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
+    unsigned status = 0;
+    RPY_CHECK(cudaMemcpyAsync(&status, t.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    RPY_CHECK(cudaStreamSynchronize(st));
+    if (status & DEVERR_NONFINITE) {
+        tree_release(scratch);
+        return RPY_ERR_NONFINITE;
+    }
+    // -- keys and sort
+    uint64_t *k0, *k1, *kcaller, *sysk = nullptr;
+    uint32_t *v0, *v1;
+    RPY_TRY(dev_alloc(scratch, (void **)&k0, sizeof(uint64_t) * n));
+    RPY_TRY(dev_alloc(scratch, (void **)&k1, sizeof(uint64_t) * n));
+    RPY_TRY(dev_alloc(scratch, (void **)&kcaller, sizeof(uint64_t) * n));
+    RPY_TRY(dev_alloc(scratch, (void **)&v0, sizeof(uint32_t) * n));
+    RPY_TRY(dev_alloc(scratch, (void **)&v1, sizeof(uint32_t) * n));
+    int ntiles = nblk(n, kSortTile);
+    int *counts;
+    RPY_TRY(dev_alloc(scratch, (void **)&counts, sizeof(int) * 256 * size_t(ntiles)));
+    size_t sbytes = std::max(scan_tmp_bytes(256 * ntiles), scan_tmp_bytes(int(n) + 1));
+    void *stmp;
+    RPY_TRY(dev_alloc(scratch, &stmp, sbytes));
+    if (nsys > 1) RPY_TRY(dev_alloc(scratch, (void **)&sysk, sizeof(uint64_t) * n));
+    k_morton<<<nblk(n, 256), 256, 0, st>>>(pos_dev, n, t.sys_off, nsys, t.sys_cube, k0, kcaller, v0, nullptr);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
+    RPY_TRY(radix_sort(k0, v0, k1, v1, int(n), 63, counts, stmp, sbytes, st));
+    if (nsys > 1) {
+        k_sysk_from_perm<<<nblk(n, 256), 256, 0, st>>>(v0, n, t.sys_off, nsys, sysk);
+        RPY_LAUNCHED(1);
+        int bits = 1;
+        while ((1 << bits) < nsys) ++bits;
+        RPY_TRY(radix_sort(sysk, v0, k1, v1, int(n), bits, counts, stmp, sbytes, st));
+    }
+    k_gather_sorted<<<nblk(n, 256), 256, 0, st>>>(pos_dev, n, v0, kcaller, t.sys_off, nsys, t.pos, t.keys, t.perm,
+                                                  t.bead_sys);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
+    // -- octree, level by level
+    t.nbox = 0;
+    RPY_TRY(grow_boxes(t, std::max(nsys * 64, int(std::min<int64_t>(n, 1 << 20) / 4 + 64)), st));
+    k_roots<<<nblk(nsys, 128), 128, 0, st>>>(nsys, t.sys_off, t.sys_cube, t.b_level, t.b_begin, t.b_end,
+                                             t.b_parent, t.b_child, t.b_coll, t.b_cell, t.b_sys, t.b_leaf,
+                                             t.b_center, t.b_side);
+    RPY_LAUNCHED(1);
+    t.nbox = nsys;
+    t.level_off.assign(1, 0);
+    t.level_off.push_back(nsys);
+    int maxl = t.params.max_level;
+    int *bounds = nullptr, *nchild = nullptr, *cbase = nullptr;
+    int bcap = 0;
+    for (int level = 0;; ++level) {
+        int b0 = t.level_off[level], nb = t.level_off[level + 1] - b0;
+        if (nb == 0) break;
+        if (nb + 1 > bcap) {
+            if (bounds) { dev_free(scratch, bounds); dev_free(scratch, nchild); dev_free(scratch, cbase); }
+            bcap = std::max(2 * (nb + 1), 4096);
+            RPY_TRY(dev_alloc(scratch, (void **)&bounds, sizeof(int) * 9 * size_t(bcap)));
+            RPY_TRY(dev_alloc(scratch, (void **)&nchild, sizeof(int) * size_t(bcap)));
+            RPY_TRY(dev_alloc(scratch, (void **)&cbase, sizeof(int) * size_t(bcap)));
+        }
+        k_split_count<<<nblk(nb + 1, 256), 256, 0, st>>>(b0, nb, level, t.params.leaf_cap, maxl, t.b_begin, t.b_end,
+                                                         t.b_side, t.b_sys, t.sys_a, t.keys, bounds, nchild);
+        RPY_LAUNCHED(1);
+        RPY_CHECK(cudaGetLastError());
+        int total = 0;
+        if (scan_tmp_bytes(nb + 1) > sbytes) return RPY_ERR_INTERNAL;
+        RPY_TRY(exclusive_scan_i32(nchild, cbase, nb + 1, &total, stmp, sbytes, st));
+        if (total == 0) break;
+        RPY_TRY(grow_boxes(t, t.nbox + total, st));
+        k_make_children<<<nblk(nb, 256), 256, 0, st>>>(b0, nb, level, t.nbox, bounds, nchild, cbase, t.b_level,
+                                                       t.b_begin, t.b_end, t.b_parent, t.b_child, t.b_coll,
+                                                       t.b_cell, t.b_sys, t.b_leaf, t.b_center, t.b_side);
+        RPY_LAUNCHED(1);
+        RPY_CHECK(cudaGetLastError());
+        t.nbox += total;
+        t.level_off.push_back(t.nbox);
+    }
+    t.nlevels = int(t.level_off.size()) - 1;
+    // -- colleagues
+    for (int level = 1; level < t.nlevels; ++level) {
+        int b0 = t.level_off[level], nb = t.level_off[level + 1] - b0;
+        k_colleagues<<<nblk(nb, 128), 128, 0, st>>>(b0, nb, t.b_parent, t.b_child, t.b_coll, t.b_cell);
+        RPY_LAUNCHED(1);
+    }
+    RPY_CHECK(cudaGetLastError());
+    // -- leaves
+    int nbx = t.nbox;
+    if (scan_tmp_bytes(nbx + 1) > sbytes) {
+        dev_free(scratch, stmp);
+        sbytes = scan_tmp_bytes(nbx + 1) + 4096;
+        RPY_TRY(dev_alloc(scratch, &stmp, sbytes));
+    }
+    int *pos_tmp;
+    RPY_TRY(dev_alloc(scratch, (void **)&pos_tmp, sizeof(int) * (nbx + 1)));
+    int nleaf = 0;
+    RPY_TRY(exclusive_scan_i32(t.b_leaf, pos_tmp, nbx, &nleaf, stmp, sbytes, st));
+    t.nleaf = nleaf;
+    RPY_TRY(dev_alloc(t, (void **)&t.leaves, sizeof(int) * nleaf));
+    RPY_TRY(dev_alloc(t, (void **)&t.b_leafid, sizeof(int) * nbx));
+    k_flag_compact<<<nblk(nbx, 256), 256, 0, st>>>(nbx, t.b_leaf, pos_tmp, t.leaves);
+    RPY_LAUNCHED(1);
+    k_leafid<<<nblk(nbx, 256), 256, 0, st>>>(nbx, t.b_leaf, pos_tmp, t.b_leafid);
+    RPY_LAUNCHED(1);
+    // -- X2X parents: non-leaf boxes at level >= 1
+    {
+        int *flag;
+        RPY_TRY(dev_alloc(scratch, (void **)&flag, sizeof(int) * (nbx + 1)));
+        int b0 = t.nlevels > 1 ? t.level_off[1] : nbx;
+        k_x2x_flag<<<nblk(nbx, 256), 256, 0, st>>>(b0, nbx, t.b_leaf, flag);
+        RPY_LAUNCHED(1);
+        int np = 0;
+        RPY_TRY(exclusive_scan_i32(flag, pos_tmp, nbx, &np, stmp, sbytes, st));
+        t.n_x2x_par = np;
+        RPY_TRY(dev_alloc(t, (void **)&t.x2x_par, sizeof(int) * std::max(np, 1)));
+        k_flag_compact<<<nblk(nbx, 256), 256, 0, st>>>(nbx, flag, pos_tmp, t.x2x_par);
+        RPY_LAUNCHED(1);
+    }
+    // -- lists
+    ListArgs A{};
+    A.lvl = t.b_level; A.par = t.b_parent; A.child = t.b_child; A.coll = t.b_coll; A.cell = t.b_cell;
+    A.leaf = t.b_leaf; A.leafid = t.b_leafid; A.beg = t.b_begin; A.end = t.b_end; A.status = t.dev_status;
+    int *ucnt, *wcnt, *xcnt;
+    RPY_TRY(dev_alloc(scratch, (void **)&ucnt, sizeof(int) * (nleaf + 1)));
+    RPY_TRY(dev_alloc(scratch, (void **)&wcnt, sizeof(int) * (nleaf + 1)));
+    RPY_TRY(dev_alloc(scratch, (void **)&xcnt, sizeof(int) * (nbx + 1)));
+    RPY_CHECK(cudaMemsetAsync(ucnt, 0, sizeof(int) * (nleaf + 1), st));
+    RPY_CHECK(cudaMemsetAsync(wcnt, 0, sizeof(int) * (nleaf + 1), st));
+    RPY_CHECK(cudaMemsetAsync(xcnt, 0, sizeof(int) * (nbx + 1), st));
+    A.ucnt = ucnt; A.wcnt = wcnt; A.xcnt = xcnt;
+    k_lists<false><<<nblk(nbx, 128), 128, 0, st>>>(nbx, A);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
+    RPY_TRY(dev_alloc(t, (void **)&t.u_off, sizeof(int) * (nleaf + 1)));
+    RPY_TRY(dev_alloc(t, (void **)&t.w_off, sizeof(int) * (nleaf + 1)));
+    RPY_TRY(dev_alloc(t, (void **)&t.x_off, sizeof(int) * (nbx + 1)));
+    int nu = 0, nw = 0, nx = 0;
+    RPY_TRY(exclusive_scan_i32(ucnt, t.u_off, nleaf + 1, &nu, stmp, sbytes, st));
+    RPY_TRY(exclusive_scan_i32(wcnt, t.w_off, nleaf + 1, &nw, stmp, sbytes, st));
+    RPY_TRY(exclusive_scan_i32(xcnt, t.x_off, nbx + 1, &nx, stmp, sbytes, st));
+    t.n_u = nu; t.n_w = nw; t.n_x = nx;
+    RPY_TRY(dev_alloc(t, (void **)&t.u_idx, sizeof(int) * std::max(nu, 1)));
+    RPY_TRY(dev_alloc(t, (void **)&t.w_idx, sizeof(int) * std::max(nw, 1)));
+    RPY_TRY(dev_alloc(t, (void **)&t.x_idx, sizeof(int) * std::max(nx, 1)));
+    A.uoff = t.u_off; A.woff = t.w_off; A.xoff = t.x_off;
+    A.uidx = t.u_idx; A.widx = t.w_idx; A.xidx = t.x_idx;
+    k_lists<true><<<nblk(nbx, 128), 128, 0, st>>>(nbx, A);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
+    // -- statistics
+    unsigned long long *d_pairs;
+    int *d_max;
+    RPY_TRY(dev_alloc(scratch, (void **)&d_pairs, sizeof(unsigned long long)));
+    RPY_TRY(dev_alloc(scratch, (void **)&d_max, 2 * sizeof(int)));
+    RPY_CHECK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st));
+    RPY_CHECK(cudaMemsetAsync(d_max, 0, 2 * sizeof(int), st));
+    k_leaf_stats<<<nblk(nleaf, 256), 256, 0, st>>>(nleaf, t.leaves, t.b_begin, t.b_end, t.u_off, t.u_idx,
+                                                   t.params.leaf_cap, d_pairs, d_max, d_max + 1);
+    RPY_LAUNCHED(1);
+    unsigned long long pairs = 0;
+    int mx[2] = {0, 0};
+    RPY_CHECK(cudaMemcpyAsync(&pairs, d_pairs, sizeof(pairs), cudaMemcpyDeviceToHost, st));
+    RPY_CHECK(cudaMemcpyAsync(mx, d_max, sizeof(mx), cudaMemcpyDeviceToHost, st));
+    RPY_CHECK(cudaMemcpyAsync(&status, t.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    RPY_CHECK(cudaStreamSynchronize(st));
+    t.u_pairs = int64_t(pairs);
+    t.max_leaf_count = mx[0];
+    t.leaves_over_cap = mx[1];
+    tree_release(scratch);
+    if (status & DEVERR_STACK) return RPY_ERR_INTERNAL;
+    return RPY_OK;
+}
+
+int tree_build_vlists(Tree &t, cudaStream_t st) {
+    if (t.v_off) return RPY_OK;
+    int nbx = t.nbox;
+    Tree scratch;
+    int *vcnt;
+    void *stmp;
+    size_t sbytes = scan_tmp_bytes(nbx + 1);
+    RPY_TRY(dev_alloc(scratch, (void **)&vcnt, sizeof(int) * (nbx + 1)));
+    RPY_TRY(dev_alloc(scratch, &stmp, sbytes));
+    RPY_CHECK(cudaMemsetAsync(vcnt, 0, sizeof(int) * (nbx + 1), st));
+    k_vlists<false><<<nblk(nbx, 128), 128, 0, st>>>(0, nbx, t.b_level, t.b_parent, t.b_child, t.b_coll, t.b_cell,
+                                                    t.b_leaf, vcnt, nullptr, nullptr);
+    RPY_LAUNCHED(1);
+    RPY_TRY(dev_alloc(t, (void **)&t.v_off, sizeof(int) * (nbx + 1)));
+    int nv = 0;
+    RPY_TRY(exclusive_scan_i32(vcnt, t.v_off, nbx + 1, &nv, stmp, sbytes, st));
+    t.n_v = nv;
+    RPY_TRY(dev_alloc(t, (void **)&t.v_idx, sizeof(int) * std::max(nv, 1)));
+    k_vlists<true><<<nblk(nbx, 128), 128, 0, st>>>(0, nbx, t.b_level, t.b_parent, t.b_child, t.b_coll, t.b_cell,
+                                                   t.b_leaf, nullptr, t.v_off, t.v_idx);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
+    RPY_CHECK(cudaStreamSynchronize(st));
+    tree_release(scratch);
+    return RPY_OK;
+}
+
+}  // namespace rpy

@@ -1,0 +1,324 @@
+"""GPU parity of the RPY matvec against the CPU oracle, through the C ABI.
+
+Tolerances: the permutation and the Morton keys are bit-exact; the direct
+(single-leaf) path and the near part agree with the oracle to 1e-12 relative
+(FP64 rounding of ~N terms); the FMM meets its digit setting, rel-L2 <= 1e-3
+(3 digits) or <= 1e-6 (6 digits), on the full velocity and on the far part
+alone (velocity minus near part).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1711_02976_gb300 as rp
+import synth
+from gpu_util import box_members, csr, cuda_tensor, leaf_members, matvec
+
+pytestmark = pytest.mark.gpu
+
+
+def _near_oracle(t, pos, f, a, s):
+    """Oracle restricted to the U list of every leaf (self term included)."""
+    lm = leaf_members(t)
+    leaves = rp.rpy_tree_export(t, "leaves")
+    ul = csr(t, "u_off", "u_idx")
+    out = np.zeros_like(f)
+    for li, b in enumerate(leaves):
+        tg = lm[int(b)]
+        src = np.concatenate([lm[int(c)] for c in ul[li]])
+        # put the targets first so that the oracle's index i matches
+        rest = np.setdiff1d(src, tg)
+        idx = np.concatenate([tg, rest])
+        out[tg] = oracle.rpy_direct(pos[idx], f[idx], a, s, targets=np.arange(len(tg)))
+    return out
+
+
+# ---------------------------------------------------------------- tree
+
+def test_permutation_and_keys_bit_exact():
+    sysm = synth.config1()
+    P = cuda_tensor(sysm.pos)
+    t = rp.rpy_tree_build(P, sysm.n, sysm.a, 3, leaf_cap=40)
+    keys, cube = oracle.morton_keys(sysm.pos)
+    perm = oracle.stable_sort(keys)
+    np.testing.assert_array_equal(rp.rpy_tree_export(t, "perm"), perm)
+    np.testing.assert_array_equal(rp.rpy_tree_export(t, "keys"), keys[perm])
+    np.testing.assert_array_equal(rp.rpy_tree_export(t, "cube")[0], cube)
+
+
+def test_forest_permutation_bit_exact():
+    rng = np.random.default_rng(5)
+    sizes = [1, 700, 33, 2000]
+    pos = [rng.random((n, 3)) * (k + 1) for k, n in enumerate(sizes)]
+    pos[2][:] = pos[2][0]                      # a degenerate system (all beads at one point)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    t = rp.rpy_forest_build(cuda_tensor(np.concatenate(pos)), off, [0.01] * 4, 3, leaf_cap=16)
+    got = rp.rpy_tree_export(t, "perm")
+    for k in range(4):
+        keys, _ = oracle.morton_keys(pos[k])
+        np.testing.assert_array_equal(got[off[k]:off[k + 1]], off[k] + oracle.stable_sort(keys))
+
+
+def _clustered(n, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.random((n // 2, 3))
+    b = 0.5 + 0.03 * rng.standard_normal((n - n // 2, 3))
+    return np.concatenate([a, b])
+
+
+def test_tree_invariants_and_list_coverage():
+    """Every bead is in exactly one leaf; U, V, W, X lists cover every ordered
+    pair of beads exactly once (brute force)."""
+    pos = _clustered(1500, 1)
+    t = rp.rpy_tree_build(cuda_tensor(pos), len(pos), 1e-4, 3, leaf_cap=6)
+    n = len(pos)
+    lm = leaf_members(t)
+    allm = np.concatenate(list(lm.values()))
+    assert np.array_equal(np.sort(allm), np.arange(n))
+    st = rp.rpy_tree_stats(t)
+    assert st["max_leaf_count"] <= 6 and st["n_leaves"] == len(lm)
+    bm = box_members(t)
+    leaves = rp.rpy_tree_export(t, "leaves")
+    U, W = csr(t, "u_off", "u_idx"), csr(t, "w_off", "w_idx")
+    V, X = csr(t, "v_off", "v_idx"), csr(t, "x_off", "x_idx")
+    assert sum(len(w) for w in W) > 0 and sum(len(x) for x in X) > 0   # the tree is adaptive
+    cnt = np.zeros((n, n), dtype=np.int32)
+    for li, b in enumerate(leaves):
+        for c in U[li]:
+            cnt[np.ix_(bm[b], bm[c])] += 1
+        for c in W[li]:
+            cnt[np.ix_(bm[b], bm[c])] += 1
+    for b in range(len(bm)):
+        for c in V[b]:
+            cnt[np.ix_(bm[b], bm[c])] += 1
+        for c in X[b]:
+            cnt[np.ix_(bm[b], bm[c])] += 1
+    assert cnt.min() == 1 and cnt.max() == 1
+    # lists are symmetric where the definitions say so
+    level = rp.rpy_tree_export(t, "box_level")
+    for li, b in enumerate(leaves):
+        for c in W[li]:
+            assert b in X[c]
+        assert b in U[li]
+
+
+# ---------------------------------------------------------------- direct parity
+
+def test_single_leaf_equals_direct_sum():
+    rng = np.random.default_rng(2)
+    n = 1000
+    pos = rng.random((n, 3)) * 0.2
+    f = rng.standard_normal((n, 3))
+    a = 0.01                                   # many overlapping pairs
+    pos[7] = pos[8]                            # one coincident pair
+    s = 6 * math.pi * a
+    u, t = matvec(pos, f, a, s, 3, leaf_cap=n)
+    assert rp.rpy_tree_stats(t)["n_leaves"] == 1
+    ref = oracle.rpy_direct(pos, f, a, s)
+    assert np.abs(u - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_near_part_matches_oracle_on_u_lists():
+    sysm = synth.config1()
+    u, t = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, 3, leaf_cap=40, parts=rp.RPY_PART_NEAR)
+    ref = _near_oracle(t, sysm.pos, sysm.f, sysm.a, sysm.s)
+    assert np.abs(u - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- far field operators
+
+@pytest.mark.parametrize("digits,tol", [(3, 1e-3), (6, 1e-6)])
+def test_laplace_far_field_against_direct_sums(digits, tol):
+    """Potential, gradient and Hessian of the four Laplace sets from the FMM
+    (everything outside each leaf's U list) against direct sums.  The digit
+    setting bounds the potential; each derivative multiplies the truncation
+    error of an order-p expansion by roughly (p+1)/(separation), so the
+    gradient is held to 3x and the Hessian to 10x the setting."""
+    import torch
+    pos = _clustered(3000, 3)
+    rng = np.random.default_rng(4)
+    q = rng.standard_normal((len(pos), 4))
+    t = rp.rpy_tree_build(cuda_tensor(pos), len(pos), 1e-5, digits, leaf_cap=12)
+    out = torch.empty((len(pos), 4, 13), dtype=torch.float64, device="cuda")
+    rp.rpy_laplace_far(t, cuda_tensor(q), out)
+    got = out.cpu().numpy()
+    lm = leaf_members(t)
+    leaves = rp.rpy_tree_export(t, "leaves")
+    ul = csr(t, "u_off", "u_idx")
+    ref = np.zeros_like(got)
+    for li, b in enumerate(leaves):
+        tg = lm[int(b)]
+        near = np.concatenate([lm[int(c)] for c in ul[li]])
+        far = np.setdiff1d(np.arange(len(pos)), near)
+        if len(far) == 0:
+            continue
+        phi, g, H = oracle.laplace_direct(pos[far], q[far], pos[tg])
+        ref[tg, :, 0] = phi
+        ref[tg, :, 1:4] = g
+        ref[tg, :, 4:13] = H.reshape(len(tg), 4, 9)
+    for name, sl, f in (("phi", slice(0, 1), 1), ("grad", slice(1, 4), 3), ("hess", slice(4, 13), 10)):
+        e = oracle.rel_l2(got[:, :, sl], ref[:, :, sl])
+        assert e < f * tol, (name, e)
+
+
+# ---------------------------------------------------------------- full matvec parity
+
+def _check(pos, f, a, s, digits, tol, targets=None, **kw):
+    u, t = matvec(pos, f, a, s, digits, **kw)
+    if targets is None:
+        ref = oracle.rpy_direct(pos, f, a, s)
+        uu = u
+    else:
+        ref = oracle.rpy_direct(pos, f, a, s, targets=targets)
+        uu = u[targets]
+    fi = f if targets is None else f[targets]
+    self_t = s / (6 * math.pi * a) * fi
+    e = oracle.rel_l2(uu, ref)
+    e_far = oracle.rel_l2(uu - self_t, ref - self_t)
+    assert e < tol, e
+    assert e_far < 5 * tol, e_far
+    return e, e_far, t
+
+
+@pytest.mark.parametrize("digits,tol", [(3, 1e-3), (6, 1e-6)])
+def test_config1_parity(digits, tol):
+    sysm = synth.config1()
+    _check(sysm.pos, sysm.f, sysm.a, sysm.s, digits, tol, leaf_cap=40)
+
+
+def test_dipole_term_regime():
+    """a comparable to the box size, where the a^2/r^2 (grad L_C) term is large:
+    a wrong sign of the dipole term would fail here."""
+    rng = np.random.default_rng(6)
+    pos = rng.random((512, 3))
+    f = rng.standard_normal((512, 3))
+    a = 0.02
+    e, e_far, t = _check(pos, f, a, 6 * math.pi * a, 6, 1e-6, leaf_cap=8)
+    assert rp.rpy_tree_stats(t)["depth"] >= 2
+
+
+def test_adaptive_sphere_6digit():
+    sysm = synth.sphere_plus_cube(20000, 12, 2e-4)
+    tg = synth.sample_targets(sysm.n, 1000)
+    _check(sysm.pos, sysm.f, sysm.a, sysm.s, 6, 1e-6, targets=tg, leaf_cap=30)
+
+
+def test_bench_configuration_sampled_parity():
+    """The benchmark workload (1M beads, sphere surface + 10% cube, a = 1e-4,
+    6 digits, FP64) on 2,000 sampled targets."""
+    sysm = synth.config2()
+    tg = synth.sample_targets(sysm.n)
+    _check(sysm.pos, sysm.f, sysm.a, sysm.s, 6, 1e-6, targets=tg)
+
+
+def test_fp32_precision_form_3digit():
+    sysm = synth.config1()
+    _check(sysm.pos, sysm.f, sysm.a, sysm.s, 3, 1e-3, leaf_cap=40, precision=rp.RPY_FP32)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_single_bead():
+    u, t = matvec(np.array([[0.2, 0.3, 0.4]]), np.array([[1.0, -2.0, 0.5]]), 0.1, 2.0, 3)
+    np.testing.assert_allclose(u, 2.0 / (6 * math.pi * 0.1) * np.array([[1.0, -2.0, 0.5]]), rtol=1e-15)
+
+
+def test_all_beads_coincident():
+    pos = np.tile([[0.5, 0.5, 0.5]], (50, 1))
+    f = np.random.default_rng(0).standard_normal((50, 3))
+    u, t = matvec(pos, f, 0.1, 1.0, 3, leaf_cap=4)
+    ref = oracle.rpy_direct(pos, f, 0.1, 1.0)
+    assert np.abs(u - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_ragged_sizes_and_tiny_leaves():
+    rng = np.random.default_rng(8)
+    for n in (2, 3, 129, 4097):
+        pos = rng.random((n, 3))
+        f = rng.standard_normal((n, 3))
+        a = 0.001
+        u, t = matvec(pos, f, a, 6 * math.pi * a, 3, leaf_cap=3)
+        ref = oracle.rpy_direct(pos, f, a, 6 * math.pi * a)
+        assert oracle.rel_l2(u, ref) < 1e-3, n
+
+
+def test_overlap_rule_stops_refinement():
+    """Beads closer than 2a are never split apart: leaves may exceed the cap."""
+    rng = np.random.default_rng(9)
+    pos = 0.5 + 0.002 * rng.standard_normal((400, 3))
+    f = rng.standard_normal((400, 3))
+    a = 0.01
+    u, t = matvec(pos, f, a, 6 * math.pi * a, 3, leaf_cap=5)
+    st = rp.rpy_tree_stats(t)
+    assert st["leaves_over_cap"] >= 1
+    side = rp.rpy_tree_export(t, "box_side")
+    assert side.min() >= 2 * a or st["n_boxes"] == 1
+    ref = oracle.rpy_direct(pos, f, a, 6 * math.pi * a)
+    assert oracle.rel_l2(u, ref) < 1e-12
+
+
+def test_nonfinite_and_invalid_inputs():
+    import torch
+    pos = np.random.default_rng(0).random((100, 3))
+    pos[17, 1] = np.nan
+    with pytest.raises(rp.RpyError) as e:
+        rp.rpy_tree_build(cuda_tensor(pos), 100, 0.01, 3)
+    assert e.value.status == -6
+    with pytest.raises(rp.RpyError) as e:
+        rp.rpy_tree_build(cuda_tensor(pos), 100, 0.0, 3)
+    assert e.value.status == -1
+    with pytest.raises(rp.RpyError) as e:
+        rp.rpy_tree_build(cuda_tensor(pos), 100, 0.01, 5)
+    assert e.value.status == -2
+
+
+def test_translation_and_linearity():
+    sysm = synth.config1()
+    u0, _ = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, 3)
+    u1, _ = matvec(sysm.pos + np.array([1e3, -1e3, 1e3]), sysm.f, sysm.a, sysm.s, 3)
+    assert oracle.rel_l2(u1, u0) < 1e-6
+    u2, _ = matvec(sysm.pos, 2.0 * sysm.f, sysm.a, 3.0 * sysm.s, 3)
+    assert oracle.rel_l2(u2, 6.0 * u0) < 1e-13
+
+
+def test_forest_results_equal_individual_systems():
+    import torch
+    rng = np.random.default_rng(11)
+    sizes = [3000, 500, 1200]
+    pos = [rng.random((n, 3)) for n in sizes]
+    f = [rng.standard_normal((n, 3)) for n in sizes]
+    a = [0.004, 0.01, 0.002]
+    s = [1.0, 2.0, 0.5]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    F = cuda_tensor(np.concatenate(f))
+    U = torch.empty_like(F)
+    t = rp.rpy_forest_build(cuda_tensor(np.concatenate(pos)), off, a, 3, leaf_cap=20)
+    rp.rpy_forest_matvec(t, F, s, U)
+    got = U.cpu().numpy()
+    for k in range(3):
+        uk, _ = matvec(pos[k], f[k], a[k], s[k], 3, leaf_cap=20)
+        np.testing.assert_array_equal(got[off[k]:off[k + 1]], uk)
+
+
+def test_host_entry_point():
+    sysm = synth.config1()
+    u = np.zeros_like(sysm.f)
+    rp.rpy_matvec_host(np.ascontiguousarray(sysm.pos), sysm.a, np.ascontiguousarray(sysm.f), sysm.s, 3, u)
+    ref = oracle.rpy_direct(sysm.pos, sysm.f, sysm.a, sysm.s)
+    assert oracle.rel_l2(u, ref) < 1e-3
+
+
+def test_update_positions_matches_fresh_build():
+    import torch
+    sysm = synth.config1()
+    P = cuda_tensor(sysm.pos)
+    F = cuda_tensor(sysm.f)
+    t = rp.rpy_tree_build(P, sysm.n, sysm.a, 3)
+    pos2 = sysm.pos + 1e-3 * np.random.default_rng(1).standard_normal(sysm.pos.shape)
+    rp.rpy_tree_update_positions(t, cuda_tensor(pos2))
+    U = torch.empty_like(F)
+    rp.rpy_matvec(t, F, sysm.s, U)
+    u2, _ = matvec(pos2, sysm.f, sysm.a, sysm.s, 3)
+    np.testing.assert_array_equal(U.cpu().numpy(), u2)
