@@ -75,6 +75,12 @@ typedef struct {
     int order_p;      /* expansion order p; 0 = default for the setting */
     int max_level;    /* deepest level allowed, 1..21; 0 = 21 */
     int flags;        /* reserved, must be 0 */
+    int direct_w;     /* W-list boxes with at most this many beads are summed directly
+                         instead of by multipole evaluation: 0 = automatic
+                         (about 1.8 (p+3)(p+4)/2), -1 = never */
+    int direct_x;     /* X-list pairs whose target box holds at most this many beads are
+                         summed directly instead of by source-to-local expansion:
+                         0 = automatic (about 0.6 (p+1)(p+2)/2), -1 = never */
 } rpy_build_params;
 
 /* Statistics of a built tree (host struct filled by rpy_tree_stats). */
@@ -94,6 +100,8 @@ typedef struct {
     int32_t leaves_over_cap;
     int64_t u_pairs;            /* bead pairs summed directly (near field, incl. self) */
     int64_t n_ulist, n_wlist, n_xlist, n_vpairs;
+    int64_t n_dlist;            /* (leaf, source box) pairs summed directly in place of W / X */
+    int64_t d_pairs;            /* bead pairs summed directly in place of W / X */
     int64_t device_bytes;       /* device memory held by the handle */
     double build_ms;            /* host-measured wall time of the last build */
 } rpy_stats;
@@ -211,7 +219,9 @@ enum {
     RPY_FIELD_X_IDX = 16,
     RPY_FIELD_V_OFF = 17,      /* int32[nbox + 1]: V lists (per box), built on request */
     RPY_FIELD_V_IDX = 18,
-    RPY_FIELD_CUBE = 19        /* double[nsys][4]: cube centre x, y, z, side */
+    RPY_FIELD_CUBE = 19,       /* double[nsys][4]: cube centre x, y, z, side */
+    RPY_FIELD_D_OFF = 20,      /* int32[nleaf + 1]: direct substitutes of W / X (per leaf) */
+    RPY_FIELD_D_IDX = 21
 };
 int rpy_tree_export(rpy_tree t, int field, void *host_dst, int64_t capacity, int64_t *bytes_out);
 

@@ -35,6 +35,7 @@ FIELDS = {
     "box_sys": (8, np.int32), "box_side": (9, np.float64), "leaves": (10, np.int32), "u_off": (11, np.int32),
     "u_idx": (12, np.int32), "w_off": (13, np.int32), "w_idx": (14, np.int32), "x_off": (15, np.int32),
     "x_idx": (16, np.int32), "v_off": (17, np.int32), "v_idx": (18, np.int32), "cube": (19, np.float64),
+    "d_off": (20, np.int32), "d_idx": (21, np.int32),
 }
 EXPORTED_SYMBOLS = [
     "rpy_tree_build", "rpy_forest_build", "rpy_tree_update_positions", "rpy_matvec", "rpy_forest_matvec",
@@ -57,7 +58,8 @@ class RpyError(RuntimeError):
 
 class BuildParams(ctypes.Structure):
     _fields_ = [("digits", ctypes.c_int), ("precision", ctypes.c_int), ("leaf_cap", ctypes.c_int),
-                ("order_p", ctypes.c_int), ("max_level", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("order_p", ctypes.c_int), ("max_level", ctypes.c_int), ("flags", ctypes.c_int),
+                ("direct_w", ctypes.c_int), ("direct_x", ctypes.c_int)]
 
 
 class RpyStats(ctypes.Structure):
@@ -67,6 +69,7 @@ class RpyStats(ctypes.Structure):
                 ("digits", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_leaf_count", ctypes.c_int32),
                 ("leaves_over_cap", ctypes.c_int32), ("u_pairs", ctypes.c_int64), ("n_ulist", ctypes.c_int64),
                 ("n_wlist", ctypes.c_int64), ("n_xlist", ctypes.c_int64), ("n_vpairs", ctypes.c_int64),
+                ("n_dlist", ctypes.c_int64), ("d_pairs", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double)]
 
     def as_dict(self):
@@ -209,11 +212,12 @@ def rpy_tree_build(pos, n, a, digits, leaf_cap=0, precision=RPY_FP64, stream=Non
 
 
 def rpy_forest_build(pos, sys_offsets, a, digits, leaf_cap=0, precision=RPY_FP64, order_p=0, max_level=0,
-                     stream=None) -> Tree:
+                     direct_w=0, direct_x=0, stream=None) -> Tree:
     lib = load()
     off = np.ascontiguousarray(sys_offsets, dtype=np.int64)
     av = np.ascontiguousarray(a, dtype=np.float64)
-    prm = BuildParams(int(digits), int(precision), int(leaf_cap), int(order_p), int(max_level), 0)
+    prm = BuildParams(int(digits), int(precision), int(leaf_cap), int(order_p), int(max_level), 0, int(direct_w),
+                      int(direct_x))
     out = ctypes.c_void_p()
     _check(lib.rpy_forest_build(_dev_f64(pos, "pos"), off.ctypes.data, int(av.size), av.ctypes.data,
                                 ctypes.byref(prm), _stream(stream), ctypes.byref(out)), "rpy_forest_build")

@@ -37,14 +37,15 @@ __global__ void k_gather_q4(const double *q, const int *perm, int64_t n, double 
     for (int k = 0; k < 4; ++k) qs[4 * i + k] = q[4 * j + k];
 }
 
-__global__ void k_combine(const int *perm, int64_t n, const double *un, const double *uf, int parts, double *u) {
+__global__ void k_combine(const int *perm, int64_t n, const double *un, const double *uf, const double *ud, int parts,
+                          double *u) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t j = perm[i];
     for (int a = 0; a < 3; ++a) {
         double v = 0.0;
         if (parts & RPY_PART_NEAR) v += un[3 * i + a];
-        if (parts & RPY_PART_FAR) v += uf[3 * i + a];
+        if (parts & RPY_PART_FAR) v += uf[3 * i + a] + ud[3 * i + a];
         u[3 * j + a] = v;
     }
 }
@@ -151,6 +152,7 @@ static void pack_tables(const OpTables &h, std::vector<char> &blob, std::vector<
     putI(h.grp_mask); // 20
     putI(h.slot_list);// 21
     putI(h.child_shift); // 22
+    putT(h.lad);      // 23
 }
 
 template <typename T>
@@ -184,6 +186,7 @@ static DevTables<T> bind_tables(const OpTables &h, char *base, const std::vector
     d.grp_mask = reinterpret_cast<const int *>(base + o[20]);
     d.slot_list = reinterpret_cast<const int *>(base + o[21]);
     d.child_shift = reinterpret_cast<const int *>(base + o[22]);
+    d.lad = reinterpret_cast<const T *>(base + o[23]);
     return d;
 }
 
@@ -273,6 +276,7 @@ int tree_alloc_workspace(Tree &t, cudaStream_t) {
     RPY_TRY(dev_alloc(t, (void **)&t.fs, sizeof(double) * 3 * t.n));
     RPY_TRY(dev_alloc(t, (void **)&t.u_near, sizeof(double) * 3 * t.n));
     RPY_TRY(dev_alloc(t, (void **)&t.u_far, sizeof(double) * 3 * t.n));
+    RPY_TRY(dev_alloc(t, (void **)&t.u_dir, sizeof(double) * 3 * t.n));
     return RPY_OK;
 }
 
@@ -315,7 +319,8 @@ int run_matvec(Tree &t, const double *f_dev, const double *s_host, double *u_dev
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     prof_mark(t, RPY_STAGE_P2P, st);
-    if (parts & RPY_PART_NEAR) RPY_TRY(run_p2p(t, t.fs, t.u_near, sc, st));
+    if (parts & RPY_PART_NEAR) RPY_TRY(run_p2p(t, t.fs, t.u_near, sc, st, false));
+    if (parts & RPY_PART_FAR) RPY_TRY(run_p2p(t, t.fs, t.u_dir, sc, st, true));
     prof_mark(t, RPY_STAGE_P2M, st);
     if (parts & RPY_PART_FAR) {
         if (t.params.precision == RPY_FP32)
@@ -324,7 +329,7 @@ int run_matvec(Tree &t, const double *f_dev, const double *s_host, double *u_dev
             RPY_TRY(run_far_t<double>(t, t.dt64, t.fs, nullptr, t.u_far, nullptr, sc, st));
     }
     prof_mark(t, RPY_STAGE_COMBINE, st);
-    k_combine<<<nb256(t.n), 256, 0, st>>>(t.perm, t.n, t.u_near, t.u_far, parts, u_dev);
+    k_combine<<<nb256(t.n), 256, 0, st>>>(t.perm, t.n, t.u_near, t.u_far, t.u_dir, parts, u_dev);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     prof_mark(t, RPY_NUM_STAGES, st);
@@ -364,6 +369,7 @@ static int check_params(const rpy_build_params &p) {
     if (p.leaf_cap < 0 || p.order_p < 0 || p.max_level < 0 || p.max_level > kMaxLevel || p.flags != 0)
         return RPY_ERR_INVALID;
     if (p.order_p != 0 && (p.order_p < 2 || p.order_p > kMaxP)) return RPY_ERR_INVALID;
+    if (p.direct_w < -1 || p.direct_x < -1) return RPY_ERR_INVALID;
     return RPY_OK;
 }
 
@@ -416,6 +422,8 @@ int rpy_forest_build(const double *pos_dev, const int64_t *sys_offsets, int nsys
     if (t.params.leaf_cap == 0) t.params.leaf_cap = default_leaf_cap(params->digits);
     if (t.params.max_level == 0) t.params.max_level = kMaxLevel;
     t.p = params->order_p ? params->order_p : default_order(params->digits);
+    t.direct_w = params->direct_w < 0 ? 0 : (params->direct_w > 0 ? params->direct_w : int(1.8 * ncoef(t.p + 2)));
+    t.direct_x = params->direct_x < 0 ? 0 : (params->direct_x > 0 ? params->direct_x : int(0.6 * ncoef(t.p)));
     t.sys_off_h.assign(sys_offsets, sys_offsets + nsys + 1);
     t.a_h.assign(a_host, a_host + nsys);
     int s = do_build(t, pos_dev, static_cast<cudaStream_t>(stream));
@@ -453,6 +461,9 @@ int rpy_tree_update_positions(rpy_tree h, const double *pos_dev, void *stream) {
     fresh.nsys = t.nsys;
     fresh.params = t.params;
     fresh.p = t.p;
+    fresh.direct_w = t.direct_w;
+    fresh.direct_x = t.direct_x;
+    fresh.prof = t.prof;
     fresh.sys_off_h = t.sys_off_h;
     fresh.a_h = t.a_h;
     tree_release(t);
@@ -571,6 +582,8 @@ int rpy_tree_export(rpy_tree h, int field, void *dst, int64_t capacity, int64_t 
             bytes = field == RPY_FIELD_V_OFF ? 4 * int64_t(t.nbox + 1) : 4 * t.n_v;
             break;
         case RPY_FIELD_CUBE: src = t.sys_cube; bytes = 32 * int64_t(t.nsys); break;
+        case RPY_FIELD_D_OFF: src = t.d_off; bytes = 4 * int64_t(t.nleaf + 1); break;
+        case RPY_FIELD_D_IDX: src = t.d_idx; bytes = 4 * t.n_d; break;
         default: return RPY_ERR_INVALID;
     }
     if (field == RPY_FIELD_BOX_RANGE) bytes = 8 * int64_t(t.nbox);
@@ -615,6 +628,8 @@ int rpy_tree_stats(rpy_tree h, rpy_stats *o) {
     o->n_wlist = t.n_w;
     o->n_xlist = t.n_x;
     o->n_vpairs = t.n_v;
+    o->n_dlist = t.n_d;
+    o->d_pairs = t.d_pairs;
     o->device_bytes = t.device_bytes;
     o->build_ms = t.build_ms;
     return RPY_OK;

@@ -103,16 +103,20 @@ __device__ void eval_fields(T x, T y, T z, int P, const cpx<T> *E, int stride, c
 // computed by the whole CTA.  src: degree ps coefficients.  dst: x, y, z
 // derivatives, each zero-padded to stride.
 template <typename T>
-__device__ void d_local(const cpx<T> *src, int ps, cpx<T> *dx, cpx<T> *dy, cpx<T> *dz, int stride, int P) {
+struct Lad {
+    const T *lz, *lp, *lq, *mz, *mp, *mq;
+};
+
+template <typename T>
+__device__ void d_local(const cpx<T> *src, int ps, cpx<T> *dx, cpx<T> *dy, cpx<T> *dz, int P, const Lad<T> &G) {
     // degree k <= ps-1 from L_{k+1}
     for (int i = threadIdx.x; i < ncoef(P); i += blockDim.x) {
         int k = deg_of(i), m = i - tri(k, 0);
         cpx<T> X = mk<T>(0, 0), Y = X, Z = X;
         if (k <= ps - 1) {
-            Z = T(sqrt(T((k + 1 + m) * (k + 1 - m)))) * src[tri(k + 1, m)];
-            cpx<T> Pv = m >= 1 ? T(sqrt(T((k - m + 1) * (k - m + 2)))) * src[tri(k + 1, m - 1)]
-                               : T(-sqrt(T((k + 1) * (k + 2)))) * conj(src[tri(k + 1, 1)]);
-            cpx<T> Qv = T(-sqrt(T((k + m + 1) * (k + m + 2)))) * src[tri(k + 1, m + 1)];
+            Z = G.lz[i] * src[tri(k + 1, m)];
+            cpx<T> Pv = m >= 1 ? G.lp[i] * src[tri(k + 1, m - 1)] : (-G.lq[i]) * conj(src[tri(k + 1, 1)]);
+            cpx<T> Qv = (-G.lq[i]) * src[tri(k + 1, m + 1)];
             X = mk(T(0.5) * (Pv.x + Qv.x), T(0.5) * (Pv.y + Qv.y));
             Y = mk(T(0.5) * (Pv.y - Qv.y), T(-0.5) * (Pv.x - Qv.x));
         }
@@ -123,17 +127,17 @@ __device__ void d_local(const cpx<T> *src, int ps, cpx<T> *dx, cpx<T> *dy, cpx<T
 }
 
 template <typename T>
-__device__ void d_multipole(const cpx<T> *src, int ps, cpx<T> *dx, cpx<T> *dy, cpx<T> *dz, int stride, int P) {
+__device__ void d_multipole(const cpx<T> *src, int ps, cpx<T> *dx, cpx<T> *dy, cpx<T> *dz, int P, const Lad<T> &G) {
     // degree k <= ps+1 from M_{k-1}
     for (int i = threadIdx.x; i < ncoef(P); i += blockDim.x) {
         int k = deg_of(i), m = i - tri(k, 0);
         cpx<T> X = mk<T>(0, 0), Y = X, Z = X;
         if (k >= 1 && k <= ps + 1) {
-            if (m <= k - 1) Z = T(-sqrt(T((k + m) * (k - m)))) * src[tri(k - 1, m)];
+            if (m <= k - 1) Z = (-G.mz[i]) * src[tri(k - 1, m)];
             cpx<T> Pv = mk<T>(0, 0), Qv = mk<T>(0, 0);
-            if (m >= 1) Pv = T(sqrt(T((k + m) * (k + m - 1)))) * src[tri(k - 1, m - 1)];
-            else if (k >= 2) Pv = T(-sqrt(T(k * (k - 1)))) * conj(src[tri(k - 1, 1)]);
-            if (m + 1 <= k - 1) Qv = T(-sqrt(T((k - m) * (k - m - 1)))) * src[tri(k - 1, m + 1)];
+            if (m >= 1) Pv = G.mp[i] * src[tri(k - 1, m - 1)];
+            else if (k >= 2) Pv = (-G.mp[i]) * conj(src[tri(k - 1, 1)]);
+            if (m + 1 <= k - 1) Qv = (-G.mq[i]) * src[tri(k - 1, m + 1)];
             X = mk(T(0.5) * (Pv.x + Qv.x), T(0.5) * (Pv.y + Qv.y));
             Y = mk(T(0.5) * (Pv.y - Qv.y), T(-0.5) * (Pv.x - Qv.x));
         }
@@ -165,9 +169,23 @@ __device__ Rec<T> load_rec(const DevTables<T> &D, T *sm) {
     return r;
 }
 
+// ladder tables follow the recurrence tables in shared memory
+template <typename T>
+__device__ Lad<T> load_lad(const DevTables<T> &D, T *sm) {
+    int nl = ncoef(D.p + 2);
+    for (int i = threadIdx.x; i < 6 * nl; i += blockDim.x) sm[i] = D.lad[i];
+    Lad<T> g{sm, sm + nl, sm + 2 * nl, sm + 3 * nl, sm + 4 * nl, sm + 5 * nl};
+    return g;
+}
+
 template <typename T>
 __host__ __device__ inline int rec_floats(int p) {
     return 2 * ncoef(p + 2) + 2 * (p + 3);
+}
+
+template <typename T>
+__host__ __device__ inline int tab_floats(int p) {   // recurrences + ladders, rounded to an even count
+    return ((rec_floats<T>(p) + 6 * ncoef(p + 2)) + 1) & ~1;
 }
 
 
@@ -364,13 +382,16 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
         for (int e = threadIdx.x; e < kSets * S; e += blockDim.x) {
             int st = e / S, j = e - st * S;
             int k = D.e_k[j];
-            cpx<T> ph = mk(D.e_cos[j], D.e_sin[j]);
+            int j0 = D.k_start[k], jl = j - j0, Mk = 2 * (D.k_start[k + 1] - j0);
+            const cpx<T> *rt = D.roots + 2 * j0;
             const cpx<T> *ae = AE + (st * s + k) * P1;
             const cpx<T> *ao = AO + (st * s + k) * P1;
             T rp = ae[0].x + ao[0].x, rm = ae[0].x - ao[0].x, ip = 0, im = 0;
-            cpx<T> z = mk<T>(1, 0);
+            int idx = 0;
             for (int m = 1; m <= p; ++m) {
-                z = z * ph;
+                idx += jl;
+                if (idx >= Mk) idx -= Mk;
+                cpx<T> z = rt[idx];                      // e^{i m a_j}
                 T se = ae[m].x * z.x - ae[m].y * z.y;   // Re(AE e^{i m a})
                 T so = ao[m].x * z.x - ao[m].y * z.y;
                 T vp = 2 * (se + so), vm = 2 * (se - so);
@@ -445,45 +466,58 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = b0 + blockIdx.x;
     const int p = D.p, nc = ncoef(p), s = D.s, S = D.S, P1 = p + 1;
-    cpx<T> *I = reinterpret_cast<cpx<T> *>(smem_raw);
-    cpx<T> *Bk = I + kSets * S;
-    cpx<T> *Lf = Bk + kSets * s * P1;
+    cpx<T> *I = reinterpret_cast<cpx<T> *>(smem_raw);   // [2][4][S]: + and - direction of the frame
+    cpx<T> *Bp = I + 2 * kSets * S;                      // [4][s][P1]
+    cpx<T> *Bm = Bp + kSets * s * P1;
+    cpx<T> *Lf = Bm + kSets * s * P1;
     cpx<T> *Lw = Lf + kSets * nc;
     cpx<T> *Lr = Lw + kSets * nc;
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] = mk<T>(0, 0);
     for (int f = 0; f < 3; ++f) {
-        for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lf[i] = mk<T>(0, 0);
-        for (int sg = 0; sg < 2; ++sg) {
-            int d = 2 * f + sg;
-            __syncthreads();
-            const cpx<T> *src = Xi + (size_t(b) * kDirs + d) * kSets * S;
-            for (int i = threadIdx.x; i < kSets * S; i += blockDim.x) I[i] = src[i];
-            __syncthreads();
-            // b_k^m = sum_{j < M_k/2} (I_j + (-1)^m conj I_j) e^{-i m a_j}
-            for (int e = threadIdx.x; e < kSets * s * P1; e += blockDim.x) {
-                int st = e / (s * P1), rem = e - st * s * P1, k = rem / P1, m = rem - k * P1;
-                int j0 = D.k_start[k], j1 = D.k_start[k + 1];
-                int Mk = 2 * (j1 - j0);
-                const cpx<T> *rt = D.roots + 2 * j0;
-                cpx<T> a = mk<T>(0, 0);
-                for (int j = j0; j < j1; ++j) {
-                    cpx<T> w = I[st * S + j];
-                    cpx<T> u = (m & 1) ? mk<T>(0, 2 * w.y) : mk<T>(2 * w.x, 0);   // w + (-1)^m conj w
-                    cpx<T> r = rt[(m * (j - j0)) % Mk];
-                    a += u * conj(r);
-                }
-                Bk[e] = a;
+        __syncthreads();
+        const cpx<T> *src = Xi + (size_t(b) * kDirs + 2 * f) * kSets * S;
+        for (int i = threadIdx.x; i < 2 * kSets * S; i += blockDim.x) I[i] = src[i];
+        __syncthreads();
+        // b_k^m = sum_{j < M_k/2} (I_j + (-1)^m conj I_j) e^{-i m a_j}
+        //       = 2 sum_j Re(I_j) e^{-i m a_j}      (m even)
+        //       = 2i sum_j Im(I_j) e^{-i m a_j}     (m odd; the factor i is applied below)
+        for (int e = threadIdx.x; e < kSets * s * P1; e += blockDim.x) {
+            int st = e / (s * P1), rem = e - st * s * P1, k = rem / P1, m = rem - k * P1;
+            int j0 = D.k_start[k], j1 = D.k_start[k + 1];
+            int Mk = 2 * (j1 - j0);
+            int mm = m % Mk;
+            const cpx<T> *rt = D.roots + 2 * j0;
+            const cpx<T> *Ip = I + st * S, *Im = I + (kSets + st) * S;
+            T bpx = 0, bpy = 0, bmx = 0, bmy = 0;
+            int idx = 0;
+            for (int j = j0; j < j1; ++j) {
+                cpx<T> r = rt[idx];
+                T vp = (m & 1) ? Ip[j].y : Ip[j].x;
+                T vm = (m & 1) ? Im[j].y : Im[j].x;
+                bpx += vp * r.x;
+                bpy -= vp * r.y;
+                bmx += vm * r.x;
+                bmy -= vm * r.y;
+                idx += mm;
+                if (idx >= Mk) idx -= Mk;
             }
-            __syncthreads();
-            for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
-                int st = e / nc, i = e - st * nc;
-                int n = deg_of(i), m = i - tri(n, 0);
-                cpx<T> a = mk<T>(0, 0);
-                for (int k = 0; k < s; ++k) a += D.x2l_c[size_t(k) * nc + i] * Bk[(st * s + k) * P1 + m];
-                a = mul_ipow(a, m);
-                if (sg == 1 && ((n + m) & 1)) a = mk(-a.x, -a.y);
-                Lf[e] += a;
+            Bp[e] = mk(2 * bpx, 2 * bpy);
+            Bm[e] = mk(2 * bmx, 2 * bmy);
+        }
+        __syncthreads();
+        // L_n^m = i^m sum_k (-lambda_k)^n / sqrt((n-m)!(n+m)!) b_k^m, the - direction reflected
+        for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
+            int st = e / nc, i = e - st * nc;
+            int n = deg_of(i), m = i - tri(n, 0);
+            T sg = ((n + m) & 1) ? T(-1) : T(1);
+            cpx<T> a = mk<T>(0, 0);
+            for (int k = 0; k < s; ++k) {
+                T c = D.x2l_c[size_t(k) * nc + i];
+                cpx<T> bp = Bp[(st * s + k) * P1 + m], bm = Bm[(st * s + k) * P1 + m];
+                a.x += c * (bp.x + sg * bm.x);
+                a.y += c * (bp.y + sg * bm.y);
             }
+            Lf[e] = mul_ipow(a, m + (m & 1));
         }
         __syncthreads();
         if (f == 0) {
@@ -493,8 +527,8 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
             __syncthreads();
             for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lr[i];
         }
-        __syncthreads();
     }
+    __syncthreads();
     cpx<T> *dst = L + size_t(b) * kSets * nc;
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) dst[i] += Lw[i];
 }
@@ -506,7 +540,7 @@ constexpr int kNE = 18;
 // IRREG = multipole source (degrees grow by one per derivative), else local.
 template <typename T, bool IRREG>
 __device__ void build_eval_set(const cpx<T> *src, int p, int P, cpx<T> *EV, cpx<T> *tmp, double cbx, double cby,
-                               double cbz) {
+                               double cbz, const Lad<T> &G) {
     const int st = ncoef(P);
     // 0..2 values
     for (int i = threadIdx.x; i < 3 * st; i += blockDim.x) {
@@ -516,8 +550,8 @@ __device__ void build_eval_set(const cpx<T> *src, int p, int P, cpx<T> *EV, cpx<
     // 3..11 gradients of sets 0..2 (index 3 + 3k + a), tmp[0..2] gradient of set 3
     for (int k = 0; k < 4; ++k) {
         cpx<T> *gx = k < 3 ? EV + (3 + 3 * k) * st : tmp;
-        if (IRREG) d_multipole(src + k * ncoef(p), p, gx, gx + st, gx + 2 * st, st, P);
-        else d_local(src + k * ncoef(p), p, gx, gx + st, gx + 2 * st, st, P);
+        if (IRREG) d_multipole(src + k * ncoef(p), p, gx, gx + st, gx + 2 * st, P, G);
+        else d_local(src + k * ncoef(p), p, gx, gx + st, gx + 2 * st, P, G);
     }
     __syncthreads();
     // 12..14: G4'_a = dL4_a - sum_k cb_k dL_k,a ; tmp[3] = L_C = dxL1 + dyL2 + dzL3
@@ -537,8 +571,8 @@ __device__ void build_eval_set(const cpx<T> *src, int p, int P, cpx<T> *EV, cpx<
     }
     __syncthreads();
     int pl = IRREG ? p + 1 : p - 1;
-    if (IRREG) d_multipole(tmp + 3 * st, pl, EV + 15 * st, EV + 16 * st, EV + 17 * st, st, P);
-    else d_local(tmp + 3 * st, pl, EV + 15 * st, EV + 16 * st, EV + 17 * st, st, P);
+    if (IRREG) d_multipole(tmp + 3 * st, pl, EV + 15 * st, EV + 16 * st, EV + 17 * st, P, G);
+    else d_local(tmp + 3 * st, pl, EV + 15 * st, EV + 16 * st, EV + 17 * st, P, G);
     __syncthreads();
 }
 
@@ -553,7 +587,8 @@ __global__ void k_far_eval(const int *leaves, DevTables<T> D, const int *beg, co
     const int p = D.p, nc = ncoef(p), P = p + 2, st = ncoef(P);
     T *smr = reinterpret_cast<T *>(smem_raw);
     Rec<T> R = load_rec(D, smr);
-    cpx<T> *EV = reinterpret_cast<cpx<T> *>(smr + ((rec_floats<T>(p) + 1) & ~1));
+    Lad<T> G = load_lad(D, smr + rec_floats<T>(p));
+    cpx<T> *EV = reinterpret_cast<cpx<T> *>(smr + tab_floats<T>(p));
     cpx<T> *tmp = EV + kNE * st;
     cpx<T> *srcs = tmp + 4 * st;
     int sy = bsys[b];
@@ -577,8 +612,8 @@ __global__ void k_far_eval(const int *leaves, DevTables<T> D, const int *beg, co
             __syncthreads();
             for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) srcs[i] = E[i];
             __syncthreads();
-            if (w < 0) build_eval_set<T, false>(srcs, p, P, EV, tmp, cbx - c0x, cby - c0y, cbz - c0z);
-            else build_eval_set<T, true>(srcs, p, P, EV, tmp, cbx - c0x, cby - c0y, cbz - c0z);
+            if (w < 0) build_eval_set<T, false>(srcs, p, P, EV, tmp, cbx - c0x, cby - c0y, cbz - c0z, G);
+            else build_eval_set<T, true>(srcs, p, P, EV, tmp, cbx - c0x, cby - c0y, cbz - c0z, G);
             double h = side[C];
             double ih = 1.0 / h;
             T acc[kNE];
@@ -601,17 +636,17 @@ __global__ void k_far_eval(const int *leaves, DevTables<T> D, const int *beg, co
 
 // Laplace diagnostic: potential, gradient and Hessian of each set from L2P and M2P.
 template <typename T, bool IRREG>
-__device__ void build_lap_set(const cpx<T> *src, int p, int P, cpx<T> *EV, cpx<T> *tmp) {
+__device__ void build_lap_set(const cpx<T> *src, int p, int P, cpx<T> *EV, cpx<T> *tmp, const Lad<T> &G) {
     const int st = ncoef(P);
     for (int i = threadIdx.x; i < st; i += blockDim.x) EV[i] = i < ncoef(p) ? src[i] : mk<T>(0, 0);
-    if (IRREG) d_multipole(src, p, EV + st, EV + 2 * st, EV + 3 * st, st, P);
-    else d_local(src, p, EV + st, EV + 2 * st, EV + 3 * st, st, P);
+    if (IRREG) d_multipole(src, p, EV + st, EV + 2 * st, EV + 3 * st, P, G);
+    else d_local(src, p, EV + st, EV + 2 * st, EV + 3 * st, P, G);
     __syncthreads();
     int pd = IRREG ? p + 1 : p - 1;
     // Hessian rows: d/dx of (x, y, z) derivatives -> 4..6, d/dy -> 7..9, d/dz -> 10..12
     for (int a = 0; a < 3; ++a) {
-        if (IRREG) d_multipole(EV + (1 + a) * st, pd, tmp, tmp + st, tmp + 2 * st, st, P);
-        else d_local(EV + (1 + a) * st, pd, tmp, tmp + st, tmp + 2 * st, st, P);
+        if (IRREG) d_multipole(EV + (1 + a) * st, pd, tmp, tmp + st, tmp + 2 * st, P, G);
+        else d_local(EV + (1 + a) * st, pd, tmp, tmp + st, tmp + 2 * st, P, G);
         __syncthreads();
         for (int i = threadIdx.x; i < st; i += blockDim.x)
             for (int c = 0; c < 3; ++c) EV[(4 + 3 * a + c) * st + i] = tmp[c * st + i];
@@ -629,7 +664,8 @@ __global__ void k_lap_eval(const int *leaves, DevTables<T> D, const int *beg, co
     const int p = D.p, nc = ncoef(p), P = p + 2, st = ncoef(P);
     T *smr = reinterpret_cast<T *>(smem_raw);
     Rec<T> R = load_rec(D, smr);   // recurrence tables cover degree p + 2
-    cpx<T> *EV = reinterpret_cast<cpx<T> *>(smr + ((rec_floats<T>(p) + 1) & ~1));
+    Lad<T> G = load_lad(D, smr + rec_floats<T>(p));
+    cpx<T> *EV = reinterpret_cast<cpx<T> *>(smr + tab_floats<T>(p));
     cpx<T> *tmp = EV + 13 * st;
     cpx<T> *srcs = tmp + 3 * st;
     double cbx = ctr[3 * b], cby = ctr[3 * b + 1], cbz = ctr[3 * b + 2];
@@ -653,8 +689,8 @@ __global__ void k_lap_eval(const int *leaves, DevTables<T> D, const int *beg, co
                 __syncthreads();
                 for (int i = threadIdx.x; i < nc; i += blockDim.x) srcs[i] = E[k * nc + i];
                 __syncthreads();
-                if (w < 0) build_lap_set<T, false>(srcs, p, P, EV, tmp);
-                else build_lap_set<T, true>(srcs, p, P, EV, tmp);
+                if (w < 0) build_lap_set<T, false>(srcs, p, P, EV, tmp, G);
+                else build_lap_set<T, true>(srcs, p, P, EV, tmp, G);
                 T acc[13];
 #pragma unroll
                 for (int q = 0; q < 13; ++q) acc[q] = 0;
@@ -687,17 +723,17 @@ static size_t smem_m2x(int p, int s) {
 template <typename T>
 static size_t smem_x2l(int p, int s, int S) {
     int nc = ncoef(p);
-    return sizeof(cpx<T>) * (kSets * S + kSets * s * (p + 1) + 3 * kSets * nc);
+    return sizeof(cpx<T>) * (2 * kSets * S + 2 * kSets * s * (p + 1) + 3 * kSets * nc);
 }
 template <typename T>
 static size_t smem_far(int p) {
     int st = ncoef(p + 2);
-    return sizeof(T) * ((rec_floats<T>(p) + 1) & ~1) + sizeof(cpx<T>) * (kNE * st + 4 * st + kSets * ncoef(p)) + 64;
+    return sizeof(T) * tab_floats<T>(p) + sizeof(cpx<T>) * (kNE * st + 4 * st + kSets * ncoef(p)) + 64;
 }
 template <typename T>
 static size_t smem_lap(int p) {
     int st = ncoef(p + 2);
-    return sizeof(T) * ((rec_floats<T>(p) + 1) & ~1) + sizeof(cpx<T>) * (13 * st + 3 * st + ncoef(p)) + 64;
+    return sizeof(T) * tab_floats<T>(p) + sizeof(cpx<T>) * (13 * st + 3 * st + ncoef(p)) + 64;
 }
 
 template <typename K>
@@ -784,7 +820,7 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     if (ufar) {
         size_t sf = smem_far<T>(p);
         RPY_TRY(set_smem(k_far_eval<T>, sf));
-        k_far_eval<T><<<t.nleaf, 128, sf, st>>>(t.leaves, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level,
+        k_far_eval<T><<<t.nleaf, 64, sf, st>>>(t.leaves, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level,
                                                 t.b_sys, t.w_off, t.w_idx, t.pos, t.n, sc, L, M, ufar);
         RPY_LAUNCHED(1);
         RPY_CHECK(cudaGetLastError());
@@ -792,7 +828,7 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     if (lapout) {
         size_t sl = smem_lap<T>(p);
         RPY_TRY(set_smem(k_lap_eval<T>, sl));
-        k_lap_eval<T><<<t.nleaf, 128, sl, st>>>(t.leaves, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level,
+        k_lap_eval<T><<<t.nleaf, 64, sl, st>>>(t.leaves, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level,
                                                 t.w_off, t.w_idx, t.pos, t.n, L, M, lapout);
         RPY_LAUNCHED(1);
         RPY_CHECK(cudaGetLastError());

@@ -113,6 +113,10 @@ struct OpTables {
     std::vector<int> child_shift; // [6][8] shift index parent centre -> child centre
     std::vector<double> roots;    // [2S][2] e^{2 pi i r / M_k}, r < M_k, node k at 2 k_start[k]
     std::vector<double> rec_a, rec_b, rec_c, rec_cm;   // harmonic recurrences to degree p + 2
+    // ladder coefficients of the derivative expansions, index tri(k, m), degree <= p + 2:
+    // local:     lz = sqrt((k+1+m)(k+1-m)), lp = sqrt((k-m+1)(k-m+2)), lq = sqrt((k+m+1)(k+m+2))
+    // multipole: mz = sqrt((k+m)(k-m)),     mp = sqrt((k+m)(k+m-1)),   mq = sqrt((k-m)(k-m-1))
+    std::vector<double> lad;      // [6][ncoef(p+2)] in the order lz lp lq mz mp mq
 };
 constexpr int kGroupMax = 32;
 
@@ -125,6 +129,7 @@ struct DevTables {
     const T *m2m_t, *l2l_t, *rot_fwd, *rot_bwd;
     const int *rot_off;
     const T *rec_a, *rec_b, *rec_c, *rec_cm;
+    const T *lad;
     const cpx<T> *roots;
     const T *m2x_c, *x2l_c;
     const int *e_k, *k_start;
@@ -173,10 +178,14 @@ struct Tree {
     int max_leaf_count = 0, leaves_over_cap = 0;
     // level-2+ boxes with children (X2X parents), and boxes at level >= 2
     int n_x2x_par = 0, *x2x_par = nullptr;
+    // direct (P2P) substitutes for small W and X interactions, per leaf
+    int *d_off = nullptr, *d_idx = nullptr;
+    int64_t n_d = 0, d_pairs = 0;
+    int direct_w = 0, direct_x = 0;    // bead-count thresholds in use (0 = none)
     // expansions and matvec workspace
     void *M = nullptr, *L = nullptr, *Xo = nullptr, *Xi = nullptr;
     double *fs = nullptr;             // sorted forces SoA [3][n]
-    double *u_near = nullptr, *u_far = nullptr;   // sorted [n][3]
+    double *u_near = nullptr, *u_far = nullptr, *u_dir = nullptr;   // sorted [n][3]
     double *lap_q = nullptr;          // [n][4] sorted charges for the Laplace debug path
     double *sys_s = nullptr;          // [nsys] kT/eta of the last matvec
     std::vector<double> sys_s_h;
@@ -223,7 +232,7 @@ struct SysConst {
 template <typename T>
 int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *lapq, double *ufar, double *lapout,
               const SysConst &sc, cudaStream_t st);
-int run_p2p(Tree &t, const double *fs, double *unear, const SysConst &sc, cudaStream_t st);
+int run_p2p(Tree &t, const double *fs, double *out, const SysConst &sc, cudaStream_t st, bool direct_list);
 const char *last_cuda_error_text();
 
 // matvec stages (rpy_fmm.cu / rpy_p2p.cu)

@@ -54,9 +54,10 @@ __device__ __forceinline__ void overlap_pair(double dx, double dy, double dz, do
 __global__ void __launch_bounds__(kP2PThreads) k_p2p64(const int *leaves, const int *beg, const int *end,
                                                         const int *bsys, const int *uoff, const int *uidx,
                                                         const double *pos, const double *fs, int64_t n, SysConst sc,
-                                                        double *unear) {
+                                                        int add_self, double *unear) {
     __shared__ double sx[kP2PThreads], sy[kP2PThreads], sz[kP2PThreads];
     __shared__ double sfx[kP2PThreads], sfy[kP2PThreads], sfz[kP2PThreads];
+    __shared__ double red[3][kP2PThreads];
     int li = blockIdx.x;
     int b = leaves[li];
     int sys = bsys[b];
@@ -64,9 +65,14 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p64(const int *leaves, const 
     double a2x4 = 4.0 * a * a, a2 = a * a;
     double cf = s / (8.0 * kPiD), co = s / (6.0 * kPiD * a);
     int u0 = uoff[li], u1 = uoff[li + 1];
-    for (int i0 = beg[b]; i0 < end[b]; i0 += blockDim.x) {
-        int i = i0 + threadIdx.x;
-        bool act = i < end[b];
+    // R targets per pass (a multiple of the warp size), G groups splitting the sources
+    int nt = end[b] - beg[b];
+    int R = nt >= int(blockDim.x) ? int(blockDim.x) : ((nt + 31) & ~31);
+    int G = int(blockDim.x) / R;
+    int tl = threadIdx.x % R, g = threadIdx.x / R;
+    for (int i0 = beg[b]; i0 < end[b]; i0 += R) {
+        int i = i0 + tl;
+        bool act = i < end[b] && g < G;
         double xi = act ? pos[i] : 0, yi = act ? pos[n + i] : 0, zi = act ? pos[2 * n + i] : 0;
         double acc[3] = {0, 0, 0};
         for (int u = u0; u < u1; ++u) {
@@ -85,7 +91,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p64(const int *leaves, const 
                 }
                 __syncthreads();
                 if (!act) continue;
-                for (int jj = 0; jj < cnt; ++jj) {
+                for (int jj = g; jj < cnt; jj += G) {
                     double dx = xi - sx[jj], dy = yi - sy[jj], dz = zi - sz[jj];
                     double r2 = dx * dx + dy * dy + dz * dz;
                     double fx = sfx[jj], fy = sfy[jj], fz = sfz[jj];
@@ -106,10 +112,16 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p64(const int *leaves, const 
                 }
             }
         }
-        if (act) {
-            unear[3 * size_t(i)] = acc[0] + co * fs[i];
-            unear[3 * size_t(i) + 1] = acc[1] + co * fs[n + i];
-            unear[3 * size_t(i) + 2] = acc[2] + co * fs[2 * n + i];
+        __syncthreads();
+        for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = acc[c];
+        __syncthreads();
+        if (act && g == 0) {
+            for (int gg = 1; gg < G; ++gg)
+                for (int c = 0; c < 3; ++c) acc[c] += red[c][threadIdx.x + gg * R];
+            double cs = add_self ? co : 0.0;
+            unear[3 * size_t(i)] = acc[0] + cs * fs[i];
+            unear[3 * size_t(i) + 1] = acc[1] + cs * fs[n + i];
+            unear[3 * size_t(i) + 2] = acc[2] + cs * fs[2 * n + i];
         }
     }
 }
@@ -124,9 +136,10 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
 __global__ void __launch_bounds__(kP2PThreads) k_p2p32(const int *leaves, const int *beg, const int *end,
                                                         const int *bsys, const double *ctr, const int *uoff,
                                                         const int *uidx, const double *pos, const double *fs,
-                                                        int64_t n, SysConst sc, double *unear) {
+                                                        int64_t n, SysConst sc, int add_self, double *unear) {
     __shared__ float sx[kP2PThreads], sy[kP2PThreads], sz[kP2PThreads];
     __shared__ float sfx[kP2PThreads], sfy[kP2PThreads], sfz[kP2PThreads];
+    __shared__ double red[3][kP2PThreads];
     int li = blockIdx.x;
     int b = leaves[li];
     int sys = bsys[b];
@@ -136,9 +149,13 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p32(const int *leaves, const 
     double co = s / (6.0 * kPiD * a);
     double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
     int u0 = uoff[li], u1 = uoff[li + 1];
-    for (int i0 = beg[b]; i0 < end[b]; i0 += blockDim.x) {
-        int i = i0 + threadIdx.x;
-        bool act = i < end[b];
+    int nt = end[b] - beg[b];
+    int R = nt >= int(blockDim.x) ? int(blockDim.x) : ((nt + 31) & ~31);
+    int G = int(blockDim.x) / R;
+    int tl = threadIdx.x % R, g = threadIdx.x / R;
+    for (int i0 = beg[b]; i0 < end[b]; i0 += R) {
+        int i = i0 + tl;
+        bool act = i < end[b] && g < G;
         float xi = act ? float(pos[i] - cx) : 0.f, yi = act ? float(pos[n + i] - cy) : 0.f,
               zi = act ? float(pos[2 * n + i] - cz) : 0.f;
         float acc[3] = {0, 0, 0}, cmp[3] = {0, 0, 0};
@@ -159,7 +176,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p32(const int *leaves, const 
                 }
                 __syncthreads();
                 if (!act) continue;
-                for (int jj = 0; jj < cnt; ++jj) {
+                for (int jj = g; jj < cnt; jj += G) {
                     float dx = xi - sx[jj], dy = yi - sy[jj], dz = zi - sz[jj];
                     float r2 = dx * dx + dy * dy + dz * dz;
                     float fx = sfx[jj], fy = sfy[jj], fz = sfz[jj];
@@ -183,22 +200,36 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p32(const int *leaves, const 
                 }
             }
         }
-        if (act) {
-            unear[3 * size_t(i)] = (double(acc[0]) - double(cmp[0])) + accd[0] + co * fs[i];
-            unear[3 * size_t(i) + 1] = (double(acc[1]) - double(cmp[1])) + accd[1] + co * fs[n + i];
-            unear[3 * size_t(i) + 2] = (double(acc[2]) - double(cmp[2])) + accd[2] + co * fs[2 * n + i];
+        __syncthreads();
+        for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = (double(acc[c]) - double(cmp[c])) + accd[c];
+        __syncthreads();
+        if (act && g == 0) {
+            double v[3];
+            for (int c = 0; c < 3; ++c) {
+                v[c] = red[c][threadIdx.x];
+                for (int gg = 1; gg < G; ++gg) v[c] += red[c][threadIdx.x + gg * R];
+            }
+            double cs = add_self ? co : 0.0;
+            unear[3 * size_t(i)] = v[0] + cs * fs[i];
+            unear[3 * size_t(i) + 1] = v[1] + cs * fs[n + i];
+            unear[3 * size_t(i) + 2] = v[2] + cs * fs[2 * n + i];
         }
     }
 }
 
-int run_p2p(Tree &t, const double *fs, double *unear, const SysConst &sc, cudaStream_t st) {
+// U lists (near field, self term added) or the direct substitutes of small
+// W / X interactions (no self term).
+int run_p2p(Tree &t, const double *fs, double *out, const SysConst &sc, cudaStream_t st, bool direct_list) {
+    const int *off = direct_list ? t.d_off : t.u_off;
+    const int *idx = direct_list ? t.d_idx : t.u_idx;
+    int add_self = direct_list ? 0 : 1;
     if (t.params.precision == RPY_FP32) {
-        k_p2p32<<<t.nleaf, kP2PThreads, 0, st>>>(t.leaves, t.b_begin, t.b_end, t.b_sys, t.b_center, t.u_off, t.u_idx,
-                                                 t.pos, fs, t.n, sc, unear);
+        k_p2p32<<<t.nleaf, kP2PThreads, 0, st>>>(t.leaves, t.b_begin, t.b_end, t.b_sys, t.b_center, off, idx, t.pos,
+                                                 fs, t.n, sc, add_self, out);
         RPY_LAUNCHED(1);
     } else {
-        k_p2p64<<<t.nleaf, kP2PThreads, 0, st>>>(t.leaves, t.b_begin, t.b_end, t.b_sys, t.u_off, t.u_idx, t.pos, fs,
-                                                 t.n, sc, unear);
+        k_p2p64<<<t.nleaf, kP2PThreads, 0, st>>>(t.leaves, t.b_begin, t.b_end, t.b_sys, off, idx, t.pos, fs, t.n, sc,
+                                                 add_self, out);
         RPY_LAUNCHED(1);
     }
     RPY_CHECK(cudaGetLastError());

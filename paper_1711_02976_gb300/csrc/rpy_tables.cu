@@ -394,6 +394,19 @@ int build_tables(int p, int digits, OpTables &t) {
     t.rec_c = h.c;
     t.rec_cm.assign(h.c.size(), 1.0);
     for (size_t m = 1; m < h.c.size(); ++m) t.rec_cm[m] = t.rec_cm[m - 1] * h.c[m];
+    int nl = ncoef(p + 2);
+    t.lad.assign(size_t(6) * nl, 0.0);
+    auto sq = [](long v) { return v > 0 ? std::sqrt(double(v)) : 0.0; };
+    for (int k = 0; k <= p + 2; ++k)
+        for (int m = 0; m <= k; ++m) {
+            int i = tri(k, m);
+            t.lad[0 * nl + i] = sq(long(k + 1 + m) * (k + 1 - m));
+            t.lad[1 * nl + i] = sq(long(k - m + 1) * (k - m + 2));
+            t.lad[2 * nl + i] = sq(long(k + m + 1) * (k + m + 2));
+            t.lad[3 * nl + i] = sq(long(k + m) * (k - m));
+            t.lad[4 * nl + i] = sq(long(k + m) * (k + m - 1));
+            t.lad[5 * nl + i] = sq(long(k - m) * (k - m - 1));
+        }
     return RPY_OK;
 }
 

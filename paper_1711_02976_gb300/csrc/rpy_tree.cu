@@ -504,13 +504,16 @@ __global__ void k_colleagues(int b0, int nb, const int *par, const int *child, i
 
 struct ListArgs {
     const int *lvl, *par, *child, *coll, *cell, *leaf, *leafid, *beg, *end;
-    int *ucnt, *wcnt, *xcnt;            // count pass
-    const int *uoff, *woff, *xoff;      // fill pass
-    int *uidx, *widx, *xidx;
+    int tw, tx;                          // direct-substitution thresholds (0 = none)
+    int *ucnt, *wcnt, *xcnt, *wdcnt, *xdcnt;            // count pass
+    const int *uoff, *woff, *xoff, *wdoff, *xdoff;      // fill pass
+    int *uidx, *widx, *xidx, *wdidx, *xdidx;
     unsigned *status;
 };
 
 constexpr int kStack = 96;
+
+__device__ __forceinline__ int box_count(const ListArgs &A, int b) { return A.end[b] - A.beg[b]; }
 
 template <bool FILL>
 __global__ void k_lists(int nbox, ListArgs A) {
@@ -518,8 +521,11 @@ __global__ void k_lists(int nbox, ListArgs A) {
     if (b >= nbox) return;
     int lb = A.lvl[b];
     const int *cb = A.cell + 3 * b;
-    // X list: leaf colleagues of ancestors, adjacent to the parent, not to b
-    int nx = 0, xo = FILL ? A.xoff[b] : 0;
+    // X list: leaf colleagues of ancestors, adjacent to the parent, not to b.
+    // Small target boxes take their X sources directly (XD).
+    bool xdirect = A.tx > 0 && box_count(A, b) <= A.tx;
+    int nx = 0, xo = 0;
+    if (FILL) xo = xdirect ? A.xdoff[b] : A.xoff[b];
     int P = A.par[b];
     if (P >= 0) {
         for (int anc = P; anc >= 0; anc = A.par[anc]) {
@@ -529,16 +535,19 @@ __global__ void k_lists(int nbox, ListArgs A) {
                 int lc = A.lvl[c];
                 if (boxes_adjacent(lc, A.cell + 3 * c, lb, cb)) continue;
                 if (!boxes_adjacent(lc, A.cell + 3 * c, A.lvl[P], A.cell + 3 * P)) continue;
-                if (FILL) A.xidx[xo + nx] = c;
+                if (FILL) (xdirect ? A.xdidx : A.xidx)[xo + nx] = c;
                 ++nx;
             }
         }
     }
-    if (!FILL) A.xcnt[b] = nx;
+    if (!FILL) {
+        A.xcnt[b] = xdirect ? 0 : nx;
+        A.xdcnt[b] = xdirect ? nx : 0;
+    }
     if (!A.leaf[b]) return;
     int li = A.leafid[b];
-    int nu = 0, nw = 0;
-    int uo = FILL ? A.uoff[li] : 0, wo = FILL ? A.woff[li] : 0;
+    int nu = 0, nw = 0, nwd = 0;
+    int uo = FILL ? A.uoff[li] : 0, wo = FILL ? A.woff[li] : 0, wdo = FILL ? A.wdoff[li] : 0;
     // (a) same-level leaf colleagues, b included
     for (int q = 0; q < 27; ++q) {
         int c = A.coll[27 * b + q];
@@ -557,7 +566,7 @@ __global__ void k_lists(int nbox, ListArgs A) {
             ++nu;
         }
     }
-    // (c) finer: descend into non-leaf colleagues
+    // (c) finer: descend into non-leaf colleagues; non-adjacent children form W
     int stack[kStack];
     int sp = 0;
     for (int q = 0; q < 27; ++q) {
@@ -578,6 +587,9 @@ __global__ void k_lists(int nbox, ListArgs A) {
                 } else {
                     atomicOr(A.status, DEVERR_STACK);
                 }
+            } else if (A.tw > 0 && box_count(A, ch) <= A.tw) {
+                if (FILL) A.wdidx[wdo + nwd] = ch;
+                ++nwd;
             } else {
                 if (FILL) A.widx[wo + nw] = ch;
                 ++nw;
@@ -587,7 +599,32 @@ __global__ void k_lists(int nbox, ListArgs A) {
     if (!FILL) {
         A.ucnt[li] = nu;
         A.wcnt[li] = nw;
+        A.wdcnt[li] = nwd;
     }
+}
+
+// Direct list of leaf b: its direct W sources, then the direct X sources of b
+// and of every ancestor whose X sources are taken directly (those are exactly
+// the ancestors holding at most tx beads, a chain upward from b).
+template <bool FILL>
+__global__ void k_dlists(int nleaf, const int *leaves, const int *par, const int *beg, const int *end, int tx,
+                         const int *wdoff, const int *wdidx, const int *xdoff, const int *xdidx, int *dcnt,
+                         const int *doff, int *didx) {
+    int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nleaf) return;
+    int b = leaves[li];
+    int nd = 0, o = FILL ? doff[li] : 0;
+    for (int k = wdoff[li]; k < wdoff[li + 1]; ++k) {
+        if (FILL) didx[o + nd] = wdidx[k];
+        ++nd;
+    }
+    if (tx > 0)
+        for (int a = b; a >= 0 && end[a] - beg[a] <= tx; a = par[a])
+            for (int k = xdoff[a]; k < xdoff[a + 1]; ++k) {
+                if (FILL) didx[o + nd] = xdidx[k];
+                ++nd;
+            }
+    if (!FILL) dcnt[li] = nd;
 }
 
 template <bool FILL>
@@ -629,14 +666,17 @@ __global__ void k_x2x_flag(int b0, int nbox, const int *leaf, int *flag) {
 }
 
 __global__ void k_leaf_stats(int nleaf, const int *leaves, const int *beg, const int *end, const int *uoff,
-                             const int *uidx, int cap, unsigned long long *pairs, int *maxcnt, int *over) {
+                             const int *uidx, const int *doff, const int *didx, int cap, unsigned long long *pairs,
+                             int *maxcnt, int *over) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nleaf) return;
     int b = leaves[i];
     int nb = end[b] - beg[b];
-    unsigned long long s = 0;
+    unsigned long long s = 0, sd = 0;
     for (int k = uoff[i]; k < uoff[i + 1]; ++k) s += unsigned(end[uidx[k]] - beg[uidx[k]]);
+    for (int k = doff[i]; k < doff[i + 1]; ++k) sd += unsigned(end[didx[k]] - beg[didx[k]]);
     atomicAdd(pairs, s * unsigned(nb));
+    atomicAdd(pairs + 1, sd * unsigned(nb));
     atomicMax(maxcnt, nb);
     if (nb > cap) atomicAdd(over, 1);
 }
@@ -822,50 +862,74 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     ListArgs A{};
     A.lvl = t.b_level; A.par = t.b_parent; A.child = t.b_child; A.coll = t.b_coll; A.cell = t.b_cell;
     A.leaf = t.b_leaf; A.leafid = t.b_leafid; A.beg = t.b_begin; A.end = t.b_end; A.status = t.dev_status;
-    int *ucnt, *wcnt, *xcnt;
+    A.tw = t.direct_w; A.tx = t.direct_x;
+    int *ucnt, *wcnt, *xcnt, *wdcnt, *xdcnt, *wdoff, *xdoff, *wdidx, *xdidx, *dcnt;
     RPY_TRY(dev_alloc(scratch, (void **)&ucnt, sizeof(int) * (nleaf + 1)));
     RPY_TRY(dev_alloc(scratch, (void **)&wcnt, sizeof(int) * (nleaf + 1)));
+    RPY_TRY(dev_alloc(scratch, (void **)&wdcnt, sizeof(int) * (nleaf + 1)));
+    RPY_TRY(dev_alloc(scratch, (void **)&dcnt, sizeof(int) * (nleaf + 1)));
     RPY_TRY(dev_alloc(scratch, (void **)&xcnt, sizeof(int) * (nbx + 1)));
-    RPY_CHECK(cudaMemsetAsync(ucnt, 0, sizeof(int) * (nleaf + 1), st));
-    RPY_CHECK(cudaMemsetAsync(wcnt, 0, sizeof(int) * (nleaf + 1), st));
-    RPY_CHECK(cudaMemsetAsync(xcnt, 0, sizeof(int) * (nbx + 1), st));
-    A.ucnt = ucnt; A.wcnt = wcnt; A.xcnt = xcnt;
+    RPY_TRY(dev_alloc(scratch, (void **)&xdcnt, sizeof(int) * (nbx + 1)));
+    RPY_TRY(dev_alloc(scratch, (void **)&wdoff, sizeof(int) * (nleaf + 1)));
+    RPY_TRY(dev_alloc(scratch, (void **)&xdoff, sizeof(int) * (nbx + 1)));
+    for (int *z : {ucnt, wcnt, wdcnt, dcnt})
+        RPY_CHECK(cudaMemsetAsync(z, 0, sizeof(int) * (nleaf + 1), st));
+    for (int *z : {xcnt, xdcnt}) RPY_CHECK(cudaMemsetAsync(z, 0, sizeof(int) * (nbx + 1), st));
+    A.ucnt = ucnt; A.wcnt = wcnt; A.xcnt = xcnt; A.wdcnt = wdcnt; A.xdcnt = xdcnt;
     k_lists<false><<<nblk(nbx, 128), 128, 0, st>>>(nbx, A);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     RPY_TRY(dev_alloc(t, (void **)&t.u_off, sizeof(int) * (nleaf + 1)));
     RPY_TRY(dev_alloc(t, (void **)&t.w_off, sizeof(int) * (nleaf + 1)));
     RPY_TRY(dev_alloc(t, (void **)&t.x_off, sizeof(int) * (nbx + 1)));
-    int nu = 0, nw = 0, nx = 0;
+    int nu = 0, nw = 0, nx = 0, nwd = 0, nxd = 0;
     RPY_TRY(exclusive_scan_i32(ucnt, t.u_off, nleaf + 1, &nu, stmp, sbytes, st));
     RPY_TRY(exclusive_scan_i32(wcnt, t.w_off, nleaf + 1, &nw, stmp, sbytes, st));
     RPY_TRY(exclusive_scan_i32(xcnt, t.x_off, nbx + 1, &nx, stmp, sbytes, st));
+    RPY_TRY(exclusive_scan_i32(wdcnt, wdoff, nleaf + 1, &nwd, stmp, sbytes, st));
+    RPY_TRY(exclusive_scan_i32(xdcnt, xdoff, nbx + 1, &nxd, stmp, sbytes, st));
     t.n_u = nu; t.n_w = nw; t.n_x = nx;
     RPY_TRY(dev_alloc(t, (void **)&t.u_idx, sizeof(int) * std::max(nu, 1)));
     RPY_TRY(dev_alloc(t, (void **)&t.w_idx, sizeof(int) * std::max(nw, 1)));
     RPY_TRY(dev_alloc(t, (void **)&t.x_idx, sizeof(int) * std::max(nx, 1)));
-    A.uoff = t.u_off; A.woff = t.w_off; A.xoff = t.x_off;
-    A.uidx = t.u_idx; A.widx = t.w_idx; A.xidx = t.x_idx;
+    RPY_TRY(dev_alloc(scratch, (void **)&wdidx, sizeof(int) * std::max(nwd, 1)));
+    RPY_TRY(dev_alloc(scratch, (void **)&xdidx, sizeof(int) * std::max(nxd, 1)));
+    A.uoff = t.u_off; A.woff = t.w_off; A.xoff = t.x_off; A.wdoff = wdoff; A.xdoff = xdoff;
+    A.uidx = t.u_idx; A.widx = t.w_idx; A.xidx = t.x_idx; A.wdidx = wdidx; A.xdidx = xdidx;
     k_lists<true><<<nblk(nbx, 128), 128, 0, st>>>(nbx, A);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
+    // per-leaf direct lists
+    k_dlists<false><<<nblk(nleaf, 128), 128, 0, st>>>(nleaf, t.leaves, t.b_parent, t.b_begin, t.b_end, t.direct_x,
+                                                      wdoff, wdidx, xdoff, xdidx, dcnt, nullptr, nullptr);
+    RPY_LAUNCHED(1);
+    RPY_TRY(dev_alloc(t, (void **)&t.d_off, sizeof(int) * (nleaf + 1)));
+    int nd = 0;
+    RPY_TRY(exclusive_scan_i32(dcnt, t.d_off, nleaf + 1, &nd, stmp, sbytes, st));
+    t.n_d = nd;
+    RPY_TRY(dev_alloc(t, (void **)&t.d_idx, sizeof(int) * std::max(nd, 1)));
+    k_dlists<true><<<nblk(nleaf, 128), 128, 0, st>>>(nleaf, t.leaves, t.b_parent, t.b_begin, t.b_end, t.direct_x,
+                                                     wdoff, wdidx, xdoff, xdidx, nullptr, t.d_off, t.d_idx);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     // -- statistics
     unsigned long long *d_pairs;
     int *d_max;
-    RPY_TRY(dev_alloc(scratch, (void **)&d_pairs, sizeof(unsigned long long)));
+    RPY_TRY(dev_alloc(scratch, (void **)&d_pairs, 2 * sizeof(unsigned long long)));
     RPY_TRY(dev_alloc(scratch, (void **)&d_max, 2 * sizeof(int)));
-    RPY_CHECK(cudaMemsetAsync(d_pairs, 0, sizeof(unsigned long long), st));
+    RPY_CHECK(cudaMemsetAsync(d_pairs, 0, 2 * sizeof(unsigned long long), st));
     RPY_CHECK(cudaMemsetAsync(d_max, 0, 2 * sizeof(int), st));
-    k_leaf_stats<<<nblk(nleaf, 256), 256, 0, st>>>(nleaf, t.leaves, t.b_begin, t.b_end, t.u_off, t.u_idx,
-                                                   t.params.leaf_cap, d_pairs, d_max, d_max + 1);
+    k_leaf_stats<<<nblk(nleaf, 256), 256, 0, st>>>(nleaf, t.leaves, t.b_begin, t.b_end, t.u_off, t.u_idx, t.d_off,
+                                                   t.d_idx, t.params.leaf_cap, d_pairs, d_max, d_max + 1);
     RPY_LAUNCHED(1);
-    unsigned long long pairs = 0;
+    unsigned long long pairs[2] = {0, 0};
     int mx[2] = {0, 0};
-    RPY_CHECK(cudaMemcpyAsync(&pairs, d_pairs, sizeof(pairs), cudaMemcpyDeviceToHost, st));
+    RPY_CHECK(cudaMemcpyAsync(pairs, d_pairs, sizeof(pairs), cudaMemcpyDeviceToHost, st));
     RPY_CHECK(cudaMemcpyAsync(mx, d_max, sizeof(mx), cudaMemcpyDeviceToHost, st));
     RPY_CHECK(cudaMemcpyAsync(&status, t.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     RPY_CHECK(cudaStreamSynchronize(st));
-    t.u_pairs = int64_t(pairs);
+    t.u_pairs = int64_t(pairs[0]);
+    t.d_pairs = int64_t(pairs[1]);
     t.max_leaf_count = mx[0];
     t.leaves_over_cap = mx[1];
     tree_release(scratch);

@@ -68,11 +68,14 @@ def _clustered(n, seed):
     return np.concatenate([a, b])
 
 
-def test_tree_invariants_and_list_coverage():
-    """Every bead is in exactly one leaf; U, V, W, X lists cover every ordered
-    pair of beads exactly once (brute force)."""
+@pytest.mark.parametrize("direct", [(-1, -1), (0, 0), (20, 30)])
+def test_tree_invariants_and_list_coverage(direct):
+    """Every bead is in exactly one leaf; the U, V, W, X lists and the direct
+    substitutes of small W / X interactions cover every ordered pair of beads
+    exactly once (brute force)."""
     pos = _clustered(1500, 1)
-    t = rp.rpy_tree_build(cuda_tensor(pos), len(pos), 1e-4, 3, leaf_cap=6)
+    t = rp.rpy_forest_build(cuda_tensor(pos), [0, len(pos)], [1e-4], 3, leaf_cap=6, direct_w=direct[0],
+                            direct_x=direct[1])
     n = len(pos)
     lm = leaf_members(t)
     allm = np.concatenate(list(lm.values()))
@@ -83,12 +86,19 @@ def test_tree_invariants_and_list_coverage():
     leaves = rp.rpy_tree_export(t, "leaves")
     U, W = csr(t, "u_off", "u_idx"), csr(t, "w_off", "w_idx")
     V, X = csr(t, "v_off", "v_idx"), csr(t, "x_off", "x_idx")
-    assert sum(len(w) for w in W) > 0 and sum(len(x) for x in X) > 0   # the tree is adaptive
+    Dl = csr(t, "d_off", "d_idx")
+    nw, nx, nd = (sum(len(z) for z in L) for L in (W, X, Dl))
+    if direct[0] < 0:
+        assert nd == 0 and nw > 0 and nx > 0          # the tree is adaptive
+    else:
+        assert nd > 0
     cnt = np.zeros((n, n), dtype=np.int32)
     for li, b in enumerate(leaves):
         for c in U[li]:
             cnt[np.ix_(bm[b], bm[c])] += 1
         for c in W[li]:
+            cnt[np.ix_(bm[b], bm[c])] += 1
+        for c in Dl[li]:
             cnt[np.ix_(bm[b], bm[c])] += 1
     for b in range(len(bm)):
         for c in V[b]:
@@ -97,10 +107,11 @@ def test_tree_invariants_and_list_coverage():
             cnt[np.ix_(bm[b], bm[c])] += 1
     assert cnt.min() == 1 and cnt.max() == 1
     # lists are symmetric where the definitions say so
-    level = rp.rpy_tree_export(t, "box_level")
+    if direct[0] < 0:
+        for li, b in enumerate(leaves):
+            for c in W[li]:
+                assert b in X[c]
     for li, b in enumerate(leaves):
-        for c in W[li]:
-            assert b in X[c]
         assert b in U[li]
 
 
@@ -140,7 +151,9 @@ def test_laplace_far_field_against_direct_sums(digits, tol):
     pos = _clustered(3000, 3)
     rng = np.random.default_rng(4)
     q = rng.standard_normal((len(pos), 4))
-    t = rp.rpy_tree_build(cuda_tensor(pos), len(pos), 1e-5, digits, leaf_cap=12)
+    # pure FMM: every W interaction by multipole evaluation (Theorem 1), every X by P2L
+    t = rp.rpy_forest_build(cuda_tensor(pos), [0, len(pos)], [1e-5], digits, leaf_cap=12, direct_w=-1, direct_x=-1)
+    assert rp.rpy_tree_stats(t)["n_wlist"] > 0
     out = torch.empty((len(pos), 4, 13), dtype=torch.float64, device="cuda")
     rp.rpy_laplace_far(t, cuda_tensor(q), out)
     got = out.cpu().numpy()
@@ -186,6 +199,20 @@ def _check(pos, f, a, s, digits, tol, targets=None, **kw):
 def test_config1_parity(digits, tol):
     sysm = synth.config1()
     _check(sysm.pos, sysm.f, sysm.a, sysm.s, digits, tol, leaf_cap=40)
+
+
+@pytest.mark.parametrize("digits,tol", [(3, 1e-3), (6, 1e-6)])
+def test_direct_substitution_matches_pure_fmm(digits, tol):
+    """Small W / X interactions summed directly give the same velocity as the
+    multipole / local expansions they replace, both within the setting."""
+    sysm = synth.sphere_plus_cube(30000, 21, 1e-4)
+    tg = synth.sample_targets(sysm.n, 600)
+    e0, _, t0 = _check(sysm.pos, sysm.f, sysm.a, sysm.s, digits, tol, targets=tg, leaf_cap=40, direct_w=-1,
+                       direct_x=-1)
+    e1, _, t1 = _check(sysm.pos, sysm.f, sysm.a, sysm.s, digits, tol, targets=tg, leaf_cap=40)
+    s0, s1 = rp.rpy_tree_stats(t0), rp.rpy_tree_stats(t1)
+    assert s0["n_dlist"] == 0 and s0["n_wlist"] > 0
+    assert s1["n_dlist"] > 0 and s1["n_wlist"] < s0["n_wlist"]
 
 
 def test_dipole_term_regime():
