@@ -277,6 +277,25 @@ int rpy_tree_stage_times(rpy_tree t, double *ms_host, int n);
  */
 int rpy_alu_peak(int precision, double *flops_per_s, void *stream);
 
+/*
+ * Bounding cube of n beads without allocating device memory, for callers
+ * that cannot call cudaMalloc (code that runs while their own memory pool is
+ * locked, real-time step loops, allocation-free embeddings).  The paper has
+ * no counterpart: it is the tree builder's first reduction exposed on its own.
+ *   pos_dev   device, n x 3 FP64 positions (read)
+ *   n         1 <= n <= 33,554,432 (beyond it: RPY_ERR_INVALID, message in
+ *             rpy_last_cuda_error())
+ *   cube_dev  device, 4 FP64 written: centre x, y, z and side, the same values
+ *             rpy_tree_build uses (side NaN if a position is not finite)
+ * Scratch is a fixed file-scope device array (about 230 KB) that every GPU
+ * loading the library holds until exit.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress, no allocation); make
+ * the first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (different streams, no ordering) race and
+ * give wrong cubes.  Asynchronous on `stream`; allocates nothing.
+ */
+int rpy_bounding_cube_noalloc(const double *pos_dev, int64_t n, double *cube_dev, void *stream);
+
 /* Number of kernels this library has launched in this process (all devices). */
 int64_t rpy_launch_count(void);
 

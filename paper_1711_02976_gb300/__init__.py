@@ -23,7 +23,7 @@ __all__ = [
     "rpy_matvec_oneshot", "rpy_matvec_host", "rpy_laplace_far", "rpy_tree_export", "rpy_tree_stats",
     "rpy_tree_sync", "rpy_tree_footprint", "rpy_tree_free", "rpy_strerror", "rpy_last_cuda_error",
     "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times", "rpy_launch_count",
-    "rpy_alu_peak", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
+    "rpy_alu_peak", "rpy_bounding_cube_noalloc", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
     "RPY_PART_ALL", "EXPORTED_SYMBOLS",
 ]
 
@@ -42,7 +42,7 @@ EXPORTED_SYMBOLS = [
     "rpy_matvec_parts", "rpy_matvec_oneshot", "rpy_matvec_host", "rpy_laplace_far", "rpy_tree_export",
     "rpy_tree_stats", "rpy_tree_sync", "rpy_tree_footprint", "rpy_tree_free", "rpy_strerror",
     "rpy_last_cuda_error", "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times",
-    "rpy_launch_count", "rpy_alu_peak",
+    "rpy_launch_count", "rpy_alu_peak", "rpy_bounding_cube_noalloc",
 ]
 STAGES = ["gather", "p2p", "p2m", "m2m", "m2x", "x2x", "x2l", "p2l", "l2l", "eval", "combine"]
 
@@ -116,6 +116,7 @@ def load(build_if_missing: bool = True):
             "rpy_tree_stage_times": [vp, vp, i],
             "rpy_launch_count": [],
             "rpy_alu_peak": [i, ctypes.POINTER(d), vp],
+            "rpy_bounding_cube_noalloc": [vp, i64, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -346,3 +347,10 @@ def rpy_alu_peak(precision=RPY_FP64, stream=None) -> float:
     v = ctypes.c_double()
     _check(load().rpy_alu_peak(int(precision), ctypes.byref(v), _stream(stream)), "rpy_alu_peak")
     return v.value
+
+
+def rpy_bounding_cube_noalloc(pos, n, cube, stream=None):
+    """Bounding cube (centre x, y, z, side) of n device positions into the
+    device array cube (4 doubles), with no device allocation in the library."""
+    _check(load().rpy_bounding_cube_noalloc(_dev_f64(pos, "pos"), int(n), _dev_f64(cube, "cube"), _stream(stream)),
+           "rpy_bounding_cube_noalloc")

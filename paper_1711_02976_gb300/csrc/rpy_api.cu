@@ -689,6 +689,12 @@ int rpy_tree_stage_times(rpy_tree h, double *ms, int n) {
 
 int64_t rpy_launch_count(void) { return g_launches.load(); }
 
+int rpy_bounding_cube_noalloc(const double *pos_dev, int64_t n, double *cube_dev, void *stream) {
+    if (!pos_dev || !cube_dev || n < 1) return RPY_ERR_INVALID;
+    RPY_TRY(have_device());
+    return bounding_cube_noalloc(pos_dev, n, cube_dev, static_cast<cudaStream_t>(stream));
+}
+
 int rpy_alu_peak(int precision, double *flops_per_s, void *stream) {
     if (!flops_per_s || (precision != RPY_FP64 && precision != RPY_FP32)) return RPY_ERR_INVALID;
     RPY_TRY(have_device());

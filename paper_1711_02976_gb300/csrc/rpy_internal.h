@@ -29,6 +29,8 @@ struct CudaError {
 };
 
 void set_last_cuda_error(const char *what, cudaError_t e);
+void set_last_error(const char *msg);
+int bounding_cube_noalloc(const double *pos_dev, int64_t n, double *cube_dev, cudaStream_t st);
 int check_cuda(const char *what, cudaError_t e);   // returns RPY_OK or RPY_ERR_CUDA/OOM
 
 #define RPY_CHECK(call)                                                   \

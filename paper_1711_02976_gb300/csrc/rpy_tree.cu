@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "rpy_internal.h"
 
@@ -28,6 +29,8 @@ static thread_local std::string g_last_err;
 void set_last_cuda_error(const char *what, cudaError_t e) {
     g_last_err = std::string(what) + ": " + cudaGetErrorString(e);
 }
+
+void set_last_error(const char *msg) { g_last_err = msg; }
 
 int check_cuda(const char *what, cudaError_t e) {
     if (e == cudaSuccess) return RPY_OK;
@@ -934,6 +937,119 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     t.leaves_over_cap = mx[1];
     tree_release(scratch);
     if (status & DEVERR_STACK) return RPY_ERR_INTERNAL;
+    return RPY_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free bounding cube
+//
+// A variant of the bounding-cube reduction (k_bbox_partial / k_bbox_final)
+// for callers that must not allocate device memory (for example code that
+// runs while a caller-owned memory pool is locked, or inside a real-time
+// step loop that forbids cudaMalloc).  Its per-chunk partials live in a
+// fixed file-scope device array instead of a cudaMalloc'd buffer.
+
+constexpr int kNoAllocMaxChunks = 4096;                                   // chunks of kChunk beads
+constexpr int64_t kNoAllocMaxBeads = int64_t(kNoAllocMaxChunks) * kChunk;  // 33,554,432 beads
+// per chunk: lo xyz, hi xyz, non-finite flag
+static __device__ __align__(256) double g_cube_scratch[kNoAllocMaxChunks * 7];
+
+static std::mutex g_cube_mu;
+static void *g_cube_ptr[256] = {};
+
+__global__ void k_bbox_partial_fixed(const double *pos, int64_t n, double *part) {
+    __shared__ double red[7][256];
+    int64_t c0 = int64_t(blockIdx.x) * kChunk;
+    int64_t c1 = c0 + kChunk < n ? c0 + kChunk : n;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double bad = 0.0;
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            double v = pos[3 * i + a];
+            if (!isfinite(v)) bad = 1.0;
+            lo[a] = fmin(lo[a], v);
+            hi[a] = fmax(hi[a], v);
+        }
+    for (int a = 0; a < 3; ++a) {
+        red[a][threadIdx.x] = lo[a];
+        red[3 + a][threadIdx.x] = hi[a];
+    }
+    red[6][threadIdx.x] = bad;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            for (int a = 0; a < 3; ++a) {
+                red[a][threadIdx.x] = fmin(red[a][threadIdx.x], red[a][threadIdx.x + s]);
+                red[3 + a][threadIdx.x] = fmax(red[3 + a][threadIdx.x], red[3 + a][threadIdx.x + s]);
+            }
+            red[6][threadIdx.x] = fmax(red[6][threadIdx.x], red[6][threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 7) part[7 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// One block: reduce nch partials, then the cube exactly as k_bbox_final.
+__global__ void k_bbox_final_fixed(const double *part, int nch, double *cube) {
+    __shared__ double red[7][256];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double bad = 0.0;
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], part[7 * c + a]);
+            hi[a] = fmax(hi[a], part[7 * c + 3 + a]);
+        }
+        bad = fmax(bad, part[7 * c + 6]);
+    }
+    for (int a = 0; a < 3; ++a) {
+        red[a][threadIdx.x] = lo[a];
+        red[3 + a][threadIdx.x] = hi[a];
+    }
+    red[6][threadIdx.x] = bad;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            for (int a = 0; a < 3; ++a) {
+                red[a][threadIdx.x] = fmin(red[a][threadIdx.x], red[a][threadIdx.x + s]);
+                red[3 + a][threadIdx.x] = fmax(red[3 + a][threadIdx.x], red[3 + a][threadIdx.x + s]);
+            }
+            red[6][threadIdx.x] = fmax(red[6][threadIdx.x], red[6][threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double side = 0.0;
+        for (int a = 0; a < 3; ++a) side = fmax(side, __dsub_rn(red[3 + a][0], red[a][0]));
+        for (int a = 0; a < 3; ++a) cube[a] = __dmul_rn(0.5, __dadd_rn(red[a][0], red[3 + a][0]));
+        cube[3] = red[6][0] != 0.0 ? NAN : side;
+    }
+}
+
+int bounding_cube_noalloc(const double *pos_dev, int64_t n, double *cube_dev, cudaStream_t st) {
+    if (n > kNoAllocMaxBeads) {
+        set_last_error("rpy_bounding_cube_noalloc: n exceeds the fixed scratch limit of 33554432 beads");
+        return RPY_ERR_INVALID;
+    }
+    int dev = 0;
+    RPY_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return RPY_ERR_INVALID;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_cube_mu);
+        if (!g_cube_ptr[dev]) {
+            // host code only knows a stand-in for the array: ask the runtime for
+            // its address on this device (the current one) once
+            void *ptr = nullptr;
+            RPY_CHECK(cudaGetSymbolAddress(&ptr, g_cube_scratch));
+            g_cube_ptr[dev] = ptr;
+        }
+        scratch = g_cube_ptr[dev];
+    }
+    int nch = int((n + kChunk - 1) / kChunk);
+    k_bbox_partial_fixed<<<nch, 256, 0, st>>>(pos_dev, n, static_cast<double *>(scratch));
+    RPY_LAUNCHED(1);
+    k_bbox_final_fixed<<<1, 256, 0, st>>>(static_cast<const double *>(scratch), nch, cube_dev);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
     return RPY_OK;
 }
 
