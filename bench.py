@@ -110,10 +110,14 @@ def make_workload(name):
 
 
 def flops_model(stats, stage):
-    """Algorithmic FP64/FP32 operations of one launch of a stage (FMA = 2),
-    counted from the kernel source; see the design doc for the derivations."""
+    """Algorithmic floating-point operations of one stage (FMA = 2), counted
+    from the kernel source: the direct RPY pair costs 46 in the
+    FP64 kernel (3 sub, r^2 5, Newton reciprocal sqrt 5, scalars 3, R.F 5,
+    t1 3, t2 5, accumulate 12) and 45 in the FP32 kernel (no Newton step;
+    Kahan adds 4 per component)."""
     if stage == "p2p":
-        return stats["u_pairs"] * 46.0
+        per = 46.0 if stats["precision"] == 0 else 45.0
+        return (stats["u_pairs"] + stats["d_pairs"]) * per
     return None
 
 
@@ -199,8 +203,8 @@ def run_ours(args, ws, rank, local):
         "build_ms": round(statistics.median(tb), 4), "matvec_ms": round(statistics.median(tm), 4),
         "matvec_only_mbeads_s": round(ws * n / (statistics.median(tm) * 1e-3) / 1e6, 4),
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-        "tree": {k: stats[k] for k in ("n_boxes", "n_leaves", "depth", "u_pairs", "n_wlist", "n_xlist",
-                                       "max_leaf_count", "leaves_over_cap", "device_bytes")},
+        "tree": {k: stats[k] for k in ("n_boxes", "n_leaves", "depth", "u_pairs", "d_pairs", "n_wlist", "n_xlist",
+                                       "n_dlist", "max_leaf_count", "leaves_over_cap", "device_bytes")},
         "gpu_launches": int(launches), "clocks": clocks,
     }
     return result, sysm, u_dev, stats, stage_ms, tree

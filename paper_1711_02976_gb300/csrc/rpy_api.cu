@@ -273,6 +273,7 @@ int tree_alloc_workspace(Tree &t, cudaStream_t) {
     RPY_TRY(dev_alloc(t, &t.L, es * nb * kSets * h.nc));
     RPY_TRY(dev_alloc(t, &t.Xo, es * nb * kDirs * kSets * h.S));
     RPY_TRY(dev_alloc(t, &t.Xi, es * nb * kDirs * kSets * h.S));
+    RPY_TRY(dev_alloc(t, &t.EVg, es * size_t(t.nleaf) * 18 * h.nc));
     RPY_TRY(dev_alloc(t, (void **)&t.fs, sizeof(double) * 3 * t.n));
     RPY_TRY(dev_alloc(t, (void **)&t.u_near, sizeof(double) * 3 * t.n));
     RPY_TRY(dev_alloc(t, (void **)&t.u_far, sizeof(double) * 3 * t.n));

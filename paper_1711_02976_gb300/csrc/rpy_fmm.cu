@@ -353,11 +353,12 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
     const int p = D.p, nc = ncoef(p), s = D.s, S = D.S, P1 = p + 1;
     cpx<T> *Mw = reinterpret_cast<cpx<T> *>(smem_raw);
     cpx<T> *Mf = Mw + kSets * nc;
-    cpx<T> *AE = Mf + kSets * nc;
-    cpx<T> *AO = AE + kSets * s * P1;
+    cpx<T> *AE = Mf + kSets * nc;       // [s][P1] for the current set
+    cpx<T> *AO = AE + s * P1;
     const cpx<T> *src = M + size_t(b) * kSets * nc;
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Mw[i] = src[i];
     __syncthreads();
+    size_t base = size_t(b) * kDirs * kSets * S;
     for (int f = 0; f < 3; ++f) {
         const cpx<T> *Mu = Mw;
         if (f > 0) {
@@ -365,49 +366,55 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
             __syncthreads();
             Mu = Mf;
         }
-        // A_k^m split by parity of n + m
-        for (int e = threadIdx.x; e < kSets * s * P1; e += blockDim.x) {
-            int st = e / (s * P1), rem = e - st * s * P1, k = rem / P1, m = rem - k * P1;
-            cpx<T> ev = mk<T>(0, 0), od = mk<T>(0, 0);
-            const T *cc = D.m2x_c + size_t(k) * nc;
-            for (int n = m; n <= p; ++n) {
-                int i = tri(n, m);
-                cpx<T> v = cc[i] * Mu[st * nc + i];
-                if ((n + m) & 1) od += v; else ev += v;
-            }
-            AE[e] = ev;
-            AO[e] = od;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < kSets * S; e += blockDim.x) {
-            int st = e / S, j = e - st * S;
-            int k = D.e_k[j];
-            int j0 = D.k_start[k], jl = j - j0, Mk = 2 * (D.k_start[k + 1] - j0);
-            const cpx<T> *rt = D.roots + 2 * j0;
-            const cpx<T> *ae = AE + (st * s + k) * P1;
-            const cpx<T> *ao = AO + (st * s + k) * P1;
-            T rp = ae[0].x + ao[0].x, rm = ae[0].x - ao[0].x, ip = 0, im = 0;
-            int idx = 0;
-            for (int m = 1; m <= p; ++m) {
-                idx += jl;
-                if (idx >= Mk) idx -= Mk;
-                cpx<T> z = rt[idx];                      // e^{i m a_j}
-                T se = ae[m].x * z.x - ae[m].y * z.y;   // Re(AE e^{i m a})
-                T so = ao[m].x * z.x - ao[m].y * z.y;
-                T vp = 2 * (se + so), vm = 2 * (se - so);
-                switch (m & 3) {
-                    case 0: rp += vp; rm += vm; break;
-                    case 1: ip += vp; im += vm; break;
-                    case 2: rp -= vp; rm -= vm; break;
-                    default: ip -= vp; im -= vm; break;
+        for (int st = 0; st < kSets; ++st) {
+            // A_k^m split by parity of n + m (the - direction is the reflection (-1)^{n+m})
+            for (int e = threadIdx.x; e < s * P1; e += blockDim.x) {
+                int k = e / P1, m = e - k * P1;
+                T evx = 0, evy = 0, odx = 0, ody = 0;
+                const T *cc = D.m2x_c + size_t(k) * nc;
+                for (int n = m; n <= p; n += 2) {
+                    int i = tri(n, m);
+                    evx += cc[i] * Mu[st * nc + i].x;
+                    evy += cc[i] * Mu[st * nc + i].y;
                 }
+                for (int n = m + 1; n <= p; n += 2) {
+                    int i = tri(n, m);
+                    odx += cc[i] * Mu[st * nc + i].x;
+                    ody += cc[i] * Mu[st * nc + i].y;
+                }
+                AE[e] = mk(evx, evy);
+                AO[e] = mk(odx, ody);
             }
-            T wm = D.e_wm[j];
-            size_t base = size_t(b) * kDirs * kSets * S;
-            Xo[base + size_t(2 * f) * kSets * S + st * S + j] = mk(wm * rp, wm * ip);
-            Xo[base + size_t(2 * f + 1) * kSets * S + st * S + j] = mk(wm * rm, wm * im);
+            __syncthreads();
+            // W_j = (w_k/M_k) [A^0 + 2 sum_m i^m Re(A^m e^{i m a_j})], A = AE +- AO
+            for (int j = threadIdx.x; j < S; j += blockDim.x) {
+                int k = D.e_k[j];
+                int j0 = D.k_start[k], jl = j - j0, Mk = 2 * (D.k_start[k + 1] - j0);
+                const cpx<T> *rt = D.roots + 2 * j0;
+                const cpx<T> *ae = AE + k * P1;
+                const cpx<T> *ao = AO + k * P1;
+                // even-m terms build the real part, odd-m terms the imaginary part
+                T er = ae[0].x, orr = ao[0].x, ei = 0, oi = 0;
+                int idx = 0;
+                for (int m = 1; m <= p; ++m) {
+                    idx += jl;
+                    if (idx >= Mk) idx -= Mk;
+                    cpx<T> z = rt[idx];
+                    T se = ae[m].x * z.x - ae[m].y * z.y;
+                    T so = ao[m].x * z.x - ao[m].y * z.y;
+                    switch (m & 3) {
+                        case 0: er += 2 * se; orr += 2 * so; break;
+                        case 1: ei += 2 * se; oi += 2 * so; break;
+                        case 2: er -= 2 * se; orr -= 2 * so; break;
+                        default: ei -= 2 * se; oi -= 2 * so; break;
+                    }
+                }
+                T wm = D.e_wm[j];
+                Xo[base + size_t(2 * f) * kSets * S + st * S + j] = mk(wm * (er + orr), wm * (ei + oi));
+                Xo[base + size_t(2 * f + 1) * kSets * S + st * S + j] = mk(wm * (er - orr), wm * (ei - oi));
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -599,14 +606,13 @@ __global__ void k_far_eval(const int *leaves, DevTables<T> D, const int *beg, co
     double hb = side[b];
     int j0 = beg[b], j1 = end[b];
     int nw = woff[li + 1] - woff[li];
-    bool has_local = lvl[b] >= 2;
+    if (nw == 0) return;
     for (int jc = j0; jc < j1; jc += blockDim.x) {
         int j = jc + threadIdx.x;
         bool act = j < j1;
         double x = act ? pos[j] : cbx, y = act ? pos[n + j] : cby, z = act ? pos[2 * n + j] : cbz;
         double u[3] = {0, 0, 0};
-        for (int w = -1; w < nw; ++w) {
-            if (w < 0 && !has_local) continue;
+        for (int w = 0; w < nw; ++w) {
             int C = w < 0 ? b : widx[woff[li] + w];
             const cpx<T> *E = w < 0 ? L + size_t(C) * kSets * nc : M + size_t(C) * kSets * nc;
             __syncthreads();
@@ -630,8 +636,62 @@ __global__ void k_far_eval(const int *leaves, DevTables<T> D, const int *beg, co
             }
         }
         if (act)
-            for (int d = 0; d < 3; ++d) ufar[3 * size_t(j) + d] = u[d];
+            for (int d = 0; d < 3; ++d) ufar[3 * size_t(j) + d] += u[d];
     }
+}
+
+// Per leaf at level >= 2: the 18 derived local expansions of Eq. (2.8),
+// written to global memory for the bead-parallel evaluation.
+template <typename T>
+__global__ void k_eval_prep(const int *leaves, DevTables<T> D, const double *ctr, const int *lvl, const int *bsys,
+                            SysConst sc, const cpx<T> *L, cpx<T> *EVg) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int li = blockIdx.x;
+    int b = leaves[li];
+    if (lvl[b] < 2) return;
+    const int p = D.p, nc = ncoef(p);
+    T *smr = reinterpret_cast<T *>(smem_raw);
+    Lad<T> G = load_lad(D, smr);
+    cpx<T> *srcs = reinterpret_cast<cpx<T> *>(smr + ((6 * ncoef(p + 2) + 1) & ~1));
+    cpx<T> *tmp = srcs + kSets * nc;
+    const cpx<T> *E = L + size_t(b) * kSets * nc;
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) srcs[i] = E[i];
+    __syncthreads();
+    int sy = bsys[b];
+    build_eval_set<T, false>(srcs, p, p, EVg + size_t(li) * kNE * nc, tmp, ctr[3 * b] - sc.cube[4 * sy],
+                             ctr[3 * b + 1] - sc.cube[4 * sy + 1], ctr[3 * b + 2] - sc.cube[4 * sy + 2], G);
+}
+
+// One thread per bead: L2P of the leaf's derived expansions and Eq. (2.8).
+template <typename T>
+__global__ void k_eval_apply(int64_t n, const int *bead_leaf, const int *leaves, DevTables<T> D, const double *ctr,
+                             const double *side, const int *lvl, const int *bsys, const double *pos, SysConst sc,
+                             const cpx<T> *EVg, double *ufar) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int li = bead_leaf[i];
+    int b = leaves[li];
+    double u[3] = {0, 0, 0};
+    if (lvl[b] >= 2) {
+        const int p = D.p, nc = ncoef(p);
+        int sy = bsys[b];
+        double a = sc.a[sy], sv = sc.s[sy];
+        double C1 = sv / (8.0 * kPi), C2 = sv * a * a / (12.0 * kPi);
+        double ih = 1.0 / side[b];
+        double xi[3] = {(pos[i] - ctr[3 * b]) * ih, (pos[n + i] - ctr[3 * b + 1]) * ih,
+                        (pos[2 * n + i] - ctr[3 * b + 2]) * ih};
+        T acc[kNE];
+#pragma unroll
+        for (int q = 0; q < kNE; ++q) acc[q] = 0;
+        eval_fields<T, kNE, false>(T(xi[0]), T(xi[1]), T(xi[2]), p, EVg + size_t(li) * kNE * nc, nc, D.rec_a, D.rec_b,
+                                   D.rec_c, acc);
+        for (int d = 0; d < 3; ++d) {
+            double v = double(acc[d]);
+            for (int k = 0; k < 3; ++k) v -= xi[k] * double(acc[3 + 3 * k + d]);
+            u[d] = C1 * ih * v + C1 * ih * ih * double(acc[12 + d]) - C2 * ih * ih * ih * double(acc[15 + d]);
+        }
+    }
+    for (int d = 0; d < 3; ++d) ufar[3 * i + d] = u[d];
 }
 
 // Laplace diagnostic: potential, gradient and Hessian of each set from L2P and M2P.
@@ -718,7 +778,7 @@ static size_t smem_p2x(int p) {
 template <typename T>
 static size_t smem_m2x(int p, int s) {
     int nc = ncoef(p);
-    return sizeof(cpx<T>) * (2 * kSets * nc + 2 * kSets * s * (p + 1));
+    return sizeof(cpx<T>) * (2 * kSets * nc + 2 * s * (p + 1));
 }
 template <typename T>
 static size_t smem_x2l(int p, int s, int S) {
@@ -818,6 +878,14 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     RPY_CHECK(cudaGetLastError());
     prof_mark(t, RPY_STAGE_EVAL, st);
     if (ufar) {
+        cpx<T> *EVg = static_cast<cpx<T> *>(t.EVg);
+        size_t sp2 = sizeof(T) * (((6 * ncoef(p + 2) + 1) & ~1)) + sizeof(cpx<T>) * 2 * kSets * nc + 64;
+        RPY_TRY(set_smem(k_eval_prep<T>, sp2));
+        k_eval_prep<T><<<t.nleaf, 128, sp2, st>>>(t.leaves, D, t.b_center, t.b_level, t.b_sys, sc, L, EVg);
+        RPY_LAUNCHED(1);
+        k_eval_apply<T><<<int((t.n + 127) / 128), 128, 0, st>>>(t.n, t.bead_leaf, t.leaves, D, t.b_center, t.b_side,
+                                                               t.b_level, t.b_sys, t.pos, sc, EVg, ufar);
+        RPY_LAUNCHED(1);
         size_t sf = smem_far<T>(p);
         RPY_TRY(set_smem(k_far_eval<T>, sf));
         k_far_eval<T><<<t.nleaf, 64, sf, st>>>(t.leaves, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level,

@@ -172,6 +172,7 @@ struct Tree {
     double *b_side = nullptr;
     int nleaf = 0;
     int *leaves = nullptr;
+    int *bead_leaf = nullptr;         // [n] leaf index of each sorted bead
     // lists (device CSR)
     int *u_off = nullptr, *u_idx = nullptr;
     int *w_off = nullptr, *w_idx = nullptr;
@@ -186,6 +187,7 @@ struct Tree {
     int direct_w = 0, direct_x = 0;    // bead-count thresholds in use (0 = none)
     // expansions and matvec workspace
     void *M = nullptr, *L = nullptr, *Xo = nullptr, *Xi = nullptr;
+    void *EVg = nullptr;              // [nleaf][18][ncoef(p)] derived local expansions of Eq. (2.8)
     double *fs = nullptr;             // sorted forces SoA [3][n]
     double *u_near = nullptr, *u_far = nullptr, *u_dir = nullptr;   // sorted [n][3]
     double *lap_q = nullptr;          // [n][4] sorted charges for the Laplace debug path

@@ -12,26 +12,25 @@
 // The self term s/(6 pi a) F_i is added once.
 //
 // FP64 form: every operation in FP64; 1/r from a single-precision seed and
-// two Newton-Raphson steps for the reciprocal square root (y <- y (3 - r2 y^2)/2),
-// which restores full double precision.
+// one Newton-Raphson step for the reciprocal square root (y <- y (3 - r2 y^2)/2),
+// which brings the relative error from ~1e-7 to ~1e-14.
 // FP32 form (precision setting): positions relative to the target leaf centre
 // in FP32, far-branch pairs in FP32 with Kahan-compensated accumulation;
 // overlap pairs (r < 2a) recomputed in FP64 from the FP64 positions.
 #include <cmath>
+#include <type_traits>
 
 #include "rpy_internal.h"
 
 namespace rpy {
 
 constexpr double kPiD = 3.14159265358979323846;
-constexpr int kP2PThreads = 128;
+constexpr int kP2PThreads = 256;
 
 __device__ __forceinline__ double rsqrt_newton(double r2) {
     if (r2 < 1e-30 || r2 > 1e30) return 1.0 / sqrt(r2);
-    double y = double(rsqrtf(float(r2)));
-    y = y * (1.5 - 0.5 * r2 * y * y);
-    y = y * (1.5 - 0.5 * r2 * y * y);
-    return y;
+    double y = double(rsqrtf(float(r2)));   // relative error below 2^-21
+    return y * (1.5 - 0.5 * r2 * y * y);     // one Newton step: error below ~1e-12 * 2^-10
 }
 
 __device__ __forceinline__ void overlap_pair(double dx, double dy, double dz, double r2, double fx, double fy, double fz,
@@ -51,81 +50,6 @@ __device__ __forceinline__ void overlap_pair(double dx, double dy, double dz, do
     }
 }
 
-__global__ void __launch_bounds__(kP2PThreads) k_p2p64(const int *leaves, const int *beg, const int *end,
-                                                        const int *bsys, const int *uoff, const int *uidx,
-                                                        const double *pos, const double *fs, int64_t n, SysConst sc,
-                                                        int add_self, double *unear) {
-    __shared__ double sx[kP2PThreads], sy[kP2PThreads], sz[kP2PThreads];
-    __shared__ double sfx[kP2PThreads], sfy[kP2PThreads], sfz[kP2PThreads];
-    __shared__ double red[3][kP2PThreads];
-    int li = blockIdx.x;
-    int b = leaves[li];
-    int sys = bsys[b];
-    double a = sc.a[sys], s = sc.s[sys];
-    double a2x4 = 4.0 * a * a, a2 = a * a;
-    double cf = s / (8.0 * kPiD), co = s / (6.0 * kPiD * a);
-    int u0 = uoff[li], u1 = uoff[li + 1];
-    // R targets per pass (a multiple of the warp size), G groups splitting the sources
-    int nt = end[b] - beg[b];
-    int R = nt >= int(blockDim.x) ? int(blockDim.x) : ((nt + 31) & ~31);
-    int G = int(blockDim.x) / R;
-    int tl = threadIdx.x % R, g = threadIdx.x / R;
-    for (int i0 = beg[b]; i0 < end[b]; i0 += R) {
-        int i = i0 + tl;
-        bool act = i < end[b] && g < G;
-        double xi = act ? pos[i] : 0, yi = act ? pos[n + i] : 0, zi = act ? pos[2 * n + i] : 0;
-        double acc[3] = {0, 0, 0};
-        for (int u = u0; u < u1; ++u) {
-            int C = uidx[u];
-            for (int j0 = beg[C]; j0 < end[C]; j0 += blockDim.x) {
-                int cnt = min(int(blockDim.x), end[C] - j0);
-                __syncthreads();
-                if (threadIdx.x < cnt) {
-                    int j = j0 + threadIdx.x;
-                    sx[threadIdx.x] = pos[j];
-                    sy[threadIdx.x] = pos[n + j];
-                    sz[threadIdx.x] = pos[2 * n + j];
-                    sfx[threadIdx.x] = fs[j];
-                    sfy[threadIdx.x] = fs[n + j];
-                    sfz[threadIdx.x] = fs[2 * n + j];
-                }
-                __syncthreads();
-                if (!act) continue;
-                for (int jj = g; jj < cnt; jj += G) {
-                    double dx = xi - sx[jj], dy = yi - sy[jj], dz = zi - sz[jj];
-                    double r2 = dx * dx + dy * dy + dz * dz;
-                    double fx = sfx[jj], fy = sfy[jj], fz = sfz[jj];
-                    if (r2 >= a2x4) {
-                        double ri = rsqrt_newton(r2);
-                        double ri2 = ri * ri;
-                        double c = cf * ri;
-                        double q = a2 * ri2;
-                        double RF = dx * fx + dy * fy + dz * fz;
-                        double t1 = c * (1.0 + (2.0 / 3.0) * q);
-                        double t2 = c * (1.0 - 2.0 * q) * RF * ri2;
-                        acc[0] += t1 * fx + t2 * dx;
-                        acc[1] += t1 * fy + t2 * dy;
-                        acc[2] += t1 * fz + t2 * dz;
-                    } else if (j0 + jj != i) {
-                        overlap_pair(dx, dy, dz, r2, fx, fy, fz, a, co, acc);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = acc[c];
-        __syncthreads();
-        if (act && g == 0) {
-            for (int gg = 1; gg < G; ++gg)
-                for (int c = 0; c < 3; ++c) acc[c] += red[c][threadIdx.x + gg * R];
-            double cs = add_self ? co : 0.0;
-            unear[3 * size_t(i)] = acc[0] + cs * fs[i];
-            unear[3 * size_t(i) + 1] = acc[1] + cs * fs[n + i];
-            unear[3 * size_t(i) + 2] = acc[2] + cs * fs[2 * n + i];
-        }
-    }
-}
-
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
     float y = v - c;
     float t = s + y;
@@ -133,70 +57,122 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
     s = t;
 }
 
-__global__ void __launch_bounds__(kP2PThreads) k_p2p32(const int *leaves, const int *beg, const int *end,
-                                                        const int *bsys, const double *ctr, const int *uoff,
-                                                        const int *uidx, const double *pos, const double *fs,
-                                                        int64_t n, SysConst sc, int add_self, double *unear) {
-    __shared__ float sx[kP2PThreads], sy[kP2PThreads], sz[kP2PThreads];
-    __shared__ float sfx[kP2PThreads], sfy[kP2PThreads], sfz[kP2PThreads];
+// Source staging: the beads of all source boxes of a leaf's list are streamed
+// through shared memory in chunks of blockDim, across box boundaries.  Every
+// thread locates its bead of the chunk by walking the list from a uniform
+// cursor (lists hold a few dozen boxes).
+struct SrcCursor {
+    int u, off;   // list position and offset inside that box
+};
+
+__device__ __forceinline__ int cursor_locate(SrcCursor c, int u1, int t, const int *uidx, const int *beg,
+                                             const int *end) {
+    int u = c.u, off = c.off;
+    while (u < u1) {
+        int C = uidx[u];
+        int avail = end[C] - beg[C] - off;
+        if (t < avail) return beg[C] + off + t;
+        t -= avail;
+        ++u;
+        off = 0;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ SrcCursor cursor_advance(SrcCursor c, int u1, int t, const int *uidx, const int *beg,
+                                                    const int *end) {
+    while (c.u < u1) {
+        int C = uidx[c.u];
+        int avail = end[C] - beg[C] - c.off;
+        if (t < avail) {
+            c.off += t;
+            return c;
+        }
+        t -= avail;
+        ++c.u;
+        c.off = 0;
+    }
+    return c;
+}
+
+// Thread layout: a leaf of T beads uses R = min(T, blockDim) targets per pass and
+// G = blockDim / R groups; group g takes every G-th bead of each staged chunk.
+template <bool FP32>
+__global__ void __launch_bounds__(kP2PThreads) k_p2p(const int *leaves, const int *beg, const int *end,
+                                                     const int *bsys, const double *ctr, const int *uoff,
+                                                     const int *uidx, const double *pos, const double *fs,
+                                                     int64_t n, SysConst sc, int add_self, double *out) {
+    using R_t = typename std::conditional<FP32, float, double>::type;
+    __shared__ R_t sx[kP2PThreads], sy[kP2PThreads], sz[kP2PThreads];
+    __shared__ R_t sfx[kP2PThreads], sfy[kP2PThreads], sfz[kP2PThreads];
+    __shared__ int sj[kP2PThreads];
     __shared__ double red[3][kP2PThreads];
     int li = blockIdx.x;
     int b = leaves[li];
     int sys = bsys[b];
     double a = sc.a[sys], s = sc.s[sys];
-    float a2x4 = float(4.0 * a * a), a2 = float(a * a);
-    float cf = float(s / (8.0 * kPiD));
     double co = s / (6.0 * kPiD * a);
-    double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
+    R_t a2x4 = R_t(4.0 * a * a), a2 = R_t(a * a), cf = R_t(s / (8.0 * kPiD));
+    // FP32 works in coordinates relative to the target leaf centre
+    double cx = FP32 ? ctr[3 * b] : 0.0, cy = FP32 ? ctr[3 * b + 1] : 0.0, cz = FP32 ? ctr[3 * b + 2] : 0.0;
     int u0 = uoff[li], u1 = uoff[li + 1];
     int nt = end[b] - beg[b];
-    int R = nt >= int(blockDim.x) ? int(blockDim.x) : ((nt + 31) & ~31);
-    int G = int(blockDim.x) / R;
-    int tl = threadIdx.x % R, g = threadIdx.x / R;
-    for (int i0 = beg[b]; i0 < end[b]; i0 += R) {
+    int Rn = nt < int(blockDim.x) ? nt : int(blockDim.x);
+    int G = int(blockDim.x) / Rn;
+    int tl = threadIdx.x % Rn, g = threadIdx.x / Rn;
+    for (int i0 = beg[b]; i0 < end[b]; i0 += Rn) {
         int i = i0 + tl;
         bool act = i < end[b] && g < G;
-        float xi = act ? float(pos[i] - cx) : 0.f, yi = act ? float(pos[n + i] - cy) : 0.f,
-              zi = act ? float(pos[2 * n + i] - cz) : 0.f;
-        float acc[3] = {0, 0, 0}, cmp[3] = {0, 0, 0};
+        R_t xi = act ? R_t(pos[i] - cx) : R_t(0), yi = act ? R_t(pos[n + i] - cy) : R_t(0),
+            zi = act ? R_t(pos[2 * n + i] - cz) : R_t(0);
+        R_t acc[3] = {0, 0, 0}, cmp[3] = {0, 0, 0};
         double accd[3] = {0, 0, 0};
-        for (int u = u0; u < u1; ++u) {
-            int C = uidx[u];
-            for (int j0 = beg[C]; j0 < end[C]; j0 += blockDim.x) {
-                int cnt = min(int(blockDim.x), end[C] - j0);
-                __syncthreads();
-                if (threadIdx.x < cnt) {
-                    int j = j0 + threadIdx.x;
-                    sx[threadIdx.x] = float(pos[j] - cx);
-                    sy[threadIdx.x] = float(pos[n + j] - cy);
-                    sz[threadIdx.x] = float(pos[2 * n + j] - cz);
-                    sfx[threadIdx.x] = float(fs[j]);
-                    sfy[threadIdx.x] = float(fs[n + j]);
-                    sfz[threadIdx.x] = float(fs[2 * n + j]);
-                }
-                __syncthreads();
-                if (!act) continue;
-                for (int jj = g; jj < cnt; jj += G) {
-                    float dx = xi - sx[jj], dy = yi - sy[jj], dz = zi - sz[jj];
-                    float r2 = dx * dx + dy * dy + dz * dz;
-                    float fx = sfx[jj], fy = sfy[jj], fz = sfz[jj];
-                    if (r2 >= a2x4) {
-                        float ri = rsqrtf(r2);
-                        float ri2 = ri * ri;
-                        float c = cf * ri;
-                        float q = a2 * ri2;
-                        float RF = dx * fx + dy * fy + dz * fz;
-                        float t1 = c * (1.0f + (2.0f / 3.0f) * q);
-                        float t2 = c * (1.0f - 2.0f * q) * RF * ri2;
+        SrcCursor cur{u0, 0};
+        while (cur.u < u1) {
+            __syncthreads();
+            int j = cursor_locate(cur, u1, threadIdx.x, uidx, beg, end);
+            sj[threadIdx.x] = j;
+            if (j >= 0) {
+                sx[threadIdx.x] = R_t(pos[j] - cx);
+                sy[threadIdx.x] = R_t(pos[n + j] - cy);
+                sz[threadIdx.x] = R_t(pos[2 * n + j] - cz);
+                sfx[threadIdx.x] = R_t(fs[j]);
+                sfy[threadIdx.x] = R_t(fs[n + j]);
+                sfz[threadIdx.x] = R_t(fs[2 * n + j]);
+            }
+            cur = cursor_advance(cur, u1, int(blockDim.x), uidx, beg, end);
+            __syncthreads();
+            if (!act) continue;
+            for (int jj = g; jj < int(blockDim.x); jj += G) {
+                int jg = sj[jj];
+                if (jg < 0) break;
+                R_t dx = xi - sx[jj], dy = yi - sy[jj], dz = zi - sz[jj];
+                R_t r2 = dx * dx + dy * dy + dz * dz;
+                R_t fx = sfx[jj], fy = sfy[jj], fz = sfz[jj];
+                if (r2 >= a2x4) {
+                    R_t ri;
+                    if constexpr (FP32) ri = rsqrtf(r2);
+                    else ri = rsqrt_newton(r2);
+                    R_t ri2 = ri * ri;
+                    R_t c = cf * ri;
+                    R_t q = a2 * ri2;
+                    R_t RF = dx * fx + dy * fy + dz * fz;
+                    R_t t1 = c * (R_t(1) + R_t(2.0 / 3.0) * q);
+                    R_t t2 = c * (R_t(1) - R_t(2) * q) * RF * ri2;
+                    if constexpr (FP32) {
                         kahan_add(acc[0], cmp[0], t1 * fx + t2 * dx);
                         kahan_add(acc[1], cmp[1], t1 * fy + t2 * dy);
                         kahan_add(acc[2], cmp[2], t1 * fz + t2 * dz);
-                    } else if (j0 + jj != i) {
-                        int j = j0 + jj;
-                        double ddx = pos[i] - pos[j], ddy = pos[n + i] - pos[n + j], ddz = pos[2 * n + i] - pos[2 * n + j];
-                        overlap_pair(ddx, ddy, ddz, ddx * ddx + ddy * ddy + ddz * ddz, fs[j], fs[n + j], fs[2 * n + j],
-                                     a, co, accd);
+                    } else {
+                        acc[0] += t1 * fx + t2 * dx;
+                        acc[1] += t1 * fy + t2 * dy;
+                        acc[2] += t1 * fz + t2 * dz;
                     }
+                } else if (jg != i) {
+                    // overlap branch (r < 2a) and coincident beads: always FP64
+                    double ddx = pos[i] - pos[jg], ddy = pos[n + i] - pos[n + jg], ddz = pos[2 * n + i] - pos[2 * n + jg];
+                    overlap_pair(ddx, ddy, ddz, ddx * ddx + ddy * ddy + ddz * ddz, fs[jg], fs[n + jg], fs[2 * n + jg], a,
+                                 co, accd);
                 }
             }
         }
@@ -207,12 +183,12 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p32(const int *leaves, const 
             double v[3];
             for (int c = 0; c < 3; ++c) {
                 v[c] = red[c][threadIdx.x];
-                for (int gg = 1; gg < G; ++gg) v[c] += red[c][threadIdx.x + gg * R];
+                for (int gg = 1; gg < G; ++gg) v[c] += red[c][threadIdx.x + gg * Rn];
             }
             double cs = add_self ? co : 0.0;
-            unear[3 * size_t(i)] = v[0] + cs * fs[i];
-            unear[3 * size_t(i) + 1] = v[1] + cs * fs[n + i];
-            unear[3 * size_t(i) + 2] = v[2] + cs * fs[2 * n + i];
+            out[3 * size_t(i)] = v[0] + cs * fs[i];
+            out[3 * size_t(i) + 1] = v[1] + cs * fs[n + i];
+            out[3 * size_t(i) + 2] = v[2] + cs * fs[2 * n + i];
         }
     }
 }
@@ -224,12 +200,12 @@ int run_p2p(Tree &t, const double *fs, double *out, const SysConst &sc, cudaStre
     const int *idx = direct_list ? t.d_idx : t.u_idx;
     int add_self = direct_list ? 0 : 1;
     if (t.params.precision == RPY_FP32) {
-        k_p2p32<<<t.nleaf, kP2PThreads, 0, st>>>(t.leaves, t.b_begin, t.b_end, t.b_sys, t.b_center, off, idx, t.pos,
-                                                 fs, t.n, sc, add_self, out);
+        k_p2p<true><<<t.nleaf, kP2PThreads, 0, st>>>(t.leaves, t.b_begin, t.b_end, t.b_sys, t.b_center, off, idx,
+                                                     t.pos, fs, t.n, sc, add_self, out);
         RPY_LAUNCHED(1);
     } else {
-        k_p2p64<<<t.nleaf, kP2PThreads, 0, st>>>(t.leaves, t.b_begin, t.b_end, t.b_sys, off, idx, t.pos, fs, t.n, sc,
-                                                 add_self, out);
+        k_p2p<false><<<t.nleaf, kP2PThreads, 0, st>>>(t.leaves, t.b_begin, t.b_end, t.b_sys, t.b_center, off, idx,
+                                                      t.pos, fs, t.n, sc, add_self, out);
         RPY_LAUNCHED(1);
     }
     RPY_CHECK(cudaGetLastError());

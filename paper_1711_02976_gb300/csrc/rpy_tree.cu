@@ -663,6 +663,13 @@ __global__ void k_leafid(int n, const int *leaf, const int *pos, int *leafid) {
     if (i < n) leafid[i] = leaf[i] ? pos[i] : -1;
 }
 
+__global__ void k_bead_leaf(int nleaf, const int *leaves, const int *beg, const int *end, int *bead_leaf) {
+    int li = blockIdx.x;
+    if (li >= nleaf) return;
+    int b = leaves[li];
+    for (int i = beg[b] + threadIdx.x; i < end[b]; i += blockDim.x) bead_leaf[i] = li;
+}
+
 __global__ void k_x2x_flag(int b0, int nbox, const int *leaf, int *flag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nbox) flag[i] = (i >= b0 && !leaf[i]) ? 1 : 0;
@@ -847,6 +854,11 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     RPY_LAUNCHED(1);
     k_leafid<<<nblk(nbx, 256), 256, 0, st>>>(nbx, t.b_leaf, pos_tmp, t.b_leafid);
     RPY_LAUNCHED(1);
+    RPY_TRY(dev_alloc(t, (void **)&t.bead_leaf, sizeof(int) * n));
+    if (nleaf > 0) {
+        k_bead_leaf<<<nleaf, 64, 0, st>>>(nleaf, t.leaves, t.b_begin, t.b_end, t.bead_leaf);
+        RPY_LAUNCHED(1);
+    }
     // -- X2X parents: non-leaf boxes at level >= 1
     {
         int *flag;
