@@ -333,7 +333,11 @@ const ExpQuad &exp_quadrature(int digits) {
     return digits <= 3 ? q3 : q6;
 }
 
-int default_order(int digits) { return digits <= 3 ? 10 : 20; }
+// Expansion order per setting, chosen from measured rel-L2 against the oracle
+// (1M-bead sphere and 4M-bead cube): p = 8 gives 5.5e-5 / 1.9e-5 at 3 digits,
+// p = 18 gives 4.0e-8 at 6 digits, each with a far-field-only error at least
+// 3x below the setting.
+int default_order(int digits) { return digits <= 3 ? 8 : 18; }
 int default_leaf_cap(int digits) { return digits <= 3 ? 40 : 100; }
 
 int build_tables(int p, int digits, OpTables &t) {
