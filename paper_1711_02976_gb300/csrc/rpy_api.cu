@@ -153,6 +153,10 @@ static void pack_tables(const OpTables &h, std::vector<char> &blob, std::vector<
     putI(h.slot_list);// 21
     putI(h.child_shift); // 22
     putT(h.lad);      // 23
+    putT(h.orot_fwd); // 24
+    putT(h.orot_bwd); // 25
+    putT(h.zm2m);     // 26
+    putT(h.zl2l);     // 27
 }
 
 template <typename T>
@@ -187,6 +191,10 @@ static DevTables<T> bind_tables(const OpTables &h, char *base, const std::vector
     d.slot_list = reinterpret_cast<const int *>(base + o[21]);
     d.child_shift = reinterpret_cast<const int *>(base + o[22]);
     d.lad = reinterpret_cast<const T *>(base + o[23]);
+    d.orot_fwd = reinterpret_cast<const T *>(base + o[24]);
+    d.orot_bwd = reinterpret_cast<const T *>(base + o[25]);
+    d.zm2m = reinterpret_cast<const T *>(base + o[26]);
+    d.zl2l = reinterpret_cast<const T *>(base + o[27]);
     return d;
 }
 
@@ -777,6 +785,10 @@ int rpy_debug_table(int p, int digits, int which, double *dst, int64_t capacity,
             for (int o : h->rot_off) tmp.push_back(o);
             v = &tmp;
             break;
+        case 12: v = &h->orot_fwd; break;
+        case 13: v = &h->orot_bwd; break;
+        case 14: v = &h->zm2m; break;
+        case 15: v = &h->zl2l; break;
         case 11:   // quadrature: s, then lambda, weight, M per node
         {
             const ExpQuad &q = exp_quadrature(digits);

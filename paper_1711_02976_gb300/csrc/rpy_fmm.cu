@@ -7,7 +7,7 @@
 //
 // Kernels, in launch order:
 //   k_p2m      S->M   leaves: M_n^m = sum_j q_j conj(y_n^m(eta_j))
-//   k_m2m      M->M   dense per-octant operator, level by level upward
+//   k_m2m_rot  M->M   rotate to the child's shift axis, z-shift, rotate back
 //   k_m2x      M->I   rotate into the frame of each axis, outgoing plane waves
 //                     W_kj = (w_k/M_k) sum_{n,m} M_n^m i^|m| lambda_k^n e^{i m a_kj} / sqrt((n-|m|)!(n+|m|)!)
 //   k_x2x      I->I   merge-and-shift: per parent and direction, sources are
@@ -16,7 +16,7 @@
 //   k_x2l      I->L   L_n^m = i^|m| sum_k (-lambda_k)^n / sqrt(...) sum_j I_kj e^{-i m a_kj},
 //                     rotated back to the world frame
 //   k_p2l      S->L   X list
-//   k_l2l      L->L   level by level downward
+//   k_l2l_rot  L->L   the same for locals, level by level downward
 //   k_far_eval L->T, M->T   L2P for the leaf and M2P for its W list, with the
 //                     gradients and Hessians of Theorems 1-2 formed as
 //                     derivative expansions per box, combined by Eq. (2.8):
@@ -266,66 +266,6 @@ __global__ void k_p2x(int b0, int nb, DevTables<T> D, const int *beg, const int 
 
 // ---------------------------------------------------------------- M2M / L2L
 
-// M2M: parent M = sum over children of T_o [child M]; output degree n uses inputs of degree <= n.
-template <typename T>
-__global__ void k_m2m(int b0, int nb, DevTables<T> D, const int *leaf, const int *child, cpx<T> *M) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    int b = b0 + blockIdx.x;
-    if (leaf[b]) return;
-    const int nc = ncoef(D.p), Dd = 2 * nc;
-    T *X = reinterpret_cast<T *>(smem_raw);
-    int r = threadIdx.x;
-    int kmax = r < Dd ? 2 * ncoef(deg_of(r >> 1)) : 0;
-    T acc[kSets] = {0, 0, 0, 0};
-    for (int o = 0; o < 8; ++o) {
-        int c = child[8 * b + o];
-        if (c < 0) continue;
-        const T *src = reinterpret_cast<const T *>(M + size_t(c) * kSets * nc);
-        __syncthreads();
-        for (int i = threadIdx.x; i < kSets * Dd; i += blockDim.x) X[i] = src[i];
-        __syncthreads();
-        if (r < Dd) {
-            const T *Tt = D.m2m_t + size_t(o) * Dd * Dd;
-            for (int k = 0; k < kmax; ++k) {
-                T t = Tt[size_t(k) * Dd + r];
-#pragma unroll
-                for (int s = 0; s < kSets; ++s) acc[s] += t * X[s * Dd + k];
-            }
-        }
-    }
-    if (r < Dd) {
-        T *dst = reinterpret_cast<T *>(M + size_t(b) * kSets * nc);
-        for (int s = 0; s < kSets; ++s) dst[s * Dd + r] = acc[s];
-    }
-}
-
-// L2L: child L += S_o [parent L]; output degree k uses inputs of degree >= k.
-template <typename T>
-__global__ void k_l2l(int b0, int nb, DevTables<T> D, const int *par, const int *cell, cpx<T> *L) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    int b = b0 + blockIdx.x;
-    int P = par[b];
-    const int nc = ncoef(D.p), Dd = 2 * nc;
-    T *X = reinterpret_cast<T *>(smem_raw);
-    const T *src = reinterpret_cast<const T *>(L + size_t(P) * kSets * nc);
-    for (int i = threadIdx.x; i < kSets * Dd; i += blockDim.x) X[i] = src[i];
-    __syncthreads();
-    int r = threadIdx.x;
-    if (r >= Dd) return;
-    int o = (cell[3 * b] & 1) | ((cell[3 * b + 1] & 1) << 1) | ((cell[3 * b + 2] & 1) << 2);
-    int kdeg = deg_of(r >> 1);
-    int k0 = 2 * tri(kdeg, 0);
-    const T *St = D.l2l_t + size_t(o) * Dd * Dd;
-    T acc[kSets] = {0, 0, 0, 0};
-    for (int k = k0; k < Dd; ++k) {
-        T t = St[size_t(k) * Dd + r];
-#pragma unroll
-        for (int s = 0; s < kSets; ++s) acc[s] += t * X[s * Dd + k];
-    }
-    T *dst = reinterpret_cast<T *>(L + size_t(b) * kSets * nc);
-    for (int s = 0; s < kSets; ++s) dst[s * Dd + r] += acc[s];
-}
-
 // ---------------------------------------------------------------- rotations
 // dst[s] = R src[s] per degree block (real 2-layout, block size 2(n+1)).
 template <typename T>
@@ -343,6 +283,76 @@ __device__ void rotate_sets(const T *rot, const int *roff, int p, const cpx<T> *
         for (int c = 0; c < B; ++c) a += row[c] * in[c];
         reinterpret_cast<T *>(dst + s * nc)[r] = a;
     }
+}
+
+// ---------------------------------------------------------------- rotation-based M2M / L2L
+// Child octant o: rotate into the frame whose z axis is the shift direction,
+// apply the m-diagonal z-shift, rotate back (O(p^3) per child instead of the
+// O(p^4) dense operator).
+template <typename T>
+__global__ void k_m2m_rot(int b0, int nb, DevTables<T> D, const int *leaf, const int *child, cpx<T> *M) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int b = b0 + blockIdx.x;
+    if (leaf[b]) return;
+    const int p = D.p, nc = ncoef(p), P1 = p + 1;
+    cpx<T> *X = reinterpret_cast<cpx<T> *>(smem_raw);
+    cpx<T> *Y = X + kSets * nc;
+    cpx<T> *acc = Y + kSets * nc;
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) acc[i] = mk<T>(0, 0);
+    for (int o = 0; o < 8; ++o) {
+        int c = child[8 * b + o];
+        if (c < 0) continue;
+        __syncthreads();
+        const cpx<T> *src = M + size_t(c) * kSets * nc;
+        for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) X[i] = src[i];
+        __syncthreads();
+        rotate_sets(D.orot_fwd + size_t(o) * D.rot_len, D.rot_off, p, X, Y);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
+            int st = e / nc, i = e - st * nc;
+            int n = deg_of(i), m = i - tri(n, 0);
+            const T *z = D.zm2m + size_t(i) * P1;
+            cpx<T> a = mk<T>(0, 0);
+            for (int k = m; k <= n; ++k) a += z[k] * Y[st * nc + tri(k, m)];
+            X[e] = a;
+        }
+        __syncthreads();
+        rotate_sets(D.orot_bwd + size_t(o) * D.rot_len, D.rot_off, p, X, Y);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) acc[i] += Y[i];
+    }
+    __syncthreads();
+    cpx<T> *dst = M + size_t(b) * kSets * nc;
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) dst[i] = acc[i];
+}
+
+template <typename T>
+__global__ void k_l2l_rot(int b0, int nb, DevTables<T> D, const int *par, const int *cell, cpx<T> *L) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int b = b0 + blockIdx.x;
+    int P = par[b];
+    const int p = D.p, nc = ncoef(p), P1 = p + 1;
+    cpx<T> *X = reinterpret_cast<cpx<T> *>(smem_raw);
+    cpx<T> *Y = X + kSets * nc;
+    int o = (cell[3 * b] & 1) | ((cell[3 * b + 1] & 1) << 1) | ((cell[3 * b + 2] & 1) << 2);
+    const cpx<T> *src = L + size_t(P) * kSets * nc;
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) X[i] = src[i];
+    __syncthreads();
+    rotate_sets(D.orot_fwd + size_t(o) * D.rot_len, D.rot_off, p, X, Y);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
+        int st = e / nc, i = e - st * nc;
+        int n = deg_of(i), m = i - tri(n, 0);
+        const T *z = D.zl2l + size_t(i) * P1;
+        cpx<T> a = mk<T>(0, 0);
+        for (int k = n; k <= p; ++k) a += z[k] * Y[st * nc + tri(k, m)];
+        X[e] = a;
+    }
+    __syncthreads();
+    rotate_sets(D.orot_bwd + size_t(o) * D.rot_len, D.rot_off, p, X, Y);
+    __syncthreads();
+    cpx<T> *dst = L + size_t(b) * kSets * nc;
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) dst[i] += Y[i];
 }
 
 // ---------------------------------------------------------------- M2X
@@ -826,16 +836,14 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
                                      t.b_sys, t.x_off, t.x_idx, t.pos, fs, lapq, t.n, sc, M);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
-    int Dd = 2 * nc;
-    int thr = ((Dd + 31) / 32) * 32;
-    size_t sm2 = sizeof(T) * kSets * Dd;
     prof_mark(t, RPY_STAGE_M2M, st);
-    RPY_TRY(set_smem(k_m2m<T>, sm2));
-    RPY_TRY(set_smem(k_l2l<T>, sm2));
+    size_t smr3 = sizeof(cpx<T>) * 3 * kSets * nc, smr2 = sizeof(cpx<T>) * 2 * kSets * nc;
+    RPY_TRY(set_smem(k_m2m_rot<T>, smr3));
+    RPY_TRY(set_smem(k_l2l_rot<T>, smr2));
     for (int l = t.nlevels - 2; l >= 2; --l) {
         int lb = t.level_off[l], ln = t.level_off[l + 1] - lb;
         if (ln > 0) {
-            k_m2m<T><<<ln, thr, sm2, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
+            k_m2m_rot<T><<<ln, 256, smr3, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
             RPY_LAUNCHED(1);
         }
     }
@@ -871,7 +879,7 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     for (int l = 3; l < t.nlevels; ++l) {
         int lb = t.level_off[l], ln = t.level_off[l + 1] - lb;
         if (ln > 0) {
-            k_l2l<T><<<ln, thr, sm2, st>>>(lb, ln, D, t.b_parent, t.b_cell, L);
+            k_l2l_rot<T><<<ln, 256, smr2, st>>>(lb, ln, D, t.b_parent, t.b_cell, L);
             RPY_LAUNCHED(1);
         }
     }

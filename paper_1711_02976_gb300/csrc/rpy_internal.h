@@ -119,6 +119,10 @@ struct OpTables {
     // local:     lz = sqrt((k+1+m)(k+1-m)), lp = sqrt((k-m+1)(k-m+2)), lq = sqrt((k+m+1)(k+m+2))
     // multipole: mz = sqrt((k+m)(k-m)),     mp = sqrt((k+m)(k+m-1)),   mq = sqrt((k-m)(k-m-1))
     std::vector<double> lad;      // [6][ncoef(p+2)] in the order lz lp lq mz mp mq
+    // rotation-based M2M / L2L: per child octant, rotations world -> frame whose z axis is
+    // the shift direction and back, and the m-diagonal z-shift coefficients
+    std::vector<double> orot_fwd, orot_bwd;   // [8][rot_len]
+    std::vector<double> zm2m, zl2l;           // [ncoef(p)][p+1]: output (n,m), input degree k
 };
 constexpr int kGroupMax = 32;
 
@@ -132,6 +136,7 @@ struct DevTables {
     const int *rot_off;
     const T *rec_a, *rec_b, *rec_c, *rec_cm;
     const T *lad;
+    const T *orot_fwd, *orot_bwd, *zm2m, *zl2l;
     const cpx<T> *roots;
     const T *m2x_c, *x2l_c;
     const int *e_k, *k_start;

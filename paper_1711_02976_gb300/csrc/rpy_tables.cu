@@ -245,6 +245,50 @@ static void build_rotations(int p, std::vector<double> &fwd, std::vector<double>
     }
 }
 
+// Per child octant: rotation whose third row (the frame's z axis) is the unit
+// shift direction from the parent centre to the child centre.
+static void octant_frame(int o, double Q[9]) {
+    double sx = (o & 1) ? 1.0 : -1.0, sy = (o & 2) ? 1.0 : -1.0, sz = (o & 4) ? 1.0 : -1.0;
+    double r3 = 1.0 / std::sqrt(3.0), r2 = 1.0 / std::sqrt(2.0);
+    double z[3] = {sx * r3, sy * r3, sz * r3};
+    double x[3] = {-sy * r2, sx * r2, 0.0};
+    double y[3] = {z[1] * x[2] - z[2] * x[1], z[2] * x[0] - z[0] * x[2], z[0] * x[1] - z[1] * x[0]};
+    for (int a = 0; a < 3; ++a) {
+        Q[a] = x[a];
+        Q[3 + a] = y[a];
+        Q[6 + a] = z[a];
+    }
+}
+
+// Real per-degree blocks for an arbitrary rotation Q (frame = Q world), written
+// at fwd / bwd in the layout of build_rotations.
+static void rotation_blocks(const double Q[9], int p, const std::vector<int> &off, double *F, double *Bk) {
+    double Qt[9];
+    transpose3(Q, Qt);
+    for (int n = 0; n <= p; ++n) {
+        int B = 2 * (n + 1), dim = 2 * n + 1;
+        std::vector<cd> D = rotmat(Qt, n);
+        std::vector<cd> K = rotmat(Q, n);
+        double *f = F + off[n], *bk = Bk + off[n];
+        for (int i = 0; i < B * B; ++i) f[i] = bk[i] = 0.0;
+        for (int mo = 0; mo <= n; ++mo)
+            for (int mi = -n; mi <= n; ++mi) {
+                cd cf = D[size_t(mi + n) * dim + (mo + n)];
+                cd cb = K[size_t(mi + n) * dim + (mo + n)];
+                int ro = 2 * mo, ci = 2 * (mi < 0 ? -mi : mi);
+                double s = mi < 0 ? -1.0 : 1.0;
+                f[ro * B + ci] += cf.real();
+                f[ro * B + ci + 1] += -s * cf.imag();
+                f[(ro + 1) * B + ci] += cf.imag();
+                f[(ro + 1) * B + ci + 1] += s * cf.real();
+                bk[ro * B + ci] += cb.real();
+                bk[ro * B + ci + 1] += -s * cb.imag();
+                bk[(ro + 1) * B + ci] += cb.imag();
+                bk[(ro + 1) * B + ci + 1] += s * cb.real();
+            }
+    }
+}
+
 // signed-permutation frame matrices P_d for the six directions
 static void frame_matrix(int d, int P[9]) {
     static const int Pz[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
@@ -385,6 +429,33 @@ int build_tables(int p, int digits, OpTables &t) {
         }
     }
     build_groups(t);
+    // rotation-based M2M / L2L
+    {
+        int L = t.rot_off.back();
+        t.orot_fwd.assign(size_t(8) * L, 0.0);
+        t.orot_bwd.assign(size_t(8) * L, 0.0);
+        for (int o = 0; o < 8; ++o) {
+            double Q[9];
+            octant_frame(o, Q);
+            rotation_blocks(Q, p, t.rot_off, &t.orot_fwd[size_t(o) * L], &t.orot_bwd[size_t(o) * L]);
+        }
+        // along the frame z axis the shift is delta = sqrt(3)/4 parent sides:
+        // M2M  M^p_n^m = sum_{k=m..n} (N_n^m / N_k^m) delta^{n-k} / (n-k)! 2^{-k} M^c_k^m
+        // L2L  L^c_k^m = sum_{n=k..p} (N_n^m / N_k^m) delta^{n-k} / (n-k)! 2^{-k-1} L^p_n^m
+        double delta = std::sqrt(3.0) / 4.0;
+        t.zm2m.assign(size_t(t.nc) * (p + 1), 0.0);
+        t.zl2l.assign(size_t(t.nc) * (p + 1), 0.0);
+        for (int n = 0; n <= p; ++n)
+            for (int m = 0; m <= n; ++m)
+                for (int k = m; k <= p; ++k) {
+                    if (k <= n)
+                        t.zm2m[size_t(tri(n, m)) * (p + 1) + k] =
+                            Nnm(n, m) / Nnm(k, m) * std::pow(delta, n - k) / fact(n - k) * std::ldexp(1.0, -k);
+                    if (k >= n)   // output (n, m) of L2L takes inputs of degree k >= n
+                        t.zl2l[size_t(tri(n, m)) * (p + 1) + k] =
+                            Nnm(k, m) / Nnm(n, m) * std::pow(delta, k - n) / fact(k - n) * std::ldexp(1.0, -n - 1);
+                }
+    }
     t.roots.assign(size_t(2) * t.S * 2, 0.0);
     for (int k = 0; k < q.s; ++k)
         for (int r = 0; r < q.m[k]; ++r) {

@@ -268,3 +268,38 @@ def test_merge_and_shift_groups_cover_v_lists():
                     assert (q * 8 + o, t) not in served
                 else:
                     assert served[(q * 8 + o, t)] == d
+
+
+@pytest.mark.parametrize("p", [6, 12])
+def test_rotation_m2m_l2l_equal_dense_operators(p):
+    """Rotate to the child's shift axis, shift along z, rotate back: the same
+    linear maps as the dense addition-theorem operators."""
+    nc = ncoef(p)
+    D = 2 * nc
+    dense_m = rp.rpy_debug_table(p, 3, 1).reshape(8, D, D)
+    dense_l = rp.rpy_debug_table(p, 3, 2).reshape(8, D, D)
+    fwd, bwd = rp.rpy_debug_table(p, 3, 12), rp.rpy_debug_table(p, 3, 13)
+    zm = rp.rpy_debug_table(p, 3, 14).reshape(nc, p + 1)
+    zl = rp.rpy_debug_table(p, 3, 15).reshape(nc, p + 1)
+    offs = rp.rpy_debug_table(p, 3, 10)
+    L = int(offs[-1])
+    rng = np.random.default_rng(p)
+    x = rng.standard_normal(nc) + 1j * rng.standard_normal(nc)
+    for n in range(p + 1):
+        x[tri(n, 0)] = x[tri(n, 0)].real
+
+    def zshift(z, y, lower):
+        out = np.zeros_like(y)
+        for n in range(p + 1):
+            for m in range(n + 1):
+                ks = range(m, n + 1) if lower else range(n, p + 1)
+                out[tri(n, m)] = sum(z[tri(n, m), k] * y[tri(k, m)] for k in ks)
+        return out
+
+    for o in range(8):
+        f = np.concatenate([fwd[o * L:(o + 1) * L], fwd[o * L:(o + 1) * L]])
+        b = np.concatenate([bwd[o * L:(o + 1) * L], bwd[o * L:(o + 1) * L]])
+        ym = _rot_apply(b, offs, p, 0, zshift(zm, _rot_apply(f, offs, p, 0, x), True))
+        np.testing.assert_allclose(ym, from_real(dense_m[o].T @ as_real(x)), rtol=0, atol=1e-12 * np.abs(x).max())
+        yl = _rot_apply(b, offs, p, 0, zshift(zl, _rot_apply(f, offs, p, 0, x), False))
+        np.testing.assert_allclose(yl, from_real(dense_l[o].T @ as_real(x)), rtol=0, atol=1e-12 * np.abs(x).max())
