@@ -300,6 +300,55 @@ int rpy_bounding_cube_noalloc(const double *pos_dev, int64_t n, double *cube_dev
 /* Number of kernels this library has launched in this process (all devices). */
 int64_t rpy_launch_count(void);
 
+/* ------------------------------------------------------------------ serving
+ * A request loop for many resident Brownian-dynamics systems (the serving
+ * form): every system keeps its tree, expansions and bead buffers on the
+ * device between requests; requests (new positions and forces of one system)
+ * are admitted as worker slots and device memory allow, and several
+ * requests of different systems run at once on separate streams (continuous
+ * batching).  Requests of one system run in submission order.  Systems that
+ * do not fit the memory budget wait; idle resident systems are evicted
+ * (least recently used) to make room.  Host-side C++, one worker thread per
+ * slot.  All arrays here are HOST arrays owned by the caller; u_host must
+ * stay valid until the request completes.
+ */
+typedef struct rpy_server_s *rpy_server;
+
+typedef struct {
+    int64_t device_budget_bytes;   /* admission limit on resident bytes; 0 = 85% of free memory */
+    int slots;                     /* concurrent requests on the device; 0 = 4 */
+    int device;                    /* CUDA device; the caller's current device if < 0 */
+} rpy_server_params;
+
+typedef struct {
+    int64_t submitted, completed, failed, cancelled, evictions, rebuilds;
+    int64_t beads_done;            /* beads of completed requests */
+    int64_t resident_bytes, peak_resident_bytes;
+    int32_t resident_systems, queued, running;
+    double p50_ms, p99_ms, mean_ms;  /* latency submit -> completion of completed requests */
+    double busy_s;                   /* wall time from first submit to last completion */
+} rpy_server_stats;
+
+int rpy_server_create(const rpy_server_params *params, rpy_server *out);
+/* Register a system (host positions copied; the tree is built on first admission). */
+int rpy_server_add_system(rpy_server s, const double *pos_host, int64_t n, double a,
+                          const rpy_build_params *params, int *system_id);
+/* Enqueue u = D(pos) f for a system.  pos_host may be NULL (keep the last positions).
+ * Returns at once with a request id; the result lands in u_host. */
+int rpy_server_submit(rpy_server s, int system_id, const double *pos_host, const double *f_host,
+                      double kT_over_eta, double *u_host, int64_t *request_id);
+/* Wait for a request; timeout_ms < 0 waits forever.  Returns the request's own
+ * status (RPY_OK, an error of its computation, RPY_ERR_STATE if cancelled) or
+ * RPY_ERR_TIMEOUT if it is still pending.  latency_ms may be NULL. */
+int rpy_server_wait(rpy_server s, int64_t request_id, int timeout_ms, double *latency_ms);
+/* Cancel a request that has not started; RPY_ERR_STATE if it already started or finished. */
+int rpy_server_cancel(rpy_server s, int64_t request_id);
+/* Wait until every submitted request has finished. */
+int rpy_server_drain(rpy_server s);
+int rpy_server_stats_get(rpy_server s, rpy_server_stats *out);
+/* Stop the workers (pending requests are cancelled) and free every resident system. */
+void rpy_server_destroy(rpy_server s);
+
 /* Library version (major * 10000 + minor * 100 + patch). */
 int rpy_version(void);
 

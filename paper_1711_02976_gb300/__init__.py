@@ -42,7 +42,9 @@ EXPORTED_SYMBOLS = [
     "rpy_matvec_parts", "rpy_matvec_oneshot", "rpy_matvec_host", "rpy_laplace_far", "rpy_tree_export",
     "rpy_tree_stats", "rpy_tree_sync", "rpy_tree_footprint", "rpy_tree_free", "rpy_strerror",
     "rpy_last_cuda_error", "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times",
-    "rpy_launch_count", "rpy_alu_peak", "rpy_bounding_cube_noalloc",
+    "rpy_launch_count", "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_server_create", "rpy_server_add_system",
+    "rpy_server_submit", "rpy_server_wait", "rpy_server_cancel", "rpy_server_drain", "rpy_server_stats_get",
+    "rpy_server_destroy",
 ]
 STAGES = ["gather", "p2p", "p2m", "m2m", "m2x", "x2x", "x2l", "p2l", "l2l", "eval", "combine"]
 
@@ -71,6 +73,22 @@ class RpyStats(ctypes.Structure):
                 ("n_wlist", ctypes.c_int64), ("n_xlist", ctypes.c_int64), ("n_vpairs", ctypes.c_int64),
                 ("n_dlist", ctypes.c_int64), ("d_pairs", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("cancelled", ctypes.c_int64), ("evictions", ctypes.c_int64), ("rebuilds", ctypes.c_int64),
+                ("beads_done", ctypes.c_int64), ("resident_bytes", ctypes.c_int64),
+                ("peak_resident_bytes", ctypes.c_int64), ("resident_systems", ctypes.c_int32),
+                ("queued", ctypes.c_int32), ("running", ctypes.c_int32), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("busy_s", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -117,12 +135,21 @@ def load(build_if_missing: bool = True):
             "rpy_launch_count": [],
             "rpy_alu_peak": [i, ctypes.POINTER(d), vp],
             "rpy_bounding_cube_noalloc": [vp, i64, vp, vp],
+            "rpy_server_create": [ctypes.POINTER(ServerParams), ctypes.POINTER(vp)],
+            "rpy_server_add_system": [vp, vp, i64, d, ctypes.POINTER(BuildParams), ctypes.POINTER(i)],
+            "rpy_server_submit": [vp, i, vp, vp, d, vp, ctypes.POINTER(i64)],
+            "rpy_server_wait": [vp, i64, i, ctypes.POINTER(d)],
+            "rpy_server_cancel": [vp, i64],
+            "rpy_server_drain": [vp],
+            "rpy_server_stats_get": [vp, ctypes.POINTER(ServerStats)],
+            "rpy_server_destroy": [vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
         lib.rpy_tree_free.restype = None
+        lib.rpy_server_destroy.restype = None
         lib.rpy_launch_count.restype = ctypes.c_int64
         lib.rpy_strerror.restype = ctypes.c_char_p
         lib.rpy_last_cuda_error.restype = ctypes.c_char_p
@@ -354,3 +381,61 @@ def rpy_bounding_cube_noalloc(pos, n, cube, stream=None):
     device array cube (4 doubles), with no device allocation in the library."""
     _check(load().rpy_bounding_cube_noalloc(_dev_f64(pos, "pos"), int(n), _dev_f64(cube, "cube"), _stream(stream)),
            "rpy_bounding_cube_noalloc")
+
+
+# ---------------------------------------------------------------- serving
+
+def rpy_server_create(device_budget_bytes=0, slots=0, device=-1) -> int:
+    h = ctypes.c_void_p()
+    prm = ServerParams(int(device_budget_bytes), int(slots), int(device))
+    _check(load().rpy_server_create(ctypes.byref(prm), ctypes.byref(h)), "rpy_server_create")
+    return h.value
+
+
+def rpy_server_add_system(server, pos, a, digits, precision=RPY_FP64, leaf_cap=0, order_p=0) -> int:
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    prm = BuildParams(int(digits), int(precision), int(leaf_cap), int(order_p), 0, 0, 0, 0)
+    sid = ctypes.c_int()
+    _check(load().rpy_server_add_system(ctypes.c_void_p(server), pos.ctypes.data, pos.shape[0], float(a),
+                                        ctypes.byref(prm), ctypes.byref(sid)), "rpy_server_add_system")
+    return sid.value
+
+
+def rpy_server_submit(server, system_id, pos, f, kT_over_eta, u) -> int:
+    """pos: host (N, 3) float64 or None; f: host (N, 3); u: host (N, 3) written on completion
+    (the caller keeps u alive until rpy_server_wait returns)."""
+    if pos is not None:
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    if not (isinstance(u, np.ndarray) and u.dtype == np.float64 and u.flags["C_CONTIGUOUS"]):
+        raise ValueError("u must be a C-contiguous float64 numpy array")
+    rid = ctypes.c_int64()
+    _check(load().rpy_server_submit(ctypes.c_void_p(server), int(system_id), pos.ctypes.data if pos is not None else None,
+                                    f.ctypes.data, float(kT_over_eta), u.ctypes.data, ctypes.byref(rid)),
+           "rpy_server_submit")
+    return rid.value
+
+
+def rpy_server_wait(server, request_id, timeout_ms=-1):
+    """Returns (status, latency_ms); status 0 on success (errors are returned, not raised)."""
+    lat = ctypes.c_double()
+    st = load().rpy_server_wait(ctypes.c_void_p(server), int(request_id), int(timeout_ms), ctypes.byref(lat))
+    return st, lat.value
+
+
+def rpy_server_cancel(server, request_id) -> int:
+    return load().rpy_server_cancel(ctypes.c_void_p(server), int(request_id))
+
+
+def rpy_server_drain(server):
+    _check(load().rpy_server_drain(ctypes.c_void_p(server)), "rpy_server_drain")
+
+
+def rpy_server_stats_get(server) -> dict:
+    st = ServerStats()
+    _check(load().rpy_server_stats_get(ctypes.c_void_p(server), ctypes.byref(st)), "rpy_server_stats_get")
+    return st.as_dict()
+
+
+def rpy_server_destroy(server):
+    load().rpy_server_destroy(ctypes.c_void_p(server))

@@ -254,6 +254,15 @@ static int have_device() {
     return RPY_OK;
 }
 
+// Completion tracking: an event owned by the tree, recorded after each call.
+static void mark_done(Tree &t, cudaStream_t st) {
+    if (!t.done) cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
+    cudaEventRecord(t.done, st);
+    t.last_stream = st;
+}
+
+static cudaError_t wait_done(Tree &t) { return t.done ? cudaEventSynchronize(t.done) : cudaSuccess; }
+
 static bool valid(rpy_tree t) { return t && t->magic == 0x52505954u; }
 
 static int alloc_tree_arrays(Tree &t, cudaStream_t st) {
@@ -291,6 +300,7 @@ int tree_alloc_workspace(Tree &t, cudaStream_t) {
 
 static int do_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     auto t0 = std::chrono::steady_clock::now();
+    t.built = false;
     RPY_TRY(alloc_tree_arrays(t, st));
     RPY_TRY(tree_build(t, pos_dev, st));
     OpTables *h = nullptr;
@@ -302,8 +312,9 @@ static int do_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     t.dt32 = ds->d32;
     RPY_TRY(tree_alloc_workspace(t, st));
     RPY_CHECK(cudaStreamSynchronize(st));
-    t.last_stream = st;
+    mark_done(t, st);
     t.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    t.built = true;
     return RPY_OK;
 }
 
@@ -320,6 +331,7 @@ static int upload_s(Tree &t, const double *s_host, cudaStream_t st) {
 }
 
 int run_matvec(Tree &t, const double *f_dev, const double *s_host, double *u_dev, int parts, cudaStream_t st) {
+    if (!t.built) return RPY_ERR_STATE;
     RPY_TRY(upload_s(t, s_host, st));
     SysConst sc{t.sys_cube, t.sys_a, t.sys_s};
     for (int k = 0; k < 16; ++k) t.ev_used[k] = false;
@@ -342,11 +354,12 @@ int run_matvec(Tree &t, const double *f_dev, const double *s_host, double *u_dev
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     prof_mark(t, RPY_NUM_STAGES, st);
-    t.last_stream = st;
+    mark_done(t, st);
     return RPY_OK;
 }
 
 int run_laplace_far(Tree &t, const double *q_dev, double *out_dev, cudaStream_t st) {
+    if (!t.built) return RPY_ERR_STATE;
     if (!t.lap_q) {
         RPY_TRY(dev_alloc(t, (void **)&t.lap_q, sizeof(double) * 4 * t.n));
     }
@@ -368,7 +381,7 @@ int run_laplace_far(Tree &t, const double *q_dev, double *out_dev, cudaStream_t 
         if (e != cudaSuccess) s = check_cuda("laplace far", e);
     }
     tree_release(scratch);
-    t.last_stream = st;
+    mark_done(t, st);
     return s;
 }
 
@@ -462,8 +475,9 @@ int rpy_tree_update_positions(rpy_tree h, const double *pos_dev, void *stream) {
     if (!valid(h) || !pos_dev) return RPY_ERR_INVALID;
     Tree &t = h->t;
     DeviceGuard g(t.device);
-    cudaStreamSynchronize(t.last_stream);
-    // keep handle-level settings, rebuild every device structure
+    wait_done(t);
+    // keep handle-level settings and the device blocks (as a cache), rebuild the structures
+    tree_recycle(t);
     Tree fresh;
     fresh.device = t.device;
     fresh.n = t.n;
@@ -473,10 +487,13 @@ int rpy_tree_update_positions(rpy_tree h, const double *pos_dev, void *stream) {
     fresh.direct_w = t.direct_w;
     fresh.direct_x = t.direct_x;
     fresh.prof = t.prof;
+    for (int k = 0; k < 16; ++k) fresh.ev[k] = t.ev[k];
+    fresh.done = t.done;
     fresh.sys_off_h = t.sys_off_h;
     fresh.a_h = t.a_h;
-    tree_release(t);
-    t = fresh;
+    fresh.cache = std::move(t.cache);
+    fresh.device_bytes = t.device_bytes;
+    t = std::move(fresh);
     return do_build(t, pos_dev, static_cast<cudaStream_t>(stream));
 }
 
@@ -551,7 +568,7 @@ int rpy_tree_sync(rpy_tree h) {
     if (!valid(h)) return RPY_ERR_INVALID;
     Tree &t = h->t;
     DeviceGuard g(t.device);
-    cudaError_t e = cudaStreamSynchronize(t.last_stream);
+    cudaError_t e = wait_done(t);
     if (e != cudaSuccess) return check_cuda("sync", e);
     unsigned status = 0;
     RPY_CHECK(cudaMemcpy(&status, t.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
@@ -586,7 +603,7 @@ int rpy_tree_export(rpy_tree h, int field, void *dst, int64_t capacity, int64_t 
         case RPY_FIELD_X_IDX: src = t.x_idx; bytes = 4 * t.n_x; break;
         case RPY_FIELD_V_OFF:
         case RPY_FIELD_V_IDX:
-            RPY_TRY(tree_build_vlists(t, t.last_stream));
+            RPY_TRY(tree_build_vlists(t, nullptr));   // debug export: legacy stream, synchronous
             src = field == RPY_FIELD_V_OFF ? (const void *)t.v_off : (const void *)t.v_idx;
             bytes = field == RPY_FIELD_V_OFF ? 4 * int64_t(t.nbox + 1) : 4 * t.n_v;
             break;
@@ -652,7 +669,8 @@ int rpy_tree_footprint(int64_t n, int digits, int precision, int leaf_cap, int64
     double es = precision == RPY_FP32 ? 8.0 : 16.0;
     // boxes: leaves ~ 2n/cap on clustered data, plus internal boxes (< leaves/7 * 8)
     double nbox = 4.0 * double(n) / double(leaf_cap) + 64.0;
-    double per_box = es * (2.0 * kSets * ncoef(p) + 2.0 * kDirs * kSets * q.half()) + 4.0 * (8 + 27 + 3 + 12) + 32.0;
+    double per_box = es * (2.0 * kSets * ncoef(p) + 2.0 * kDirs * kSets * q.half() + 18.0 * ncoef(p)) +
+                     4.0 * (8 + 27 + 3 + 12) + 32.0;
     double per_bead = 3 * 8 /*pos*/ + 8 /*key*/ + 4 + 4 + 9 * 8 /*fs, unear, ufar*/ + 27 * 4 /*U list share*/;
     *bytes = int64_t(nbox * per_box + double(n) * per_bead + 32.0 * 1024 * 1024);
     return RPY_OK;
@@ -663,10 +681,11 @@ void rpy_tree_free(rpy_tree h) {
     Tree &t = h->t;
     {
         DeviceGuard g(t.device);
-        cudaStreamSynchronize(t.last_stream);
+        wait_done(t);
         tree_release(t);
         for (int k = 0; k < 16; ++k)
             if (t.ev[k]) cudaEventDestroy(t.ev[k]);
+        if (t.done) cudaEventDestroy(t.done);
     }
     h->magic = 0;
     delete h;
@@ -682,7 +701,7 @@ int rpy_tree_stage_times(rpy_tree h, double *ms, int n) {
     if (!valid(h) || !ms || n < 0) return RPY_ERR_INVALID;
     Tree &t = h->t;
     DeviceGuard g(t.device);
-    RPY_CHECK(cudaStreamSynchronize(t.last_stream));   // NULL is the legacy default stream
+    RPY_CHECK(wait_done(t));
     for (int k = 0; k < n; ++k) {
         ms[k] = 0.0;
         if (k >= RPY_NUM_STAGES || !t.ev_used[k]) continue;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -149,6 +150,7 @@ struct DevTables {
 
 struct Tree {
     int device = 0;
+    bool built = false;               // false while (or after a failed) build
     cudaStream_t last_stream = nullptr;
     int64_t n = 0;
     int nsys = 0;
@@ -209,10 +211,17 @@ struct Tree {
     void *dtabs_mem = nullptr;        // one device block holding all tables
     DevTables<double> dt64{};
     DevTables<float> dt32{};
-    // scratch for builds
-    std::vector<void *> allocs;       // every cudaMalloc of the handle
+    // device memory: blocks in use, and free blocks kept for the next rebuild
+    struct Block {
+        void *p;
+        size_t bytes;
+    };
+    std::vector<Block> allocs;
+    std::multimap<size_t, void *> cache;
+    Tree *owner = nullptr;            // scratch trees take from and return to their owner's cache
     // per-stage profiling (events recorded between stages when enabled)
     bool prof = false;
+    cudaEvent_t done = nullptr;       // recorded after every asynchronous call (survives the caller's stream)
     cudaEvent_t ev[16] = {};
     bool ev_used[16] = {};
 };
@@ -228,7 +237,8 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st);
 int tree_alloc_workspace(Tree &t, cudaStream_t st);
 int tree_upload_tables(Tree &t, cudaStream_t st);
 int tree_build_vlists(Tree &t, cudaStream_t st);
-void tree_release(Tree &t);
+void tree_release(Tree &t);     // owner: free everything; scratch: return blocks to the owner
+void tree_recycle(Tree &t);     // move every block in use into the cache
 int dev_alloc(Tree &t, void **p, size_t bytes);
 
 // per-system constants seen by the kernels

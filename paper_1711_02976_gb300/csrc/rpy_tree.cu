@@ -45,30 +45,63 @@ const char *last_cuda_error_text() { return g_last_err.c_str(); }
 
 int dev_alloc(Tree &t, void **p, size_t bytes) {
     *p = nullptr;
+    Tree &P = t.owner ? *t.owner : t;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    bytes = (bytes + 255) & ~size_t(255);
+    auto it = P.cache.lower_bound(bytes);
+    if (it != P.cache.end() && it->first <= 2 * bytes + (size_t(1) << 20)) {
+        *p = it->second;
+        t.allocs.push_back({it->second, it->first});
+        P.cache.erase(it);
+        return RPY_OK;
+    }
+    size_t sz = bytes + bytes / 8;   // slack so that a slightly larger rebuild reuses the block
+    cudaError_t e = cudaMalloc(p, sz);
+    if (e == cudaErrorMemoryAllocation && !P.cache.empty()) {
+        // give the cached blocks back to the device and retry once
+        cudaGetLastError();
+        for (auto &kv : P.cache) {
+            cudaFree(kv.second);
+            P.device_bytes -= int64_t(kv.first);
+        }
+        P.cache.clear();
+        e = cudaMalloc(p, sz);
+    }
     if (e != cudaSuccess) {
         *p = nullptr;
         return check_cuda("cudaMalloc", e);
     }
-    t.allocs.push_back(*p);
-    t.device_bytes += int64_t(bytes);
+    t.allocs.push_back({*p, sz});
+    P.device_bytes += int64_t(sz);
     return RPY_OK;
 }
 
 static void dev_free(Tree &t, void *p) {
     if (!p) return;
+    Tree &P = t.owner ? *t.owner : t;
     for (size_t i = 0; i < t.allocs.size(); ++i)
-        if (t.allocs[i] == p) {
+        if (t.allocs[i].p == p) {
+            P.cache.insert({t.allocs[i].bytes, p});
             t.allocs.erase(t.allocs.begin() + i);
-            break;
+            return;
         }
-    cudaFree(p);
+}
+
+void tree_recycle(Tree &t) {
+    Tree &P = t.owner ? *t.owner : t;
+    for (auto &b : t.allocs) P.cache.insert({b.bytes, b.p});
+    t.allocs.clear();
 }
 
 void tree_release(Tree &t) {
-    for (void *p : t.allocs) cudaFree(p);
+    if (t.owner) {
+        tree_recycle(t);
+        return;
+    }
+    for (auto &b : t.allocs) cudaFree(b.p);
+    for (auto &kv : t.cache) cudaFree(kv.second);
     t.allocs.clear();
+    t.cache.clear();
     t.device_bytes = 0;
 }
 
@@ -707,7 +740,6 @@ static int grow_boxes(Tree &t, int need, cudaStream_t st) {
         RPY_TRY(dev_alloc(t, &np, f.es * f.per * size_t(cap)));
         if (*f.p) {
             RPY_CHECK(cudaMemcpyAsync(np, *f.p, f.es * f.per * size_t(t.nbox), cudaMemcpyDeviceToDevice, st));
-            t.device_bytes -= int64_t(f.es * f.per * size_t(t.nbox_cap));
             dev_free(t, *f.p);
         }
         *f.p = np;
@@ -733,8 +765,9 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     }
     sco[nsys] = int(cb.size());
     int nch = int(cb.size());
-    // scratch for the build (freed at the end)
+    // scratch for the build (returned to the tree's block cache at the end)
     Tree scratch;
+    scratch.owner = &t;
     int64_t *d_cb, *d_ce;
     int *d_sco;
     double *d_part;
@@ -1069,6 +1102,7 @@ int tree_build_vlists(Tree &t, cudaStream_t st) {
     if (t.v_off) return RPY_OK;
     int nbx = t.nbox;
     Tree scratch;
+    scratch.owner = &t;
     int *vcnt;
     void *stmp;
     size_t sbytes = scan_tmp_bytes(nbx + 1);

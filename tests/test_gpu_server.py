@@ -1,0 +1,106 @@
+"""Serving loop: resident systems, continuous batching across worker streams,
+admission by device-memory budget with eviction, per-request failures and
+cancellation.  Every result must equal the same system's result computed
+alone (bitwise: the kernels are deterministic and a request touches only its
+own system's buffers)."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import paper_1711_02976_gb300 as rp
+import synth
+from gpu_util import matvec
+
+pytestmark = pytest.mark.gpu
+
+
+def _systems(seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k, n in enumerate([3000, 12000, 800, 25000, 5000]):
+        pos = rng.random((n, 3)) if k % 2 == 0 else synth._sphere_surface(rng, n, 0.5, (0.5, 0.5, 0.5))
+        a = 0.5 / n ** (1 / 3) * 0.3
+        out.append((pos, a, 3 if k % 2 == 0 else 6, 1 if k % 2 == 0 else 0))
+    return out
+
+
+def test_results_in_the_mix_equal_results_alone():
+    rng = np.random.default_rng(1)
+    systems = _systems()
+    srv = rp.rpy_server_create(slots=3)
+    try:
+        ids = [rp.rpy_server_add_system(srv, pos, a, d, precision=prec) for pos, a, d, prec in systems]
+        jobs = []
+        for r in range(30):
+            k = int(rng.integers(len(systems)))
+            pos, a, d, prec = systems[k]
+            newpos = pos + 1e-3 * rng.standard_normal(pos.shape) if r % 3 else None
+            f = rng.standard_normal(pos.shape)
+            u = np.zeros_like(f)
+            rid = rp.rpy_server_submit(srv, ids[k], newpos, f, 6 * math.pi * a, u)
+            jobs.append((rid, k, newpos, f, u))
+        last_pos = [s[0] for s in systems]
+        for rid, k, newpos, f, u in jobs:
+            st, lat = rp.rpy_server_wait(srv, rid)
+            assert st == 0 and lat > 0
+            pos, a, d, prec = systems[k]
+            if newpos is not None:
+                last_pos[k] = newpos
+            ref, _ = matvec(last_pos[k], f, a, 6 * math.pi * a, d, precision=prec)
+            np.testing.assert_array_equal(u, ref)
+        stats = rp.rpy_server_stats_get(srv)
+        assert stats["completed"] == 30 and stats["failed"] == 0 and stats["p99_ms"] >= stats["p50_ms"] > 0
+    finally:
+        rp.rpy_server_destroy(srv)
+
+
+def test_admission_budget_evicts_and_serves_everything():
+    rng = np.random.default_rng(2)
+    systems = _systems(3)
+    fps = [rp.rpy_tree_footprint(len(p), d, prec) for p, a, d, prec in systems]
+    budget = max(fps) + min(fps)          # never all resident at once
+    srv = rp.rpy_server_create(device_budget_bytes=budget, slots=2)
+    try:
+        ids = [rp.rpy_server_add_system(srv, pos, a, d, precision=prec) for pos, a, d, prec in systems]
+        jobs = []
+        for r in range(20):
+            k = r % len(systems)
+            pos, a, d, prec = systems[k]
+            f = rng.standard_normal(pos.shape)
+            u = np.zeros_like(f)
+            jobs.append((rp.rpy_server_submit(srv, ids[k], None, f, 1.0, u), k, f, u))
+        for rid, k, f, u in jobs:
+            assert rp.rpy_server_wait(srv, rid)[0] == 0
+            pos, a, d, prec = systems[k]
+            ref, _ = matvec(pos, f, a, 1.0, d, precision=prec)
+            np.testing.assert_array_equal(u, ref)
+        st = rp.rpy_server_stats_get(srv)
+        assert st["evictions"] > 0 and st["peak_resident_bytes"] <= budget * 1.5
+    finally:
+        rp.rpy_server_destroy(srv)
+
+
+def test_poisoned_request_fails_alone_and_cancel():
+    rng = np.random.default_rng(4)
+    pos, a, d, prec = _systems()[0]
+    srv = rp.rpy_server_create(slots=1)
+    try:
+        sid = rp.rpy_server_add_system(srv, pos, a, d, precision=prec)
+        bad = pos.copy()
+        bad[5, 0] = np.nan
+        f = rng.standard_normal(pos.shape)
+        u_bad, u_ok, u_c = np.zeros_like(f), np.zeros_like(f), np.zeros_like(f)
+        r_bad = rp.rpy_server_submit(srv, sid, bad, f, 1.0, u_bad)
+        r_ok = rp.rpy_server_submit(srv, sid, pos, f, 1.0, u_ok)
+        r_c = rp.rpy_server_submit(srv, sid, None, f, 1.0, u_c)
+        cancelled = rp.rpy_server_cancel(srv, r_c) == 0
+        assert rp.rpy_server_wait(srv, r_bad)[0] == -6          # non-finite positions
+        assert rp.rpy_server_wait(srv, r_ok)[0] == 0             # the system recovers
+        ref, _ = matvec(pos, f, a, 1.0, d, precision=prec)
+        np.testing.assert_array_equal(u_ok, ref)
+        st_c = rp.rpy_server_wait(srv, r_c)[0]
+        assert st_c == (-7 if cancelled else 0)
+    finally:
+        rp.rpy_server_destroy(srv)
