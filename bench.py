@@ -44,6 +44,9 @@ CONFIGS = {
                                  desc="4,096 beads uniform cube, a=0.004, 3-digit, FP64, leaf cap 40"),
     "cube15m_3digit_fp32": dict(gen="config3", digits=3, precision=1, leaf_cap=0,
                                 desc="15,000,000 beads uniform cube, a=2e-5, 3-digit, FP32 precision form"),
+    "batch256_3digit_fp32": dict(gen="config4", digits=3, precision=1, leaf_cap=0,
+                                 desc="256 systems in one forest, sizes log-uniform 1e3..2e5 (seed 4), uniform "
+                                      "cube or Plummer cluster, a=0.5/N^(1/3), 3-digit, FP32 precision form"),
 }
 DEFAULT = "sphere1m_6digit_fp64"
 
@@ -104,9 +107,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class Forest:
+    """Many systems concatenated (caller order = system order)."""
+
+    def __init__(self, systems):
+        self.systems = systems
+        self.pos = np.concatenate([sy.pos for sy in systems])
+        self.f = np.concatenate([sy.f for sy in systems])
+        self.off = np.concatenate([[0], np.cumsum([sy.n for sy in systems])]).astype(np.int64)
+        self.a_list = [sy.a for sy in systems]
+        self.s_list = [sy.s for sy in systems]
+        self.n = int(self.off[-1])
+
+
 def make_workload(name):
     import synth
-    return getattr(synth, CONFIGS[name]["gen"])()
+    w = getattr(synth, CONFIGS[name]["gen"])()
+    return Forest(w) if isinstance(w, list) else w
 
 
 def flops_model(stats, stage):
@@ -121,32 +138,35 @@ def flops_model(stats, stage):
     return None
 
 
-def run_ours(args, ws, rank, local):
+def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profile=True):
     import torch
     import paper_1711_02976_gb300 as rp
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = CONFIGS[args.config]
-    sysm = make_workload(args.config)
+    config = config or args.config
+    steps = steps or args.steps
+    warmup = args.warmup if warmup is None else warmup
+    cfg = CONFIGS[config]
+    sysm = make_workload(config)
+    forest = isinstance(sysm, Forest)
     n = sysm.n
     P = torch.from_numpy(sysm.pos).to(dev)
     F = torch.from_numpy(sysm.f).to(dev)
     U = torch.empty_like(F)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    if forest:
+        tree = rp.rpy_forest_build(P, sysm.off, sysm.a_list, cfg["digits"], leaf_cap=cfg["leaf_cap"],
+                                   precision=cfg["precision"])
+        matvec = lambda: rp.rpy_forest_matvec(tree, F, sysm.s_list, U)
+    else:
+        tree = rp.rpy_tree_build(P, n, sysm.a, cfg["digits"], leaf_cap=cfg["leaf_cap"], precision=cfg["precision"])
+        matvec = lambda: rp.rpy_matvec(tree, F, sysm.s, U)
 
-    def build():
-        return rp.rpy_tree_build(P, n, sysm.a, cfg["digits"], leaf_cap=cfg["leaf_cap"], precision=cfg["precision"])
-
-    tree = build()
-
-    def step():
+    for _ in range(warmup):
         rp.rpy_tree_update_positions(tree, P)
-        rp.rpy_matvec(tree, F, sysm.s, U)
-
-    for _ in range(args.warmup):
-        step()
+        matvec()
     torch.cuda.synchronize()
     if ws > 1:
         import torch.distributed as dist
@@ -155,20 +175,20 @@ def run_ours(args, ws, rank, local):
     sampler.start()
     launches0 = rp.rpy_launch_count()
     times, tb, tm = [], [], []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         rp.rpy_tree_update_positions(tree, P)
         e1.record(stream)
-        rp.rpy_matvec(tree, F, sysm.s, U)
+        matvec()
         e2.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e2))
         tb.append(e0.elapsed_time(e1))
         tm.append(e1.elapsed_time(e2))
-    launches = (rp.rpy_launch_count() - launches0) // max(1, args.steps)
+    launches = (rp.rpy_launch_count() - launches0) // max(1, steps)
     clocks = sampler.stop()
     ms = sum(times) / len(times)
     if ws > 1:
@@ -180,34 +200,50 @@ def run_ours(args, ws, rank, local):
     value = ws * n / (ms * 1e-3) / 1e6
     stats = rp.rpy_tree_stats(tree)
 
-    # stage profile of one matvec (separate, untimed for the headline)
-    rp.rpy_tree_set_profiling(tree, True)
-    prof = []
+    # repeated matvecs on the resident tree (the Krylov use), replayed as a CUDA graph
+    reps = []
     for _ in range(3):
         flush.zero_()
-        rp.rpy_matvec(tree, F, sysm.s, U)
-        prof.append(rp.rpy_tree_stage_times(tree))
-    rp.rpy_tree_set_profiling(tree, False)
-    stage_ms = {k: statistics.median(p[k] for p in prof) for k in prof[0]}
+        torch.cuda.synchronize()
+        e1, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e1.record(stream)
+        matvec()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        reps.append(e1.elapsed_time(e2))
+    stage_ms = {}
+    if profile:
+        rp.rpy_tree_set_profiling(tree, True)
+        prof = []
+        for _ in range(3):
+            flush.zero_()
+            matvec()
+            prof.append(rp.rpy_tree_stage_times(tree))
+        rp.rpy_tree_set_profiling(tree, False)
+        stage_ms = {k: statistics.median(p[k] for p in prof) for k in prof[0]}
+    matvec()
+    torch.cuda.synchronize()
     u_dev = U.cpu().numpy()
 
     result = {
-        "metric": METRIC, "value": round(value, 4), "unit": "Mbeads/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": round(value, 4), "unit": "Mbeads/s", "n_gpus": ws, "steps": steps,
+        "warmup": warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if cfg["precision"] == 0 else "f32+f64",
         "data": "synthetic (seeded numpy; shapes of the paper's sphere/cube workloads)",
-        "config": {"workload": args.config, "description": cfg["desc"], "n_beads": n, "digits": cfg["digits"],
+        "config": {"workload": config, "description": cfg["desc"], "n_beads": n, "digits": cfg["digits"],
                    "precision": "fp64" if cfg["precision"] == 0 else "fp32", "parallelism": f"replicas x{ws}",
                    "l2": "flushed between timed steps (256 MB write)", "step": "tree build + matvec",
                    "leaf_cap": stats["leaf_cap"], "order_p": stats["order_p"], "exp_terms": stats["exp_terms"]},
         "build_ms": round(statistics.median(tb), 4), "matvec_ms": round(statistics.median(tm), 4),
         "matvec_only_mbeads_s": round(ws * n / (statistics.median(tm) * 1e-3) / 1e6, 4),
+        "resident_tree_matvec_ms": round(statistics.median(reps), 4),
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-        "tree": {k: stats[k] for k in ("n_boxes", "n_leaves", "depth", "u_pairs", "d_pairs", "n_wlist", "n_xlist",
-                                       "n_dlist", "max_leaf_count", "leaves_over_cap", "device_bytes")},
+        "tree": {k: stats[k] for k in ("n_systems", "n_boxes", "n_leaves", "depth", "u_pairs", "d_pairs", "n_wlist",
+                                       "n_xlist", "n_dlist", "max_leaf_count", "leaves_over_cap", "device_bytes")},
         "gpu_launches": int(launches), "clocks": clocks,
     }
-    return result, sysm, u_dev, stats, stage_ms, tree
+    tree.close()
+    return result, sysm, u_dev, stats, stage_ms, None
 
 
 def roofline(result, stats, stage_ms, peaks):
@@ -225,8 +261,10 @@ def roofline(result, stats, stage_ms, peaks):
 
 
 def e2e_host(args, sysm, cfg):
-    """The same matvec through the host-array entry point: H2D of positions and
-    forces from pinned memory, build, matvec, D2H of velocities, every step."""
+    """The same work through the public API with host data: H2D of positions
+    and forces from pinned memory, build, matvec, D2H of velocities, every step
+    (rpy_matvec_host for one system; for a forest the binding calls
+    rpy_forest_build, rpy_forest_matvec and the copies)."""
     import torch
     import paper_1711_02976_gb300 as rp
     n = sysm.n
@@ -234,13 +272,28 @@ def e2e_host(args, sysm, cfg):
     f_h = torch.from_numpy(sysm.f).pin_memory()
     u_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     lib = rp.load()
+    if isinstance(sysm, Forest):
+        P = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        F = torch.empty_like(P)
+        U = torch.empty_like(P)
 
-    def call():
-        st = lib.rpy_matvec_host(pos_h.data_ptr(), n, sysm.a, f_h.data_ptr(), sysm.s, cfg["digits"], cfg["precision"],
-                                 u_h.data_ptr(), rp._stream(None))
-        if st:
-            raise rp.RpyError(st, "rpy_matvec_host")
-
+        def call():
+            P.copy_(pos_h, non_blocking=True)
+            F.copy_(f_h, non_blocking=True)
+            t = rp.rpy_forest_build(P, sysm.off, sysm.a_list, cfg["digits"], leaf_cap=cfg["leaf_cap"],
+                                    precision=cfg["precision"])
+            rp.rpy_forest_matvec(t, F, sysm.s_list, U)
+            u_h.copy_(U, non_blocking=True)
+            torch.cuda.synchronize()
+            t.close()
+        api = "rpy_forest_build + rpy_forest_matvec (pinned host arrays in, velocities out)"
+    else:
+        def call():
+            st = lib.rpy_matvec_host(pos_h.data_ptr(), n, sysm.a, f_h.data_ptr(), sysm.s, cfg["digits"],
+                                     cfg["precision"], u_h.data_ptr(), rp._stream(None))
+            if st:
+                raise rp.RpyError(st, "rpy_matvec_host")
+        api = "rpy_matvec_host (pinned host arrays in, velocities out)"
     for _ in range(2):
         call()
     torch.cuda.synchronize()
@@ -252,19 +305,113 @@ def e2e_host(args, sysm, cfg):
         ts.append(time.perf_counter() - t0)
     t = statistics.median(ts)
     return {"value": round(n / t / 1e6, 4), "unit": "Mbeads/s", "h2d_bytes_per_step": 2 * n * 3 * 8,
-            "d2h_bytes_per_step": n * 3 * 8, "ms_per_step": round(t * 1e3, 3),
-            "api": "rpy_matvec_host (pinned host arrays in, velocities out)"}
+            "d2h_bytes_per_step": n * 3 * 8, "ms_per_step": round(t * 1e3, 3), "api": api}
 
 
 def cpu_oracle_sample(sysm, k):
+    """Oracle velocities on k sampled targets (for a forest: spread over the
+    systems, each against its own system)."""
     import oracle
     import synth
-    tg = synth.sample_targets(sysm.n, k)
     th = oracle.default_threads()
+    if isinstance(sysm, Forest):
+        rng = np.random.default_rng(12345)
+        pick = rng.choice(len(sysm.systems), min(len(sysm.systems), 32), replace=False)
+        per = max(1, k // len(pick))
+        tg, refs, dt = [], [], 0.0
+        for j in sorted(pick):
+            sy = sysm.systems[j]
+            loc = synth.sample_targets(sy.n, per)
+            t0 = time.perf_counter()
+            refs.append(oracle.rpy_direct(sy.pos, sy.f, sy.a, sy.s, targets=loc, threads=th))
+            dt += time.perf_counter() - t0
+            tg.append(sysm.off[j] + loc)
+        return np.concatenate(tg), np.concatenate(refs), dt, th
+    tg = synth.sample_targets(sysm.n, k)
     t0 = time.perf_counter()
     ref = oracle.rpy_direct(sysm.pos, sysm.f, sysm.a, sysm.s, targets=tg, threads=th)
     dt = time.perf_counter() - t0
     return tg, ref, dt, th
+
+
+def self_term(sysm, tg):
+    if isinstance(sysm, Forest):
+        sysid = np.searchsorted(sysm.off, tg, side="right") - 1
+        c = np.array([sysm.s_list[j] / (6 * math.pi * sysm.a_list[j]) for j in sysid])
+        return c[:, None] * sysm.f[tg]
+    return sysm.s / (6 * math.pi * sysm.a) * sysm.f[tg]
+
+
+def precision_form(args, local, sysm_cfg):
+    """The FP32 precision form on the same workload and digit setting."""
+    cfg = dict(CONFIGS[sysm_cfg])
+    name = sysm_cfg + "__fp32"
+    CONFIGS[name] = dict(cfg, precision=1, desc=cfg["desc"].replace("FP64", "FP32 precision form"))
+    res, sysm, u, stats, stage_ms, _ = run_ours(args, 1, 0, local, config=name, steps=3, warmup=2, profile=False)
+    return res, sysm, u
+
+
+def serve(args, local):
+    """Serving form: Poisson requests from resident systems (sizes log-uniform
+    1e4..2e6, cube or sphere, jittered positions and fresh forces per request,
+    50/50 3-digit FP32 / 6-digit FP64), admitted by device-memory footprint."""
+    import torch
+    import paper_1711_02976_gb300 as rp
+    import synth
+    torch.cuda.set_device(local)
+    systems = synth.config5(nsys=args.serve_systems)
+    rng = np.random.default_rng(55)
+    srv = rp.rpy_server_create(slots=args.serve_slots)
+    kinds = []
+    for k, sy in enumerate(systems):
+        d, prec = (3, 1) if k % 2 == 0 else (6, 0)
+        kinds.append((d, prec))
+        rp.rpy_server_add_system(srv, sy.pos, sy.a, d, precision=prec)
+
+    def run(n_req, rate, order=None):
+        outs, t_next = [], time.perf_counter()
+        for r in range(n_req):
+            k = order[r] if order is not None else int(rng.integers(len(systems)))
+            sy = systems[k]
+            pos = synth.jitter(rng, sy.pos)
+            f = rng.standard_normal(sy.pos.shape)
+            u = np.zeros_like(f)
+            if rate:
+                t_next += rng.exponential(1.0 / rate)
+                while time.perf_counter() < t_next:
+                    time.sleep(0.0005)
+            outs.append((rp.rpy_server_submit(srv, k, pos, f, sy.s, u), sy.n, u))
+        t0 = time.perf_counter()
+        lat, beads = [], 0
+        for rid, nb, u in outs:
+            st, l = rp.rpy_server_wait(srv, rid)
+            if st == 0:
+                lat.append(l)
+                beads += nb
+        return lat, beads
+
+    # warm every system once (first admission builds its tree), then capacity from a closed loop
+    run(len(systems), 0, order=list(range(len(systems))))
+    t0 = time.perf_counter()
+    lat, beads = run(args.serve_requests, 0)
+    wall = time.perf_counter() - t0
+    cap_rps = args.serve_requests / wall
+    out = {"mode": "serve", "metric": "served RPY matvec Mbeads/s (mixed 3-digit FP32 / 6-digit FP64)",
+           "unit": "Mbeads/s", "systems": len(systems), "slots": args.serve_slots,
+           "total_beads": int(sum(sy.n for sy in systems)), "capacity_req_s": round(cap_rps, 3),
+           "closed_loop": {"Mbeads_s": round(beads / wall / 1e6, 3), "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                           "p99_ms": round(float(np.percentile(lat, 99)), 2)}, "rates": []}
+    for frac in (0.5, 0.9):
+        t0 = time.perf_counter()
+        lat, beads = run(args.serve_requests, frac * cap_rps)
+        wall = time.perf_counter() - t0
+        out["rates"].append({"load": frac, "req_s": round(args.serve_requests / wall, 3),
+                             "Mbeads_s": round(beads / wall / 1e6, 3), "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                             "p99_ms": round(float(np.percentile(lat, 99)), 2)})
+    out["server"] = {k: v for k, v in rp.rpy_server_stats_get(srv).items() if k in
+                     ("completed", "failed", "evictions", "rebuilds", "peak_resident_bytes", "resident_systems")}
+    rp.rpy_server_destroy(srv)
+    return out
 
 
 def main():
@@ -276,6 +423,11 @@ def main():
     ap.add_argument("--config", default=DEFAULT, choices=sorted(CONFIGS))
     ap.add_argument("--targets", type=int, default=2000, help="oracle sample for the CPU baseline / error")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP32 precision-form measurement")
+    ap.add_argument("--mode", default="bench", choices=["bench", "serve"])
+    ap.add_argument("--serve-systems", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     ws, rank, local = _dist()
     if ws > 1:
@@ -307,7 +459,11 @@ def main():
                           "e2e": {"value": round(v, 6), "unit": "Mbeads/s", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}), flush=True)
         return
-    result, sysm, u_dev, stats, stage_ms, tree = run_ours(args, ws, rank, local)
+    if args.mode == "serve":
+        if rank == 0:
+            print(json.dumps(serve(args, local)), flush=True)
+        return
+    result, sysm, u_dev, stats, stage_ms, _ = run_ours(args, ws, rank, local)
     import paper_1711_02976_gb300 as rp
     peaks = {"fp64": rp.rpy_alu_peak(rp.RPY_FP64), "fp32": rp.rpy_alu_peak(rp.RPY_FP32)}
     result["alu_peaks_tflops"] = {k: round(v / 1e12, 3) for k, v in peaks.items()}
@@ -318,16 +474,22 @@ def main():
         import oracle
         tg, ref, dt, th = cpu_oracle_sample(sysm, args.targets)
         err = oracle.rel_l2(u_dev[tg], ref)
-        selft = sysm.s / (6 * math.pi * sysm.a) * sysm.f[tg]
+        selft = self_term(sysm, tg)
         err_far = oracle.rel_l2(u_dev[tg] - selft, ref - selft)
         result["rel_l2"] = err
         result["rel_l2_far"] = err_far
+        if not args.no_forms and CONFIGS[args.config]["precision"] == 0:
+            pf, psys, pu = precision_form(args, local, args.config)
+            result["precision_form"] = {
+                "value": pf["value"], "unit": "Mbeads/s", "ms_per_step": pf["ms_per_step"],
+                "resident_tree_matvec_ms": pf["resident_tree_matvec_ms"], "dtype": "f32+f64",
+                "rel_l2": oracle.rel_l2(pu[tg], ref), "rel_l2_far": oracle.rel_l2(pu[tg] - selft, ref - selft),
+                "note": "same workload and digit setting, P2P and translations in FP32 with compensated sums"}
         result["cpu_baseline"] = {"value": round(len(tg) / dt / 1e6, 6), "unit": "Mbeads/s", "cores": th,
                                   "kind": "oracle",
                                   "sample": f"{len(tg)} targets (seed 12345) x all {sysm.n} sources; extrapolated "
                                             f"O(N^2) direct rate = targets/s"}
         print(json.dumps(result), flush=True)
-    tree.close()
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()

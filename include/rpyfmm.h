@@ -74,7 +74,8 @@ typedef struct {
                          (Sec. 4.2 "threshold"); 0 = default for the setting */
     int order_p;      /* expansion order p; 0 = default for the setting */
     int max_level;    /* deepest level allowed, 1..21; 0 = 21 */
-    int flags;        /* reserved, must be 0 */
+    int flags;        /* bit 0 (RPY_FLAG_NO_GRAPH): never replay the matvec as a CUDA graph;
+                         other bits must be 0 */
     int direct_w;     /* W-list boxes with at most this many beads are summed directly
                          instead of by multipole evaluation: 0 = automatic
                          (about 1.8 (p+3)(p+4)/2), -1 = never */
@@ -82,6 +83,8 @@ typedef struct {
                          summed directly instead of by source-to-local expansion:
                          0 = automatic (about 0.6 (p+1)(p+2)/2), -1 = never */
 } rpy_build_params;
+
+enum { RPY_FLAG_NO_GRAPH = 1 };
 
 /* Statistics of a built tree (host struct filled by rpy_tree_stats). */
 typedef struct {
@@ -144,7 +147,10 @@ int rpy_forest_build(const double *pos_dev, const int64_t *sys_offsets, int nsys
 int rpy_tree_update_positions(rpy_tree t, const double *pos_dev, void *stream);
 
 /*
- * u = D F for every bead of the tree (the hot path).
+ * u = D F for every bead of the tree (the hot path).  From the second call on
+ * the same build, the body of the matvec (everything after the force gather
+ * and before the final combine) is replayed as a CUDA graph captured once on
+ * a stream owned by the tree (unless RPY_FLAG_NO_GRAPH or profiling is on).
  *   f_dev        device, N x 3 FP64 forces, caller order
  *   kT_over_eta  kT/eta, finite
  *   u_dev        device, N x 3 FP64 velocities, caller order (overwritten)

@@ -240,12 +240,12 @@ def rpy_tree_build(pos, n, a, digits, leaf_cap=0, precision=RPY_FP64, stream=Non
 
 
 def rpy_forest_build(pos, sys_offsets, a, digits, leaf_cap=0, precision=RPY_FP64, order_p=0, max_level=0,
-                     direct_w=0, direct_x=0, stream=None) -> Tree:
+                     direct_w=0, direct_x=0, flags=0, stream=None) -> Tree:
     lib = load()
     off = np.ascontiguousarray(sys_offsets, dtype=np.int64)
     av = np.ascontiguousarray(a, dtype=np.float64)
-    prm = BuildParams(int(digits), int(precision), int(leaf_cap), int(order_p), int(max_level), 0, int(direct_w),
-                      int(direct_x))
+    prm = BuildParams(int(digits), int(precision), int(leaf_cap), int(order_p), int(max_level), int(flags),
+                      int(direct_w), int(direct_x))
     out = ctypes.c_void_p()
     _check(lib.rpy_forest_build(_dev_f64(pos, "pos"), off.ctypes.data, int(av.size), av.ctypes.data,
                                 ctypes.byref(prm), _stream(stream), ctypes.byref(out)), "rpy_forest_build")

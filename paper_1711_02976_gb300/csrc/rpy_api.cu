@@ -330,15 +330,8 @@ static int upload_s(Tree &t, const double *s_host, cudaStream_t st) {
     return RPY_OK;
 }
 
-int run_matvec(Tree &t, const double *f_dev, const double *s_host, double *u_dev, int parts, cudaStream_t st) {
-    if (!t.built) return RPY_ERR_STATE;
-    RPY_TRY(upload_s(t, s_host, st));
-    SysConst sc{t.sys_cube, t.sys_a, t.sys_s};
-    for (int k = 0; k < 16; ++k) t.ev_used[k] = false;
-    prof_mark(t, RPY_STAGE_GATHER, st);
-    k_gather_f<<<nb256(t.n), 256, 0, st>>>(f_dev, t.perm, t.n, t.fs);
-    RPY_LAUNCHED(1);
-    RPY_CHECK(cudaGetLastError());
+// Body of the matvec on stream st: near field, direct substitutes, far field.
+static int matvec_body(Tree &t, const SysConst &sc, int parts, cudaStream_t st) {
     prof_mark(t, RPY_STAGE_P2P, st);
     if (parts & RPY_PART_NEAR) RPY_TRY(run_p2p(t, t.fs, t.u_near, sc, st, false));
     if (parts & RPY_PART_FAR) RPY_TRY(run_p2p(t, t.fs, t.u_dir, sc, st, true));
@@ -349,12 +342,60 @@ int run_matvec(Tree &t, const double *f_dev, const double *s_host, double *u_dev
         else
             RPY_TRY(run_far_t<double>(t, t.dt64, t.fs, nullptr, t.u_far, nullptr, sc, st));
     }
+    return RPY_OK;
+}
+
+static void drop_graph(Tree &t) {
+    if (t.gexec) cudaGraphExecDestroy(t.gexec);
+    t.gexec = nullptr;
+}
+
+// Capture the matvec body once on the tree's own stream (capture on the legacy
+// stream is not allowed) and keep the instantiated graph.
+static int capture_graph(Tree &t, const SysConst &sc) {
+    if (!t.cap_stream) RPY_CHECK(cudaStreamCreateWithFlags(&t.cap_stream, cudaStreamNonBlocking));
+    RPY_CHECK(cudaStreamBeginCapture(t.cap_stream, cudaStreamCaptureModeThreadLocal));
+    int s = matvec_body(t, sc, RPY_PART_ALL, t.cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(t.cap_stream, &g);
+    if (s != RPY_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return check_cuda("cudaStreamEndCapture", e);
+    e = cudaGraphInstantiate(&t.gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        t.gexec = nullptr;
+        return check_cuda("cudaGraphInstantiate", e);
+    }
+    return RPY_OK;
+}
+
+int run_matvec(Tree &t, const double *f_dev, const double *s_host, double *u_dev, int parts, cudaStream_t st) {
+    if (!t.built) return RPY_ERR_STATE;
+    RPY_TRY(upload_s(t, s_host, st));
+    SysConst sc{t.sys_cube, t.sys_a, t.sys_s};
+    for (int k = 0; k < 16; ++k) t.ev_used[k] = false;
+    prof_mark(t, RPY_STAGE_GATHER, st);
+    k_gather_f<<<nb256(t.n), 256, 0, st>>>(f_dev, t.perm, t.n, t.fs);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
+    bool graph = parts == RPY_PART_ALL && !t.prof && !(t.params.flags & RPY_FLAG_NO_GRAPH) && t.matvecs >= 1;
+    if (graph && !t.gexec) RPY_TRY(capture_graph(t, sc));
+    if (graph) {
+        RPY_CHECK(cudaGraphLaunch(t.gexec, st));
+        RPY_LAUNCHED(1);
+    } else {
+        RPY_TRY(matvec_body(t, sc, parts, st));
+    }
     prof_mark(t, RPY_STAGE_COMBINE, st);
     k_combine<<<nb256(t.n), 256, 0, st>>>(t.perm, t.n, t.u_near, t.u_far, t.u_dir, parts, u_dev);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     prof_mark(t, RPY_NUM_STAGES, st);
     mark_done(t, st);
+    t.matvecs++;
     return RPY_OK;
 }
 
@@ -388,7 +429,8 @@ int run_laplace_far(Tree &t, const double *q_dev, double *out_dev, cudaStream_t 
 static int check_params(const rpy_build_params &p) {
     if (p.digits != 3 && p.digits != 6) return RPY_ERR_DIGITS;
     if (p.precision != RPY_FP64 && p.precision != RPY_FP32) return RPY_ERR_INVALID;
-    if (p.leaf_cap < 0 || p.order_p < 0 || p.max_level < 0 || p.max_level > kMaxLevel || p.flags != 0)
+    if (p.leaf_cap < 0 || p.order_p < 0 || p.max_level < 0 || p.max_level > kMaxLevel ||
+        (p.flags & ~RPY_FLAG_NO_GRAPH) != 0)
         return RPY_ERR_INVALID;
     if (p.order_p != 0 && (p.order_p < 2 || p.order_p > kMaxP)) return RPY_ERR_INVALID;
     if (p.direct_w < -1 || p.direct_x < -1) return RPY_ERR_INVALID;
@@ -476,6 +518,7 @@ int rpy_tree_update_positions(rpy_tree h, const double *pos_dev, void *stream) {
     Tree &t = h->t;
     DeviceGuard g(t.device);
     wait_done(t);
+    drop_graph(t);
     // keep handle-level settings and the device blocks (as a cache), rebuild the structures
     tree_recycle(t);
     Tree fresh;
@@ -489,6 +532,7 @@ int rpy_tree_update_positions(rpy_tree h, const double *pos_dev, void *stream) {
     fresh.prof = t.prof;
     for (int k = 0; k < 16; ++k) fresh.ev[k] = t.ev[k];
     fresh.done = t.done;
+    fresh.cap_stream = t.cap_stream;
     fresh.sys_off_h = t.sys_off_h;
     fresh.a_h = t.a_h;
     fresh.cache = std::move(t.cache);
@@ -686,6 +730,8 @@ void rpy_tree_free(rpy_tree h) {
         for (int k = 0; k < 16; ++k)
             if (t.ev[k]) cudaEventDestroy(t.ev[k]);
         if (t.done) cudaEventDestroy(t.done);
+        drop_graph(t);
+        if (t.cap_stream) cudaStreamDestroy(t.cap_stream);
     }
     h->magic = 0;
     delete h;

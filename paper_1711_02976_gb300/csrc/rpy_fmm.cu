@@ -23,6 +23,8 @@
 //                     u = C1 [L1 L2 L3] - C1 sum_k x_k grad L_k + C1 grad L4 - C2 grad L_C.
 #include <cmath>
 #include <cstdio>
+#include <map>
+#include <mutex>
 
 #include "rpy_harmonics.h"
 
@@ -806,9 +808,23 @@ static size_t smem_lap(int p) {
     return sizeof(T) * tab_floats<T>(p) + sizeof(cpx<T>) * (13 * st + 3 * st + ncoef(p)) + 64;
 }
 
+// Raise a kernel's dynamic shared-memory limit once per device and kernel
+// (never while a stream is being captured: the first, uncaptured matvec sets
+// every limit it needs).
+static std::mutex g_smem_mu;
+static std::map<std::pair<int, const void *>, size_t> g_smem_done;
+
 template <typename K>
 static int set_smem(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024) RPY_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+    if (bytes <= 48 * 1024) return RPY_OK;
+    int dev = 0;
+    RPY_CHECK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    size_t &d = g_smem_done[{dev, reinterpret_cast<const void *>(kernel)}];
+    if (bytes > d) {
+        RPY_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+        d = bytes;
+    }
     return RPY_OK;
 }
 

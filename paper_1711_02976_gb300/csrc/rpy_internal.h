@@ -222,6 +222,10 @@ struct Tree {
     // per-stage profiling (events recorded between stages when enabled)
     bool prof = false;
     cudaEvent_t done = nullptr;       // recorded after every asynchronous call (survives the caller's stream)
+    // CUDA graph of the matvec body (P2P .. L2P), captured on the second matvec of a build
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int matvecs = 0;                  // matvecs since the last build
     cudaEvent_t ev[16] = {};
     bool ev_used[16] = {};
 };

@@ -15,8 +15,9 @@
 // one Newton-Raphson step for the reciprocal square root (y <- y (3 - r2 y^2)/2),
 // which brings the relative error from ~1e-7 to ~1e-14.
 // FP32 form (precision setting): positions relative to the target leaf centre
-// in FP32, far-branch pairs in FP32 with Kahan-compensated accumulation;
-// overlap pairs (r < 2a) recomputed in FP64 from the FP64 positions.
+// in FP32, pairs in FP32 with Kahan-compensated accumulation; pairs closer than
+// 1e-3 a (where the FP32 difference of coordinates loses the direction) are
+// recomputed in FP64 from the FP64 positions.
 #include <cmath>
 #include <type_traits>
 
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(const int *leaves, const in
     double a = sc.a[sys], s = sc.s[sys];
     double co = s / (6.0 * kPiD * a);
     R_t a2x4 = R_t(4.0 * a * a), a2 = R_t(a * a), cf = R_t(s / (8.0 * kPiD));
+    const float tiny2 = float(1e-6 * a * a), co32 = float(co), c9 = float(9.0 / (32.0 * a)), c3 = float(3.0 / (32.0 * a));
     // FP32 works in coordinates relative to the target leaf centre
     double cx = FP32 ? ctr[3 * b] : 0.0, cy = FP32 ? ctr[3 * b + 1] : 0.0, cz = FP32 ? ctr[3 * b + 2] : 0.0;
     int u0 = uoff[li], u1 = uoff[li + 1];
@@ -169,7 +171,20 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(const int *leaves, const in
                         acc[2] += t1 * fz + t2 * dz;
                     }
                 } else if (jg != i) {
-                    // overlap branch (r < 2a) and coincident beads: always FP64
+                    if constexpr (FP32) {
+                        if (r2 > tiny2) {
+                            // overlap branch in FP32: well conditioned away from r = 0
+                            float r = sqrtf(r2);
+                            float RF = dx * fx + dy * fy + dz * fz;
+                            float t1 = co32 * (1.0f - c9 * r);
+                            float t2 = co32 * c3 * RF / r;
+                            kahan_add(acc[0], cmp[0], t1 * fx + t2 * dx);
+                            kahan_add(acc[1], cmp[1], t1 * fy + t2 * dy);
+                            kahan_add(acc[2], cmp[2], t1 * fz + t2 * dz);
+                            continue;
+                        }
+                    }
+                    // FP64 form, and beads within 1e-3 a of each other in the FP32 form
                     double ddx = pos[i] - pos[jg], ddy = pos[n + i] - pos[n + jg], ddz = pos[2 * n + i] - pos[2 * n + jg];
                     overlap_pair(ddx, ddy, ddz, ddx * ddx + ddy * ddy + ddz * ddz, fs[jg], fs[n + jg], fs[2 * n + jg], a,
                                  co, accd);

@@ -349,3 +349,27 @@ def test_update_positions_matches_fresh_build():
     rp.rpy_matvec(t, F, sysm.s, U)
     u2, _ = matvec(pos2, sysm.f, sysm.a, sysm.s, 3)
     np.testing.assert_array_equal(U.cpu().numpy(), u2)
+
+
+def test_graph_replay_matches_plain_launches():
+    """From the second matvec on a build, the body runs as a captured CUDA graph;
+    results stay bitwise equal to plain launches, also after a rebuild."""
+    import torch
+    sysm = synth.sphere_plus_cube(20000, 31, 2e-4)
+    P, F = cuda_tensor(sysm.pos), cuda_tensor(sysm.f)
+    t_graph = rp.rpy_forest_build(P, [0, sysm.n], [sysm.a], 6, leaf_cap=40)
+    t_plain = rp.rpy_forest_build(P, [0, sysm.n], [sysm.a], 6, leaf_cap=40, flags=1)
+    U0, U1 = torch.empty_like(F), torch.empty_like(F)
+    for rep in range(3):
+        rp.rpy_matvec(t_graph, F, sysm.s, U0)
+        rp.rpy_matvec(t_plain, F, sysm.s, U1)
+        torch.cuda.synchronize()
+        assert torch.equal(U0, U1), rep
+    P2 = cuda_tensor(sysm.pos + 1e-4 * np.random.default_rng(0).standard_normal(sysm.pos.shape))
+    rp.rpy_tree_update_positions(t_graph, P2)
+    rp.rpy_tree_update_positions(t_plain, P2)
+    for rep in range(3):
+        rp.rpy_matvec(t_graph, 2.0 * F, sysm.s, U0)
+        rp.rpy_matvec(t_plain, 2.0 * F, sysm.s, U1)
+        torch.cuda.synchronize()
+        assert torch.equal(U0, U1), rep
