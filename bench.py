@@ -57,6 +57,21 @@ CONFIGS = {
 DEFAULT = "sphere1m_6digit_fp64"
 
 
+def replica_value(n_per_rank, ms_local, ws, device=None):
+    """Whole-job rate of N independent replicas: every rank times its own
+    system; the step time is the maximum over ranks (all_reduce MAX after a
+    barrier), the value counts every rank's beads.  Returns (Mbeads/s, ms)."""
+    ms = float(ms_local)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ws * n_per_rank / (ms * 1e-3) / 1e6, ms
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -199,14 +214,7 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
         tm.append(e1.elapsed_time(e2))
     launches = (rp.rpy_launch_count() - launches0) // max(1, steps)
     clocks = sampler.stop()
-    ms = sum(times) / len(times)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        ms = float(t.item())
-    value = ws * n / (ms * 1e-3) / 1e6
+    value, ms = replica_value(n, sum(times) / len(times), ws, dev)
     stats = rp.rpy_tree_stats(tree)
 
     # repeated matvecs on the resident tree (the Krylov use), replayed as a CUDA graph
