@@ -152,12 +152,13 @@ def make_workload(name):
 
 def flops_model(stats, stage):
     """Algorithmic floating-point operations of one stage (FMA = 2), counted
-    from the kernel source: the direct RPY pair costs 46 in the
-    FP64 kernel (3 sub, r^2 5, Newton reciprocal sqrt 5, scalars 3, R.F 5,
-    t1 3, t2 5, accumulate 12) and 45 in the FP32 kernel (no Newton step;
-    Kahan adds 4 per component)."""
+    from the kernel source: the far-branch RPY pair costs 39 in
+    the FP64 kernel (3 sub, r^2 5, Newton reciprocal sqrt 5, scalars 9 (1/r^2,
+    A, B, t1, 1-2a^2/r^2, t2), R.F 5, accumulate 12) and 43 in the FP32 kernel
+    (hardware reciprocal sqrt, no Newton step; Kahan-compensated accumulation
+    21)."""
     if stage == "p2p":
-        per = 46.0 if stats["precision"] == 0 else 45.0
+        per = 39.0 if stats["precision"] == 0 else 43.0
         return (stats["u_pairs"] + stats["d_pairs"]) * per
     return None
 

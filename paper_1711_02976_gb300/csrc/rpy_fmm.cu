@@ -379,7 +379,9 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
             Mu = Mf;
         }
         for (int st = 0; st < kSets; ++st) {
-            // A_k^m split by parity of n + m (the - direction is the reflection (-1)^{n+m})
+            // A_k^m split by parity of n + m (the - direction is the reflection (-1)^{n+m}),
+            // stored as 2 i^m A_k^m so that the wave sum below needs no sign logic:
+            // even m feed the real part, odd m the imaginary part.
             for (int e = threadIdx.x; e < s * P1; e += blockDim.x) {
                 int k = e / P1, m = e - k * P1;
                 T evx = 0, evy = 0, odx = 0, ody = 0;
@@ -394,8 +396,9 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
                     odx += cc[i] * Mu[st * nc + i].x;
                     ody += cc[i] * Mu[st * nc + i].y;
                 }
-                AE[e] = mk(evx, evy);
-                AO[e] = mk(odx, ody);
+                T sg = m == 0 ? T(1) : (((m >> 1) & 1) ? T(-2) : T(2));   // 2 i^m up to the factor i for odd m
+                AE[e] = mk(sg * evx, sg * evy);
+                AO[e] = mk(sg * odx, sg * ody);
             }
             __syncthreads();
             // W_j = (w_k/M_k) [A^0 + 2 sum_m i^m Re(A^m e^{i m a_j})], A = AE +- AO
@@ -405,21 +408,24 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
                 const cpx<T> *rt = D.roots + 2 * j0;
                 const cpx<T> *ae = AE + k * P1;
                 const cpx<T> *ao = AO + k * P1;
-                // even-m terms build the real part, odd-m terms the imaginary part
                 T er = ae[0].x, orr = ao[0].x, ei = 0, oi = 0;
-                int idx = 0;
-                for (int m = 1; m <= p; ++m) {
-                    idx += jl;
+                int step2 = 2 * jl;
+                if (step2 >= Mk) step2 -= Mk;
+                int idx = 0;   // (m jl) mod Mk for even m
+                for (int m = 2; m <= p; m += 2) {
+                    idx += step2;
                     if (idx >= Mk) idx -= Mk;
                     cpx<T> z = rt[idx];
-                    T se = ae[m].x * z.x - ae[m].y * z.y;
-                    T so = ao[m].x * z.x - ao[m].y * z.y;
-                    switch (m & 3) {
-                        case 0: er += 2 * se; orr += 2 * so; break;
-                        case 1: ei += 2 * se; oi += 2 * so; break;
-                        case 2: er -= 2 * se; orr -= 2 * so; break;
-                        default: ei -= 2 * se; oi -= 2 * so; break;
-                    }
+                    er += ae[m].x * z.x - ae[m].y * z.y;
+                    orr += ao[m].x * z.x - ao[m].y * z.y;
+                }
+                idx = jl;      // odd m, starting at m = 1
+                for (int m = 1; m <= p; m += 2) {
+                    cpx<T> z = rt[idx];
+                    ei += ae[m].x * z.x - ae[m].y * z.y;
+                    oi += ao[m].x * z.x - ao[m].y * z.y;
+                    idx += step2;
+                    if (idx >= Mk) idx -= Mk;
                 }
                 T wm = D.e_wm[j];
                 Xo[base + size_t(2 * f) * kSets * S + st * S + j] = mk(wm * (er + orr), wm * (ei + oi));

@@ -28,10 +28,12 @@ namespace rpy {
 constexpr double kPiD = 3.14159265358979323846;
 constexpr int kP2PThreads = 256;
 
+// Reciprocal square root: single-precision seed (relative error below 2^-21)
+// and one Newton step, y (3 - r2 y^2) / 2 (error ~1e-14).  Valid while r2 is
+// inside the float range; callers with r2 possibly outside use 1/sqrt.
 __device__ __forceinline__ double rsqrt_newton(double r2) {
-    if (r2 < 1e-30 || r2 > 1e30) return 1.0 / sqrt(r2);
-    double y = double(rsqrtf(float(r2)));   // relative error below 2^-21
-    return y * (1.5 - 0.5 * r2 * y * y);     // one Newton step: error below ~1e-12 * 2^-10
+    double y = double(rsqrtf(float(r2)));
+    return y * (1.5 - 0.5 * r2 * y * y);
 }
 
 __device__ __forceinline__ void overlap_pair(double dx, double dy, double dz, double r2, double fx, double fy, double fz,
@@ -115,6 +117,9 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(const int *leaves, const in
     double co = s / (6.0 * kPiD * a);
     R_t a2x4 = R_t(4.0 * a * a), a2 = R_t(a * a), cf = R_t(s / (8.0 * kPiD));
     const float tiny2 = float(1e-6 * a * a), co32 = float(co), c9 = float(9.0 / (32.0 * a)), c3 = float(3.0 / (32.0 * a));
+    const R_t k23 = R_t(2.0 * a * a / 3.0), k2 = R_t(2.0 * a * a);
+    // far-branch pairs have r2 >= 4a^2; the float seed needs r2 inside the float range
+    const bool safe_range = 4.0 * a * a > 1e-30 && 4.0 * a * a * 1e12 < 1e30;
     // FP32 works in coordinates relative to the target leaf centre
     double cx = FP32 ? ctr[3 * b] : 0.0, cy = FP32 ? ctr[3 * b + 1] : 0.0, cz = FP32 ? ctr[3 * b + 2] : 0.0;
     int u0 = uoff[li], u1 = uoff[li + 1];
@@ -152,15 +157,17 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(const int *leaves, const in
                 R_t r2 = dx * dx + dy * dy + dz * dz;
                 R_t fx = sfx[jj], fy = sfy[jj], fz = sfz[jj];
                 if (r2 >= a2x4) {
+                    // s/(8 pi r) [(1 + 2a^2/(3r^2)) F + (1 - 2a^2/r^2)(R.F)/r^2 R]
+                    //   = t1 F + t2 R with A = cf/r, B = A/r^2
                     R_t ri;
                     if constexpr (FP32) ri = rsqrtf(r2);
-                    else ri = rsqrt_newton(r2);
+                    else ri = safe_range ? rsqrt_newton(r2) : 1.0 / sqrt(r2);
                     R_t ri2 = ri * ri;
-                    R_t c = cf * ri;
-                    R_t q = a2 * ri2;
+                    R_t A = cf * ri;
+                    R_t B = A * ri2;
                     R_t RF = dx * fx + dy * fy + dz * fz;
-                    R_t t1 = c * (R_t(1) + R_t(2.0 / 3.0) * q);
-                    R_t t2 = c * (R_t(1) - R_t(2) * q) * RF * ri2;
+                    R_t t1 = k23 * B + A;
+                    R_t t2 = B * (R_t(1) - k2 * ri2) * RF;
                     if constexpr (FP32) {
                         kahan_add(acc[0], cmp[0], t1 * fx + t2 * dx);
                         kahan_add(acc[1], cmp[1], t1 * fy + t2 * dy);
