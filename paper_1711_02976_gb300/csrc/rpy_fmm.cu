@@ -268,6 +268,68 @@ __global__ void k_p2x(int b0, int nb, DevTables<T> D, const int *beg, const int 
 
 // ---------------------------------------------------------------- M2M / L2L
 
+// Dense per-octant operators (used by the FP32 form, where one streaming pass
+// over the operator beats the rotation's extra synchronisation).
+// M2M: parent M = sum over children of T_o [child M]; output degree n uses inputs of degree <= n.
+template <typename T>
+__global__ void k_m2m(int b0, int nb, DevTables<T> D, const int *leaf, const int *child, cpx<T> *M) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int b = b0 + blockIdx.x;
+    if (leaf[b]) return;
+    const int nc = ncoef(D.p), Dd = 2 * nc;
+    T *X = reinterpret_cast<T *>(smem_raw);
+    int r = threadIdx.x;
+    int kmax = r < Dd ? 2 * ncoef(deg_of(r >> 1)) : 0;
+    T acc[kSets] = {0, 0, 0, 0};
+    for (int o = 0; o < 8; ++o) {
+        int c = child[8 * b + o];
+        if (c < 0) continue;
+        const T *src = reinterpret_cast<const T *>(M + size_t(c) * kSets * nc);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kSets * Dd; i += blockDim.x) X[i] = src[i];
+        __syncthreads();
+        if (r < Dd) {
+            const T *Tt = D.m2m_t + size_t(o) * Dd * Dd;
+            for (int k = 0; k < kmax; ++k) {
+                T t = Tt[size_t(k) * Dd + r];
+#pragma unroll
+                for (int s = 0; s < kSets; ++s) acc[s] += t * X[s * Dd + k];
+            }
+        }
+    }
+    if (r < Dd) {
+        T *dst = reinterpret_cast<T *>(M + size_t(b) * kSets * nc);
+        for (int s = 0; s < kSets; ++s) dst[s * Dd + r] = acc[s];
+    }
+}
+
+// L2L: child L += S_o [parent L]; output degree k uses inputs of degree >= k.
+template <typename T>
+__global__ void k_l2l(int b0, int nb, DevTables<T> D, const int *par, const int *cell, cpx<T> *L) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int b = b0 + blockIdx.x;
+    int P = par[b];
+    const int nc = ncoef(D.p), Dd = 2 * nc;
+    T *X = reinterpret_cast<T *>(smem_raw);
+    const T *src = reinterpret_cast<const T *>(L + size_t(P) * kSets * nc);
+    for (int i = threadIdx.x; i < kSets * Dd; i += blockDim.x) X[i] = src[i];
+    __syncthreads();
+    int r = threadIdx.x;
+    if (r >= Dd) return;
+    int o = (cell[3 * b] & 1) | ((cell[3 * b + 1] & 1) << 1) | ((cell[3 * b + 2] & 1) << 2);
+    int kdeg = deg_of(r >> 1);
+    int k0 = 2 * tri(kdeg, 0);
+    const T *St = D.l2l_t + size_t(o) * Dd * Dd;
+    T acc[kSets] = {0, 0, 0, 0};
+    for (int k = k0; k < Dd; ++k) {
+        T t = St[size_t(k) * Dd + r];
+#pragma unroll
+        for (int s = 0; s < kSets; ++s) acc[s] += t * X[s * Dd + k];
+    }
+    T *dst = reinterpret_cast<T *>(L + size_t(b) * kSets * nc);
+    for (int s = 0; s < kSets; ++s) dst[s * Dd + r] += acc[s];
+}
+
 // ---------------------------------------------------------------- rotations
 // dst[s] = R src[s] per degree block (real 2-layout, block size 2(n+1)).
 template <typename T>
@@ -491,58 +553,63 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = b0 + blockIdx.x;
     const int p = D.p, nc = ncoef(p), s = D.s, S = D.S, P1 = p + 1;
-    cpx<T> *I = reinterpret_cast<cpx<T> *>(smem_raw);   // [2][4][S]: + and - direction of the frame
-    cpx<T> *Bp = I + 2 * kSets * S;                      // [4][s][P1]
-    cpx<T> *Bm = Bp + kSets * s * P1;
-    cpx<T> *Lf = Bm + kSets * s * P1;
-    cpx<T> *Lw = Lf + kSets * nc;
-    cpx<T> *Lr = Lw + kSets * nc;
+    cpx<T> *Ip = reinterpret_cast<cpx<T> *>(smem_raw);   // [S]: + direction of the frame, one set
+    cpx<T> *Im = Ip + S;                                  // [S]: - direction
+    cpx<T> *Bp = Im + S;                                  // [s][P1]
+    cpx<T> *Bm = Bp + s * P1;
+    cpx<T> *Lf = Bm + s * P1;                             // [4][nc] frame accumulation
+    cpx<T> *Lw = Lf + kSets * nc;                         // [4][nc] world accumulation
+    cpx<T> *Lr = Lw + kSets * nc;                         // [4][nc] rotated
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] = mk<T>(0, 0);
     for (int f = 0; f < 3; ++f) {
-        __syncthreads();
-        const cpx<T> *src = Xi + (size_t(b) * kDirs + 2 * f) * kSets * S;
-        for (int i = threadIdx.x; i < 2 * kSets * S; i += blockDim.x) I[i] = src[i];
-        __syncthreads();
-        // b_k^m = sum_{j < M_k/2} (I_j + (-1)^m conj I_j) e^{-i m a_j}
-        //       = 2 sum_j Re(I_j) e^{-i m a_j}      (m even)
-        //       = 2i sum_j Im(I_j) e^{-i m a_j}     (m odd; the factor i is applied below)
-        for (int e = threadIdx.x; e < kSets * s * P1; e += blockDim.x) {
-            int st = e / (s * P1), rem = e - st * s * P1, k = rem / P1, m = rem - k * P1;
-            int j0 = D.k_start[k], j1 = D.k_start[k + 1];
-            int Mk = 2 * (j1 - j0);
-            int mm = m % Mk;
-            const cpx<T> *rt = D.roots + 2 * j0;
-            const cpx<T> *Ip = I + st * S, *Im = I + (kSets + st) * S;
-            T bpx = 0, bpy = 0, bmx = 0, bmy = 0;
-            int idx = 0;
-            for (int j = j0; j < j1; ++j) {
-                cpx<T> r = rt[idx];
-                T vp = (m & 1) ? Ip[j].y : Ip[j].x;
-                T vm = (m & 1) ? Im[j].y : Im[j].x;
-                bpx += vp * r.x;
-                bpy -= vp * r.y;
-                bmx += vm * r.x;
-                bmy -= vm * r.y;
-                idx += mm;
-                if (idx >= Mk) idx -= Mk;
+        for (int st = 0; st < kSets; ++st) {
+            __syncthreads();
+            const cpx<T> *sp = Xi + ((size_t(b) * kDirs + 2 * f) * kSets + st) * S;
+            const cpx<T> *sm = Xi + ((size_t(b) * kDirs + 2 * f + 1) * kSets + st) * S;
+            for (int i = threadIdx.x; i < S; i += blockDim.x) {
+                Ip[i] = sp[i];
+                Im[i] = sm[i];
             }
-            Bp[e] = mk(2 * bpx, 2 * bpy);
-            Bm[e] = mk(2 * bmx, 2 * bmy);
-        }
-        __syncthreads();
-        // L_n^m = i^m sum_k (-lambda_k)^n / sqrt((n-m)!(n+m)!) b_k^m, the - direction reflected
-        for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
-            int st = e / nc, i = e - st * nc;
-            int n = deg_of(i), m = i - tri(n, 0);
-            T sg = ((n + m) & 1) ? T(-1) : T(1);
-            cpx<T> a = mk<T>(0, 0);
-            for (int k = 0; k < s; ++k) {
-                T c = D.x2l_c[size_t(k) * nc + i];
-                cpx<T> bp = Bp[(st * s + k) * P1 + m], bm = Bm[(st * s + k) * P1 + m];
-                a.x += c * (bp.x + sg * bm.x);
-                a.y += c * (bp.y + sg * bm.y);
+            __syncthreads();
+            // b_k^m = sum_{j < M_k/2} (I_j + (-1)^m conj I_j) e^{-i m a_j}
+            //       = 2 sum_j Re(I_j) e^{-i m a_j}      (m even)
+            //       = 2i sum_j Im(I_j) e^{-i m a_j}     (m odd; the factor i is applied below)
+            for (int e = threadIdx.x; e < s * P1; e += blockDim.x) {
+                int k = e / P1, m = e - k * P1;
+                int j0 = D.k_start[k], j1 = D.k_start[k + 1];
+                int Mk = 2 * (j1 - j0);
+                int mm = m % Mk;
+                const cpx<T> *rt = D.roots + 2 * j0;
+                T bpx = 0, bpy = 0, bmx = 0, bmy = 0;
+                int idx = 0;
+                for (int j = j0; j < j1; ++j) {
+                    cpx<T> r = rt[idx];
+                    T vp = (m & 1) ? Ip[j].y : Ip[j].x;
+                    T vm = (m & 1) ? Im[j].y : Im[j].x;
+                    bpx += vp * r.x;
+                    bpy -= vp * r.y;
+                    bmx += vm * r.x;
+                    bmy -= vm * r.y;
+                    idx += mm;
+                    if (idx >= Mk) idx -= Mk;
+                }
+                Bp[e] = mk(2 * bpx, 2 * bpy);
+                Bm[e] = mk(2 * bmx, 2 * bmy);
             }
-            Lf[e] = mul_ipow(a, m + (m & 1));
+            __syncthreads();
+            // L_n^m = i^m sum_k (-lambda_k)^n / sqrt((n-m)!(n+m)!) b_k^m, the - direction reflected
+            for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+                int n = deg_of(i), m = i - tri(n, 0);
+                T sg = ((n + m) & 1) ? T(-1) : T(1);
+                cpx<T> a = mk<T>(0, 0);
+                for (int k = 0; k < s; ++k) {
+                    T c = D.x2l_c[size_t(k) * nc + i];
+                    cpx<T> bp = Bp[k * P1 + m], bm = Bm[k * P1 + m];
+                    a.x += c * (bp.x + sg * bm.x);
+                    a.y += c * (bp.y + sg * bm.y);
+                }
+                Lf[st * nc + i] = mul_ipow(a, m + (m & 1));
+            }
         }
         __syncthreads();
         if (f == 0) {
@@ -801,7 +868,7 @@ static size_t smem_m2x(int p, int s) {
 template <typename T>
 static size_t smem_x2l(int p, int s, int S) {
     int nc = ncoef(p);
-    return sizeof(cpx<T>) * (2 * kSets * S + 2 * kSets * s * (p + 1) + 3 * kSets * nc);
+    return sizeof(cpx<T>) * (2 * S + 2 * s * (p + 1) + 3 * kSets * nc);
 }
 template <typename T>
 static size_t smem_far(int p) {
@@ -859,13 +926,20 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     prof_mark(t, RPY_STAGE_M2M, st);
+    // FP64: rotation-based (fewer FP64 operations); FP32: dense operator
+    const bool rot = sizeof(T) == 8;
     size_t smr3 = sizeof(cpx<T>) * 3 * kSets * nc, smr2 = sizeof(cpx<T>) * 2 * kSets * nc;
+    int Dd = 2 * nc, thr = ((Dd + 31) / 32) * 32;
+    size_t smd = sizeof(T) * kSets * Dd;
     RPY_TRY(set_smem(k_m2m_rot<T>, smr3));
     RPY_TRY(set_smem(k_l2l_rot<T>, smr2));
+    RPY_TRY(set_smem(k_m2m<T>, smd));
+    RPY_TRY(set_smem(k_l2l<T>, smd));
     for (int l = t.nlevels - 2; l >= 2; --l) {
         int lb = t.level_off[l], ln = t.level_off[l + 1] - lb;
         if (ln > 0) {
-            k_m2m_rot<T><<<ln, 256, smr3, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
+            if (rot) k_m2m_rot<T><<<ln, 256, smr3, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
+            else k_m2m<T><<<ln, thr, smd, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
             RPY_LAUNCHED(1);
         }
     }
@@ -901,7 +975,8 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     for (int l = 3; l < t.nlevels; ++l) {
         int lb = t.level_off[l], ln = t.level_off[l + 1] - lb;
         if (ln > 0) {
-            k_l2l_rot<T><<<ln, 256, smr2, st>>>(lb, ln, D, t.b_parent, t.b_cell, L);
+            if (rot) k_l2l_rot<T><<<ln, 256, smr2, st>>>(lb, ln, D, t.b_parent, t.b_cell, L);
+            else k_l2l<T><<<ln, thr, smd, st>>>(lb, ln, D, t.b_parent, t.b_cell, L);
             RPY_LAUNCHED(1);
         }
     }
