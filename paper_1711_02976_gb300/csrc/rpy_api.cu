@@ -21,13 +21,46 @@ static constexpr double kPiA = 3.14159265358979323846;
 
 // ---------------------------------------------------------------- kernels used here
 
-__global__ void k_gather_f(const double *f, const int *perm, int64_t n, double *fs) {
+// Forces into sorted SoA; the FP32 form also keeps a single-precision copy.
+__global__ void k_gather_f(const double *f, const int *perm, int64_t n, double *fs, float *f32) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t j = perm[i];
-    fs[i] = f[3 * j];
-    fs[n + i] = f[3 * j + 1];
-    fs[2 * n + i] = f[3 * j + 2];
+    double fx = f[3 * j], fy = f[3 * j + 1], fz = f[3 * j + 2];
+    fs[i] = fx;
+    fs[n + i] = fy;
+    fs[2 * n + i] = fz;
+    if (f32) {
+        f32[i] = float(fx);
+        f32[n + i] = float(fy);
+        f32[2 * n + i] = float(fz);
+    }
+}
+
+__global__ void k_pair_const(int nsys, const double *a_, const double *s_, const double *cube, PairConst *pc) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsys) return;
+    const double a = a_[k], s = s_[k];
+    PairConst c;
+    c.a = a;
+    c.co = s / (6.0 * kPiA * a);
+    c.cf = s / (8.0 * kPiA);
+    c.k23 = 2.0 * a * a / 3.0;
+    c.nk2 = -2.0 * a * a;
+    c.a2x4 = 4.0 * a * a;
+    c.C1 = s / (8.0 * kPiA);
+    c.C2 = s * a * a / (12.0 * kPiA);
+    c.icube = 1.0 / cube[4 * k + 3];
+    const double co_cf = c.co / c.cf;
+    c.f_a2x4 = float(c.a2x4);
+    c.f_tiny2 = float(1e-6 * a * a);
+    c.f_k23 = float(c.k23);
+    c.f_nk2 = float(c.nk2);
+    c.f_co_cf = float(co_cf);
+    c.f_nco_c9 = float(-co_cf * 9.0 / (32.0 * a));
+    c.f_co_c3 = float(co_cf * 3.0 / (32.0 * a));
+    c.f_pad = 0.f;
+    pc[k] = c;
 }
 
 __global__ void k_gather_q4(const double *q, const int *perm, int64_t n, double *qs) {
@@ -270,6 +303,7 @@ static int alloc_tree_arrays(Tree &t, cudaStream_t st) {
     RPY_TRY(dev_alloc(t, (void **)&t.sys_off, sizeof(int64_t) * (t.nsys + 1)));
     RPY_TRY(dev_alloc(t, (void **)&t.sys_a, sizeof(double) * t.nsys));
     RPY_TRY(dev_alloc(t, (void **)&t.sys_s, sizeof(double) * t.nsys));
+    RPY_TRY(dev_alloc(t, (void **)&t.sys_pc, sizeof(PairConst) * t.nsys));
     RPY_TRY(dev_alloc(t, (void **)&t.sys_cube, sizeof(double) * 4 * t.nsys));
     RPY_TRY(dev_alloc(t, (void **)&t.perm, sizeof(int) * n));
     RPY_TRY(dev_alloc(t, (void **)&t.keys, sizeof(uint64_t) * n));
@@ -292,6 +326,10 @@ int tree_alloc_workspace(Tree &t, cudaStream_t) {
     RPY_TRY(dev_alloc(t, &t.Xi, es * nb * kDirs * kSets * h.S));
     RPY_TRY(dev_alloc(t, &t.EVg, es * size_t(t.nleaf) * 18 * h.nc));
     RPY_TRY(dev_alloc(t, (void **)&t.fs, sizeof(double) * 3 * t.n));
+    if (t.params.precision == RPY_FP32) {
+        RPY_TRY(dev_alloc(t, (void **)&t.p32, sizeof(float) * 6 * t.n));
+        RPY_TRY(dev_alloc(t, (void **)&t.f32, sizeof(float) * 3 * t.n));
+    }
     RPY_TRY(dev_alloc(t, (void **)&t.u_near, sizeof(double) * 3 * t.n));
     RPY_TRY(dev_alloc(t, (void **)&t.u_far, sizeof(double) * 3 * t.n));
     RPY_TRY(dev_alloc(t, (void **)&t.u_dir, sizeof(double) * 3 * t.n));
@@ -311,6 +349,7 @@ static int do_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     t.dt64 = ds->d64;
     t.dt32 = ds->d32;
     RPY_TRY(tree_alloc_workspace(t, st));
+    if (t.params.precision == RPY_FP32) RPY_TRY(split_positions_f32(t, st));
     RPY_CHECK(cudaStreamSynchronize(st));
     mark_done(t, st);
     t.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -325,6 +364,9 @@ static int upload_s(Tree &t, const double *s_host, cudaStream_t st) {
     if (same) return RPY_OK;
     // the copy is ordered on st before every kernel that reads it
     RPY_CHECK(cudaMemcpyAsync(t.sys_s, s_host, sizeof(double) * t.nsys, cudaMemcpyHostToDevice, st));
+    k_pair_const<<<(t.nsys + 127) / 128, 128, 0, st>>>(t.nsys, t.sys_a, t.sys_s, t.sys_cube, t.sys_pc);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
     RPY_CHECK(cudaStreamSynchronize(st));
     t.sys_s_h.assign(s_host, s_host + t.nsys);
     return RPY_OK;
@@ -375,10 +417,10 @@ static int capture_graph(Tree &t, const SysConst &sc) {
 int run_matvec(Tree &t, const double *f_dev, const double *s_host, double *u_dev, int parts, cudaStream_t st) {
     if (!t.built) return RPY_ERR_STATE;
     RPY_TRY(upload_s(t, s_host, st));
-    SysConst sc{t.sys_cube, t.sys_a, t.sys_s};
+    SysConst sc{t.sys_cube, t.sys_a, t.sys_s, t.sys_pc};
     for (int k = 0; k < 16; ++k) t.ev_used[k] = false;
     prof_mark(t, RPY_STAGE_GATHER, st);
-    k_gather_f<<<nb256(t.n), 256, 0, st>>>(f_dev, t.perm, t.n, t.fs);
+    k_gather_f<<<nb256(t.n), 256, 0, st>>>(f_dev, t.perm, t.n, t.fs, t.f32);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     bool graph = parts == RPY_PART_ALL && !t.prof && !(t.params.flags & RPY_FLAG_NO_GRAPH) && t.matvecs >= 1;
@@ -407,7 +449,7 @@ int run_laplace_far(Tree &t, const double *q_dev, double *out_dev, cudaStream_t 
     double *lap_out = nullptr;
     Tree scratch;
     RPY_TRY(dev_alloc(scratch, (void **)&lap_out, sizeof(double) * 52 * t.n));
-    SysConst sc{t.sys_cube, t.sys_a, t.sys_s};
+    SysConst sc{t.sys_cube, t.sys_a, t.sys_s, t.sys_pc};
     k_gather_q4<<<nb256(t.n), 256, 0, st>>>(q_dev, t.perm, t.n, t.lap_q);
     RPY_LAUNCHED(1);
     int s;
@@ -715,7 +757,8 @@ int rpy_tree_footprint(int64_t n, int digits, int precision, int leaf_cap, int64
     double nbox = 4.0 * double(n) / double(leaf_cap) + 64.0;
     double per_box = es * (2.0 * kSets * ncoef(p) + 2.0 * kDirs * kSets * q.half() + 18.0 * ncoef(p)) +
                      4.0 * (8 + 27 + 3 + 12) + 32.0;
-    double per_bead = 3 * 8 /*pos*/ + 8 /*key*/ + 4 + 4 + 9 * 8 /*fs, unear, ufar*/ + 27 * 4 /*U list share*/;
+    double per_bead = 3 * 8 /*pos*/ + 8 /*key*/ + 4 + 4 + 9 * 8 /*fs, unear, ufar*/ + 27 * 4 /*U list share*/ +
+                      (precision == RPY_FP32 ? 9 * 4 /*p32, f32*/ : 0);
     *bytes = int64_t(nbox * per_box + double(n) * per_bead + 32.0 * 1024 * 1024);
     return RPY_OK;
 }

@@ -478,14 +478,18 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
                     idx += step2;
                     if (idx >= Mk) idx -= Mk;
                     cpx<T> z = rt[idx];
-                    er += ae[m].x * z.x - ae[m].y * z.y;
-                    orr += ao[m].x * z.x - ao[m].y * z.y;
+                    er = fma(ae[m].x, z.x, er);
+                    er = fma(-ae[m].y, z.y, er);
+                    orr = fma(ao[m].x, z.x, orr);
+                    orr = fma(-ao[m].y, z.y, orr);
                 }
                 idx = jl;      // odd m, starting at m = 1
                 for (int m = 1; m <= p; m += 2) {
                     cpx<T> z = rt[idx];
-                    ei += ae[m].x * z.x - ae[m].y * z.y;
-                    oi += ao[m].x * z.x - ao[m].y * z.y;
+                    ei = fma(ae[m].x, z.x, ei);
+                    ei = fma(-ae[m].y, z.y, ei);
+                    oi = fma(ao[m].x, z.x, oi);
+                    oi = fma(-ao[m].y, z.y, oi);
                     idx += step2;
                     if (idx >= Mk) idx -= Mk;
                 }
@@ -526,13 +530,20 @@ __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const
         for (int t = 0; t < 8; ++t) acc[t] = mk<T>(0, 0);
         for (int g = 0; g < ng; ++g) {
             cpx<T> ga = mk<T>(0, 0);
+            bool any = false;
             for (int z = goff[g]; z < goff[g + 1]; ++z) {
                 int ent = slots[z];
                 int sb = src[ent & 255];
                 if (sb < 0) continue;
+                any = true;
                 cpx<T> x = Xo[(size_t(sb) * kDirs + d) * kSets * S + e];
-                ga += x * D.shift[size_t(ent >> 8) * S + j];
+                cpx<T> sh = D.shift[size_t(ent >> 8) * S + j];
+                ga.x = fma(x.x, sh.x, ga.x);
+                ga.x = fma(-x.y, sh.y, ga.x);
+                ga.y = fma(x.x, sh.y, ga.y);
+                ga.y = fma(x.y, sh.x, ga.y);
             }
+            if (!any) continue;   // the uniform src[] makes this branch block-uniform
             int mask = gmask[g];
 #pragma unroll
             for (int t = 0; t < 8; ++t)
@@ -593,22 +604,24 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
                     idx += mm;
                     if (idx >= Mk) idx -= Mk;
                 }
-                Bp[e] = mk(2 * bpx, 2 * bpy);
-                Bm[e] = mk(2 * bmx, 2 * bmy);
+                // the + direction and the reflected - direction enter L through
+                // b+ + b- (n + m even) and b+ - b- (n + m odd)
+                Bp[e] = mk(bpx + bmx, bpy + bmy);
+                Bm[e] = mk(bpx - bmx, bpy - bmy);
             }
             __syncthreads();
             // L_n^m = i^m sum_k (-lambda_k)^n / sqrt((n-m)!(n+m)!) b_k^m, the - direction reflected
             for (int i = threadIdx.x; i < nc; i += blockDim.x) {
                 int n = deg_of(i), m = i - tri(n, 0);
-                T sg = ((n + m) & 1) ? T(-1) : T(1);
+                const cpx<T> *Bs = ((n + m) & 1) ? Bm : Bp;
                 cpx<T> a = mk<T>(0, 0);
                 for (int k = 0; k < s; ++k) {
                     T c = D.x2l_c[size_t(k) * nc + i];
-                    cpx<T> bp = Bp[k * P1 + m], bm = Bm[k * P1 + m];
-                    a.x += c * (bp.x + sg * bm.x);
-                    a.y += c * (bp.y + sg * bm.y);
+                    cpx<T> bb = Bs[k * P1 + m];
+                    a.x = fma(c, bb.x, a.x);
+                    a.y = fma(c, bb.y, a.y);
                 }
-                Lf[st * nc + i] = mul_ipow(a, m + (m & 1));
+                Lf[st * nc + i] = mul_ipow(mk(2 * a.x, 2 * a.y), m + (m & 1));
             }
         }
         __syncthreads();
@@ -684,11 +697,9 @@ __global__ void k_far_eval(const int *leaves, DevTables<T> D, const int *beg, co
     cpx<T> *tmp = EV + kNE * st;
     cpx<T> *srcs = tmp + 4 * st;
     int sy = bsys[b];
-    double a = sc.a[sy], sv = sc.s[sy];
-    double C1 = sv / (8.0 * kPi), C2 = sv * a * a / (12.0 * kPi);
+    const double C1 = sc.pc[sy].C1, C2 = sc.pc[sy].C2, icube = sc.pc[sy].icube;
     double c0x = sc.cube[4 * sy], c0y = sc.cube[4 * sy + 1], c0z = sc.cube[4 * sy + 2];
     double cbx = ctr[3 * b], cby = ctr[3 * b + 1], cbz = ctr[3 * b + 2];
-    double hb = side[b];
     int j0 = beg[b], j1 = end[b];
     int nw = woff[li + 1] - woff[li];
     if (nw == 0) return;
@@ -705,8 +716,7 @@ __global__ void k_far_eval(const int *leaves, DevTables<T> D, const int *beg, co
             __syncthreads();
             if (w < 0) build_eval_set<T, false>(srcs, p, P, EV, tmp, cbx - c0x, cby - c0y, cbz - c0z, G);
             else build_eval_set<T, true>(srcs, p, P, EV, tmp, cbx - c0x, cby - c0y, cbz - c0z, G);
-            double h = side[C];
-            double ih = 1.0 / h;
+            double ih = icube * pow2i(lvl[C]);   // 1 / side[C], exactly
             T acc[kNE];
 #pragma unroll
             for (int q = 0; q < kNE; ++q) acc[q] = 0;
@@ -760,9 +770,8 @@ __global__ void k_eval_apply(int64_t n, const int *bead_leaf, const int *leaves,
     if (lvl[b] >= 2) {
         const int p = D.p, nc = ncoef(p);
         int sy = bsys[b];
-        double a = sc.a[sy], sv = sc.s[sy];
-        double C1 = sv / (8.0 * kPi), C2 = sv * a * a / (12.0 * kPi);
-        double ih = 1.0 / side[b];
+        const double C1 = sc.pc[sy].C1, C2 = sc.pc[sy].C2;
+        const double ih = sc.pc[sy].icube * pow2i(lvl[b]);   // 1 / side[b], exactly
         double xi[3] = {(pos[i] - ctr[3 * b]) * ih, (pos[n + i] - ctr[3 * b + 1]) * ih,
                         (pos[2 * n + i] - ctr[3 * b + 2]) * ih};
         T acc[kNE];

@@ -148,6 +148,16 @@ struct DevTables {
 
 // ---------------------------------------------------------------- tree
 
+// Per-system constants of the pair formulas and of Eq. (2.8), formed once per
+// change of kT/eta (the kernels then do no FP64 division of their own).
+struct PairConst {
+    double a, co, cf, k23, nk2;   // co = s/(6 pi a), cf = s/(8 pi), k23 = 2a^2/3, nk2 = -2a^2
+    double a2x4;                  // 4a^2
+    double C1, C2, icube;         // C1 = s/(8 pi), C2 = s a^2/(12 pi), 1/(side of the root cube)
+    float f_a2x4, f_tiny2, f_k23, f_nk2;   // FP32 copies; tiny2 = 1e-6 a^2
+    float f_co_cf, f_nco_c9, f_co_c3, f_pad;   // co/cf, -(co/cf) 9/(32a), (co/cf) 3/(32a)
+};
+
 struct Tree {
     int device = 0;
     bool built = false;               // false while (or after a failed) build
@@ -196,9 +206,12 @@ struct Tree {
     void *M = nullptr, *L = nullptr, *Xo = nullptr, *Xi = nullptr;
     void *EVg = nullptr;              // [nleaf][18][ncoef(p)] derived local expansions of Eq. (2.8)
     double *fs = nullptr;             // sorted forces SoA [3][n]
+    float *p32 = nullptr;             // FP32 form: sorted positions as hi + lo floats, [6][n] (x,y,z hi; x,y,z lo)
+    float *f32 = nullptr;             // FP32 form: sorted forces [3][n]
     double *u_near = nullptr, *u_far = nullptr, *u_dir = nullptr;   // sorted [n][3]
     double *lap_q = nullptr;          // [n][4] sorted charges for the Laplace debug path
     double *sys_s = nullptr;          // [nsys] kT/eta of the last matvec
+    PairConst *sys_pc = nullptr;      // [nsys] constants derived from a, kT/eta and the root cube
     std::vector<double> sys_s_h;
     unsigned *dev_status = nullptr;
     int64_t device_bytes = 0;
@@ -250,12 +263,17 @@ struct SysConst {
     const double *cube;   // [nsys][4]
     const double *a;      // [nsys]
     const double *s;      // [nsys] kT/eta
+    const PairConst *pc;  // [nsys]
 };
+
+// 2^l as a double, by its bit pattern (0 <= l < 1000)
+__device__ __forceinline__ double pow2i(int l) { return __hiloint2double((1023 + l) << 20, 0); }
 
 template <typename T>
 int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *lapq, double *ufar, double *lapout,
               const SysConst &sc, cudaStream_t st);
 int run_p2p(Tree &t, const double *fs, double *out, const SysConst &sc, cudaStream_t st, bool direct_list);
+int split_positions_f32(Tree &t, cudaStream_t st);
 const char *last_cuda_error_text();
 
 // matvec stages (rpy_fmm.cu / rpy_p2p.cu)
