@@ -152,13 +152,14 @@ def make_workload(name):
 
 def flops_model(stats, stage):
     """Algorithmic floating-point operations of one stage (FMA = 2), counted
-    from the kernel source: the far-branch RPY pair costs 39 in
-    the FP64 kernel (3 sub, r^2 5, Newton reciprocal sqrt 5, scalars 9 (1/r^2,
-    A, B, t1, 1-2a^2/r^2, t2), R.F 5, accumulate 12) and 43 in the FP32 kernel
-    (hardware reciprocal sqrt, no Newton step; Kahan-compensated accumulation
-    21)."""
+    from the far branch of the pair kernels: FP64 38 per pair (3 sub, r^2 5,
+    Newton step of the reciprocal square root 5, 1/r^2 1, 1/r^3 1, t1 2,
+    1 - 2a^2/r^2 2, c 1, R.F 5, t2 1, accumulate 12); FP32 33 per pair (the
+    same without the Newton step: the reciprocal square root runs on the
+    special-function unit and is not counted; the Kahan merges, one per 32
+    pairs, are not counted either)."""
     if stage == "p2p":
-        per = 39.0 if stats["precision"] == 0 else 43.0
+        per = 38.0 if stats["precision"] == 0 else 33.0
         return (stats["u_pairs"] + stats["d_pairs"]) * per
     return None
 
@@ -265,9 +266,9 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
 
 
 # DRAM bytes per bead of one FP64 U-list P2P launch, from the ncu capture of the
-# 200k-bead sphere case (profiles/k_p2p_fp64_sphere200k.md: 10,262,528 B); the
+# 200k-bead sphere case (profiles/k_p2p_fp64_sphere200k.md: 10,256,896 B); the
 # traffic is the sources' positions and forces, so it grows with the bead count.
-P2P64_DRAM_BYTES_PER_BEAD = 10262528.0 / 200000.0
+P2P64_DRAM_BYTES_PER_BEAD = 10256896.0 / 200000.0
 
 
 def roofline(result, stats, stage_ms, peaks):
@@ -284,7 +285,7 @@ def roofline(result, stats, stage_ms, peaks):
                 "unit": "TFLOP/s", "frac": round(ach / (peak / 1e12), 4), "traffic": traffic,
                 "traffic_note": "DRAM bytes of the U-list launch, scaled by bead count from a 200k-bead ncu capture"
                 if traffic else None,
-                "fp64_pipe_utilisation_ncu": 0.862 if (top == "p2p" and prec == "fp64") else None,
+                "fp64_pipe_utilisation_ncu": 0.910 if (top == "p2p" and prec == "fp64") else None,
                 "peak_source": "measured FMA-chain probe on this GPU (rpy_alu_peak)"}
     return {"kernel": top, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
             "traffic": None}
