@@ -182,13 +182,18 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
     U = torch.empty_like(F)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
-    if forest:
-        tree = rp.rpy_forest_build(P, sysm.off, sysm.a_list, cfg["digits"], leaf_cap=cfg["leaf_cap"],
-                                   precision=cfg["precision"])
-        matvec = lambda: rp.rpy_forest_matvec(tree, F, sysm.s_list, U)
-    else:
-        tree = rp.rpy_tree_build(P, n, sysm.a, cfg["digits"], leaf_cap=cfg["leaf_cap"], precision=cfg["precision"])
-        matvec = lambda: rp.rpy_matvec(tree, F, sysm.s, U)
+    off = sysm.off if forest else [0, n]
+    a_list = sysm.a_list if forest else [sysm.a]
+    s_list = sysm.s_list if forest else [sysm.s]
+    tune = None
+    bp = {"leaf_cap": cfg["leaf_cap"], "order_p": 0, "direct_w": 0, "direct_x": 0}
+    if args.autotune:
+        # parameter search (untimed): order p, leaf capacity and direct-substitution
+        # thresholds, by sampled-target error against the GPU direct sum and timed matvecs
+        tune = rp.rpy_autotune(P, off, a_list, F, s_list, cfg["digits"], cfg["precision"])
+        bp = {k: tune["best"][k] for k in ("leaf_cap", "order_p", "direct_w", "direct_x")}
+    tree = rp.rpy_forest_build(P, off, a_list, cfg["digits"], precision=cfg["precision"], **bp)
+    matvec = lambda: rp.rpy_forest_matvec(tree, F, s_list, U)
 
     for _ in range(warmup):
         rp.rpy_tree_update_positions(tree, P)
@@ -252,7 +257,9 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
         "config": {"workload": config, "description": cfg["desc"], "n_beads": n, "digits": cfg["digits"],
                    "precision": "fp64" if cfg["precision"] == 0 else "fp32", "parallelism": f"replicas x{ws}",
                    "l2": "flushed between timed steps (256 MB write)", "step": "tree build + matvec",
-                   "leaf_cap": stats["leaf_cap"], "order_p": stats["order_p"], "exp_terms": stats["exp_terms"]},
+                   "leaf_cap": stats["leaf_cap"], "order_p": stats["order_p"], "exp_terms": stats["exp_terms"],
+                   "direct_w": bp["direct_w"], "direct_x": bp["direct_x"],
+                   "params": "autotuned" if tune is not None else "defaults"},
         "build_ms": round(statistics.median(tb), 4), "matvec_ms": round(statistics.median(tm), 4),
         "matvec_only_mbeads_s": round(ws * n / (statistics.median(tm) * 1e-3) / 1e6, 4),
         "resident_tree_matvec_ms": round(statistics.median(reps), 4),
@@ -260,6 +267,10 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
         "tree": {k: stats[k] for k in ("n_systems", "n_boxes", "n_leaves", "depth", "u_pairs", "d_pairs", "n_wlist",
                                        "n_xlist", "n_dlist", "max_leaf_count", "leaves_over_cap", "device_bytes")},
         "gpu_launches": int(launches), "clocks": clocks,
+        "autotune": None if tune is None else {
+            "chosen": bp, "est_rel_l2": tune["est_rel_l2"], "goal": tune["goal"], "tune_ms": round(tune["tune_ms"], 1),
+            "n_trials": len(tune["trials"]), "samples": 256,
+            "method": "order: smallest p with sampled error <= goal; then leaf cap and direct thresholds by timed matvecs"},
     }
     tree.close()
     return result, sysm, u_dev, stats, stage_ms, None
@@ -291,11 +302,12 @@ def roofline(result, stats, stage_ms, peaks):
             "traffic": None}
 
 
-def e2e_host(args, sysm, cfg):
+def e2e_host(args, sysm, cfg, bp=None):
     """The same work through the public API with host data: H2D of positions
     and forces from pinned memory, build, matvec, D2H of velocities, every step
-    (rpy_matvec_host for one system; for a forest the binding calls
-    rpy_forest_build, rpy_forest_matvec and the copies)."""
+    (rpy_matvec_host for one system at the default parameters; otherwise the
+    binding calls rpy_forest_build with the benchmark's build parameters,
+    rpy_forest_matvec and the copies)."""
     import torch
     import paper_1711_02976_gb300 as rp
     n = sysm.n
@@ -303,17 +315,21 @@ def e2e_host(args, sysm, cfg):
     f_h = torch.from_numpy(sysm.f).pin_memory()
     u_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     lib = rp.load()
-    if isinstance(sysm, Forest):
+    forest = isinstance(sysm, Forest)
+    if forest or bp is not None:
         P = torch.empty((n, 3), dtype=torch.float64, device="cuda")
         F = torch.empty_like(P)
         U = torch.empty_like(P)
+        off = sysm.off if forest else [0, n]
+        a_list = sysm.a_list if forest else [sysm.a]
+        s_list = sysm.s_list if forest else [sysm.s]
+        kw = bp if bp is not None else {"leaf_cap": cfg["leaf_cap"]}
 
         def call():
             P.copy_(pos_h, non_blocking=True)
             F.copy_(f_h, non_blocking=True)
-            t = rp.rpy_forest_build(P, sysm.off, sysm.a_list, cfg["digits"], leaf_cap=cfg["leaf_cap"],
-                                    precision=cfg["precision"])
-            rp.rpy_forest_matvec(t, F, sysm.s_list, U)
+            t = rp.rpy_forest_build(P, off, a_list, cfg["digits"], precision=cfg["precision"], **kw)
+            rp.rpy_forest_matvec(t, F, s_list, U)
             u_h.copy_(U, non_blocking=True)
             torch.cuda.synchronize()
             t.close()
@@ -455,6 +471,8 @@ def main():
     ap.add_argument("--targets", type=int, default=2000, help="oracle sample for the CPU baseline / error")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32 precision-form measurement")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="build with the default leaf capacity / order instead of the autotuner's choice")
     ap.add_argument("--mode", default="bench", choices=["bench", "serve"])
     ap.add_argument("--serve-systems", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=64)
@@ -500,7 +518,9 @@ def main():
     result["alu_peaks_tflops"] = {k: round(v / 1e12, 3) for k, v in peaks.items()}
     result["roofline"] = roofline(result, stats, stage_ms, peaks)
     if not args.no_e2e:
-        result["e2e"] = e2e_host(args, sysm, CONFIGS[args.config])
+        c = result["config"]
+        bp = {k: c[k] for k in ("leaf_cap", "order_p", "direct_w", "direct_x")} if c["params"] == "autotuned" else None
+        result["e2e"] = e2e_host(args, sysm, CONFIGS[args.config], bp)
     if rank == 0:
         import oracle
         tg, ref, dt, th = cpu_oracle_sample(sysm, args.targets)
@@ -515,6 +535,8 @@ def main():
                 "value": pf["value"], "unit": "Mbeads/s", "ms_per_step": pf["ms_per_step"],
                 "resident_tree_matvec_ms": pf["resident_tree_matvec_ms"], "dtype": "f32+f64",
                 "rel_l2": oracle.rel_l2(pu[tg], ref), "rel_l2_far": oracle.rel_l2(pu[tg] - selft, ref - selft),
+                "leaf_cap": pf["config"]["leaf_cap"], "order_p": pf["config"]["order_p"],
+                "params": pf["config"]["params"],
                 "note": "same workload and digit setting, P2P and translations in FP32 with compensated sums"}
         result["cpu_baseline"] = {"value": round(len(tg) / dt / 1e6, 6), "unit": "Mbeads/s", "cores": th,
                                   "kind": "oracle",

@@ -277,6 +277,67 @@ enum {
 int rpy_tree_set_profiling(rpy_tree t, int enable);
 int rpy_tree_stage_times(rpy_tree t, double *ms_host, int n);
 
+/* ------------------------------------------------------------------ tuning
+ * FP64 direct sum of u_t = sum_j D_tj F_j at chosen targets t (caller
+ * indices into the whole array), over all beads j of t's system (Sec. 1:
+ * self term, r >= 2a branch, r < 2a overlap branch, coincident beads), on the
+ * GPU.  The autotuner's accuracy reference; also a check for callers.
+ *   pos_dev, f_dev        device, N x 3 FP64, caller order (N = sys_offsets[nsys])
+ *   sys_offsets, a_host, kT_over_eta_host   host, as for rpy_forest_build /
+ *                         rpy_forest_matvec (one system: {0, N})
+ *   targets_host          host, nt indices in [0, N)
+ *   u_host                host, nt x 3 FP64 (written)
+ * Allocates and frees device scratch; synchronises `stream`.
+ */
+int rpy_direct_sampled(const double *pos_dev, const int64_t *sys_offsets, int nsys, const double *a_host,
+                       const double *f_dev, const double *kT_over_eta_host, const int64_t *targets_host,
+                       int64_t nt, double *u_host, void *stream);
+
+typedef struct {
+    int n_samples;       /* sampled targets of the error estimate; 0 = 256 */
+    int timed_reps;      /* timed matvecs per candidate (median kept); 0 = 3 */
+    double margin;       /* accept settings whose sampled relative L2 error is at most
+                            margin x bound (bound 1e-3 at 3 digits, 1e-6 at 6); 0 = 0.3 */
+    uint64_t seed;       /* sample seed; 0 = a fixed default */
+} rpy_autotune_params;
+
+typedef struct {
+    int leaf_cap, order_p, direct_w, direct_x;   /* the candidate */
+    int status;                                  /* RPY_OK, or why it was skipped */
+    double est_rel_l2;                           /* sampled relative L2 error vs rpy_direct_sampled */
+    double matvec_ms;                            /* median timed matvec; < 0 when not timed */
+} rpy_autotune_trial;
+
+typedef struct {
+    rpy_build_params best;   /* chosen parameters (digits and precision as requested) */
+    double est_rel_l2;       /* sampled error at the choice */
+    double matvec_ms;        /* median matvec time at the choice */
+    double goal;             /* margin x bound */
+    double tune_ms;          /* host wall time of the search */
+    int n_trials;            /* entries of trials[] filled (the search stops recording at 48) */
+    rpy_autotune_trial trials[48];
+} rpy_autotune_result;
+
+/*
+ * Autotuner for one bead configuration (one system or a forest): picks the
+ * expansion order, the leaf capacity and the direct-substitution thresholds
+ * of small W / X interactions for the matvec at `digits` / `precision`.
+ *   1. draws n_samples distinct targets and sums RPY there directly
+ *      (rpy_direct_sampled, FP64);
+ *   2. order p: starting from the default, the smallest p whose sampled
+ *      relative L2 error (default leaf capacity) is at most margin x bound;
+ *      if none up to the largest candidate, the p of least error;
+ *   3. leaf capacity in {0.5, 0.7, 1, 1.4, 2} x default, then the thresholds
+ *      {never, half, automatic, double}: the fastest median matvec (CUDA events
+ *      on `stream`) among candidates that keep the error within the goal.
+ * Builds and frees one tree per candidate; allocates device scratch of
+ * N x 3 doubles.  Synchronises `stream`.  Arguments as for rpy_forest_build and
+ * rpy_forest_matvec; params may be NULL (all defaults).
+ */
+int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, int nsys, const double *a_host,
+                 const double *f_dev, const double *kT_over_eta_host, int digits, int precision,
+                 const rpy_autotune_params *params, rpy_autotune_result *out, void *stream);
+
 /*
  * Measured FMA throughput of the current device (FLOP/s, 2 per FMA) for
  * RPY_FP64 or RPY_FP32: a short kernel of independent FMA chains on every

@@ -23,7 +23,7 @@ __all__ = [
     "rpy_matvec_oneshot", "rpy_matvec_host", "rpy_laplace_far", "rpy_tree_export", "rpy_tree_stats",
     "rpy_tree_sync", "rpy_tree_footprint", "rpy_tree_free", "rpy_strerror", "rpy_last_cuda_error",
     "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times", "rpy_launch_count",
-    "rpy_alu_peak", "rpy_bounding_cube_noalloc", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
+    "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_direct_sampled", "rpy_autotune", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
     "RPY_PART_ALL", "EXPORTED_SYMBOLS",
 ]
 
@@ -44,7 +44,7 @@ EXPORTED_SYMBOLS = [
     "rpy_last_cuda_error", "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times",
     "rpy_launch_count", "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_server_create", "rpy_server_add_system",
     "rpy_server_submit", "rpy_server_wait", "rpy_server_cancel", "rpy_server_drain", "rpy_server_stats_get",
-    "rpy_server_destroy",
+    "rpy_server_destroy", "rpy_direct_sampled", "rpy_autotune",
 ]
 STAGES = ["gather", "p2p", "p2m", "m2m", "m2x", "x2x", "x2l", "p2l", "l2l", "eval", "combine"]
 
@@ -76,6 +76,23 @@ class RpyStats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AutotuneParams(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_int), ("timed_reps", ctypes.c_int), ("margin", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class AutotuneTrial(ctypes.Structure):
+    _fields_ = [("leaf_cap", ctypes.c_int), ("order_p", ctypes.c_int), ("direct_w", ctypes.c_int),
+                ("direct_x", ctypes.c_int), ("status", ctypes.c_int), ("est_rel_l2", ctypes.c_double),
+                ("matvec_ms", ctypes.c_double)]
+
+
+class AutotuneResult(ctypes.Structure):
+    _fields_ = [("best", BuildParams), ("est_rel_l2", ctypes.c_double), ("matvec_ms", ctypes.c_double),
+                ("goal", ctypes.c_double), ("tune_ms", ctypes.c_double), ("n_trials", ctypes.c_int),
+                ("trials", AutotuneTrial * 48)]
 
 
 class ServerParams(ctypes.Structure):
@@ -135,6 +152,9 @@ def load(build_if_missing: bool = True):
             "rpy_launch_count": [],
             "rpy_alu_peak": [i, ctypes.POINTER(d), vp],
             "rpy_bounding_cube_noalloc": [vp, i64, vp, vp],
+            "rpy_direct_sampled": [vp, vp, i, vp, vp, vp, vp, i64, vp, vp],
+            "rpy_autotune": [vp, vp, i, vp, vp, vp, i, i, ctypes.POINTER(AutotuneParams),
+                             ctypes.POINTER(AutotuneResult), vp],
             "rpy_server_create": [ctypes.POINTER(ServerParams), ctypes.POINTER(vp)],
             "rpy_server_add_system": [vp, vp, i64, d, ctypes.POINTER(BuildParams), ctypes.POINTER(i)],
             "rpy_server_submit": [vp, i, vp, vp, d, vp, ctypes.POINTER(i64)],
@@ -250,6 +270,39 @@ def rpy_forest_build(pos, sys_offsets, a, digits, leaf_cap=0, precision=RPY_FP64
     _check(lib.rpy_forest_build(_dev_f64(pos, "pos"), off.ctypes.data, int(av.size), av.ctypes.data,
                                 ctypes.byref(prm), _stream(stream), ctypes.byref(out)), "rpy_forest_build")
     return Tree(out.value, int(off[-1]), int(av.size))
+
+
+def rpy_direct_sampled(pos, sys_offsets, a, f, kT_over_eta, targets, stream=None) -> np.ndarray:
+    """FP64 direct RPY sum at the given targets (caller indices); returns (nt, 3) numpy."""
+    off = np.ascontiguousarray(sys_offsets, dtype=np.int64)
+    av = np.ascontiguousarray(a, dtype=np.float64)
+    sv = np.ascontiguousarray(np.broadcast_to(np.asarray(kT_over_eta, dtype=np.float64), av.shape))
+    tg = np.ascontiguousarray(targets, dtype=np.int64)
+    u = np.zeros((tg.size, 3), dtype=np.float64)
+    _check(load().rpy_direct_sampled(_dev_f64(pos, "pos"), off.ctypes.data, int(av.size), av.ctypes.data,
+                                     _dev_f64(f, "f"), sv.ctypes.data, tg.ctypes.data, int(tg.size), u.ctypes.data,
+                                     _stream(stream)), "rpy_direct_sampled")
+    return u
+
+
+def rpy_autotune(pos, sys_offsets, a, f, kT_over_eta, digits, precision=RPY_FP64, n_samples=0, timed_reps=0,
+                 margin=0.0, seed=0, stream=None) -> dict:
+    """Search leaf capacity, order and direct-substitution thresholds; returns a dict with the
+    chosen build parameters ("best"), the sampled error and time there, and every trial."""
+    off = np.ascontiguousarray(sys_offsets, dtype=np.int64)
+    av = np.ascontiguousarray(a, dtype=np.float64)
+    sv = np.ascontiguousarray(np.broadcast_to(np.asarray(kT_over_eta, dtype=np.float64), av.shape))
+    prm = AutotuneParams(int(n_samples), int(timed_reps), float(margin), int(seed))
+    res = AutotuneResult()
+    _check(load().rpy_autotune(_dev_f64(pos, "pos"), off.ctypes.data, int(av.size), av.ctypes.data,
+                               _dev_f64(f, "f"), sv.ctypes.data, int(digits), int(precision), ctypes.byref(prm),
+                               ctypes.byref(res), _stream(stream)), "rpy_autotune")
+    b = res.best
+    return {
+        "best": {k: getattr(b, k) for k, _ in BuildParams._fields_},
+        "est_rel_l2": res.est_rel_l2, "matvec_ms": res.matvec_ms, "goal": res.goal, "tune_ms": res.tune_ms,
+        "trials": [{k: getattr(res.trials[i], k) for k, _ in AutotuneTrial._fields_} for i in range(res.n_trials)],
+    }
 
 
 def rpy_tree_update_positions(tree, pos, stream=None):

@@ -1,0 +1,76 @@
+"""GPU checks of the sampled direct sum and of the autotuner, through the C ABI.
+
+The sampled direct sum is the plain definition evaluated on the GPU in FP64;
+it must agree with the CPU oracle to 1e-12 relative (rounding of the ~N-term
+sums in a different order).  The autotuner's choice must meet the digit
+setting against the oracle (rel-L2 <= 1e-3 or <= 1e-6), and its own sampled
+estimate must be within its goal.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1711_02976_gb300 as rp
+import synth
+from gpu_util import cuda_tensor
+
+pytestmark = pytest.mark.gpu
+
+
+def test_direct_sampled_matches_oracle_one_system():
+    sysm = synth.config1()
+    tg = np.array([0, 1, 7, 100, 2048, 4095], dtype=np.int64)
+    u = rp.rpy_direct_sampled(cuda_tensor(sysm.pos), [0, sysm.n], [sysm.a], cuda_tensor(sysm.f), sysm.s, tg)
+    ref = oracle.rpy_direct(sysm.pos, sysm.f, sysm.a, sysm.s, targets=tg)
+    assert np.max(np.abs(u - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_direct_sampled_forest_systems_do_not_interact():
+    a_sys = synth.uniform_cube(3000, seed=21, a=0.01)
+    b_sys = synth.sphere_plus_cube(5000, seed=22, a=0.003)
+    pos = np.concatenate([a_sys.pos, b_sys.pos])
+    f = np.concatenate([a_sys.f, b_sys.f])
+    off = [0, a_sys.n, a_sys.n + b_sys.n]
+    s = [a_sys.s, 2.0 * b_sys.s]
+    tg = np.array([5, 2999, 3000, 4444, 7999], dtype=np.int64)
+    u = rp.rpy_direct_sampled(cuda_tensor(pos), off, [a_sys.a, b_sys.a], cuda_tensor(f), s, tg)
+    ra = oracle.rpy_direct(a_sys.pos, a_sys.f, a_sys.a, a_sys.s, targets=tg[:2])
+    rb = oracle.rpy_direct(b_sys.pos, b_sys.f, b_sys.a, 2.0 * b_sys.s, targets=tg[2:] - a_sys.n)
+    ref = np.concatenate([ra, rb])
+    assert np.max(np.abs(u - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_direct_sampled_coincident_beads():
+    pos = np.array([[0.5, 0.5, 0.5], [0.5, 0.5, 0.5], [0.5, 0.5, 0.5005], [0.9, 0.1, 0.2]])
+    f = np.array([[1.0, 0.0, 0.0], [0.0, 2.0, 0.0], [0.0, 0.0, 3.0], [1.0, 1.0, 1.0]])
+    a, s = 0.001, 1.0
+    tg = np.arange(4, dtype=np.int64)
+    u = rp.rpy_direct_sampled(cuda_tensor(pos), [0, 4], [a], cuda_tensor(f), s, tg)
+    ref = oracle.rpy_direct(pos, f, a, s)
+    assert np.max(np.abs(u - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("digits,precision", [(3, rp.RPY_FP64), (6, rp.RPY_FP64), (3, rp.RPY_FP32)])
+def test_autotune_choice_meets_the_setting(digits, precision):
+    sysm = synth.sphere_plus_cube(60000, seed=31, a=4e-4)
+    P, F = cuda_tensor(sysm.pos), cuda_tensor(sysm.f)
+    res = rp.rpy_autotune(P, [0, sysm.n], [sysm.a], F, sysm.s, digits, precision, n_samples=200, timed_reps=2)
+    best = res["best"]
+    bound = 1e-3 if digits == 3 else 1e-6
+    assert best["digits"] == digits and best["precision"] == precision
+    assert best["order_p"] > 0 and best["leaf_cap"] >= 8
+    assert res["est_rel_l2"] <= res["goal"] <= bound
+    assert res["matvec_ms"] > 0 and len(res["trials"]) >= 6
+    assert all(t["status"] == 0 for t in res["trials"])
+    # the chosen parameters against the oracle on other targets
+    t = rp.rpy_forest_build(P, [0, sysm.n], [sysm.a], digits, leaf_cap=best["leaf_cap"], precision=precision,
+                            order_p=best["order_p"], direct_w=best["direct_w"], direct_x=best["direct_x"])
+    import torch
+    U = torch.empty_like(F)
+    rp.rpy_forest_matvec(t, F, [sysm.s], U)
+    rp.rpy_tree_sync(t)
+    tg = synth.sample_targets(sysm.n, k=300, seed=77)
+    ref = oracle.rpy_direct(sysm.pos, sysm.f, sysm.a, sysm.s, targets=tg)
+    err = oracle.rel_l2(U.cpu().numpy()[tg], ref)
+    assert err <= bound, (err, best)
+    t.close()

@@ -47,6 +47,24 @@ def test_strerror_and_validation_without_device():
         assert out.value is None
     assert lib.rpy_matvec(None, fake, 1.0, fake, None) == -1
     assert rp.rpy_tree_footprint(10 ** 6, 6) > 10 ** 6
+    # sampled direct sum and autotuner: argument checks, then no device
+    off = np.array([0, 10], dtype=np.int64)
+    bad_off = np.array([0, 0], dtype=np.int64)
+    av, sv = np.array([0.1]), np.array([1.0])
+    tg = np.array([0, 3], dtype=np.int64)
+    u = np.zeros((2, 3))
+    res = rp.AutotuneResult()
+    assert lib.rpy_direct_sampled(fake, bad_off.ctypes.data, 1, av.ctypes.data, fake, sv.ctypes.data,
+                                  tg.ctypes.data, 2, u.ctypes.data, None) == -1
+    assert lib.rpy_autotune(fake, off.ctypes.data, 1, av.ctypes.data, fake, sv.ctypes.data, 5, 0, None,
+                            ctypes.byref(res), None) == -2
+    assert lib.rpy_autotune(fake, off.ctypes.data, 1, av.ctypes.data, fake, sv.ctypes.data, 3, 0, None,
+                            None, None) == -1
+    if not has_gpu:
+        assert lib.rpy_direct_sampled(fake, off.ctypes.data, 1, av.ctypes.data, fake, sv.ctypes.data,
+                                      tg.ctypes.data, 2, u.ctypes.data, None) == -8
+        assert lib.rpy_autotune(fake, off.ctypes.data, 1, av.ctypes.data, fake, sv.ctypes.data, 3, 0, None,
+                                ctypes.byref(res), None) == -8
 
 
 @pytest.mark.parametrize("p", [6, 10])
