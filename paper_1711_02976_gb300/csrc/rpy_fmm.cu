@@ -639,7 +639,8 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
 }
 
 // ---------------------------------------------------------------- far-field evaluation
-constexpr int kNE = 18;
+constexpr int kNE = 18;   // evaluation expansions of Eq. (2.8) per box
+constexpr int kNF = 12;   // of them evaluated per bead after the fold in k_eval_prep
 
 // Build the 18 evaluation expansions of Eq. (2.8) from 4 source expansions.
 // IRREG = multipole source (degrees grow by one per derivative), else local.
@@ -753,8 +754,21 @@ __global__ void k_eval_prep(const int *leaves, DevTables<T> D, const double *ctr
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) srcs[i] = E[i];
     __syncthreads();
     int sy = bsys[b];
-    build_eval_set<T, false>(srcs, p, p, EVg + size_t(li) * kNE * nc, tmp, ctr[3 * b] - sc.cube[4 * sy],
-                             ctr[3 * b + 1] - sc.cube[4 * sy + 1], ctr[3 * b + 2] - sc.cube[4 * sy + 2], G);
+    cpx<T> *EV = EVg + size_t(li) * kNE * nc;
+    build_eval_set<T, false>(srcs, p, p, EV, tmp, ctr[3 * b] - sc.cube[4 * sy], ctr[3 * b + 1] - sc.cube[4 * sy + 1],
+                             ctr[3 * b + 2] - sc.cube[4 * sy + 2], G);
+    // Fold the terms of Eq. (2.8) that are not multiplied by a coordinate into
+    // fields 0..2 (in units of C1/h):  L_d + h^-1 dL4'_d - (C2/C1) h^-2 dL_C,d.
+    // The bead evaluation then needs fields 0..11 only.
+    const double ih = sc.pc[sy].icube * pow2i(lvl[b]);
+    const T c4 = T(ih), cc = T(sc.pc[sy].C2 / sc.pc[sy].C1 * ih * ih);
+    for (int i = threadIdx.x; i < 3 * nc; i += blockDim.x) {
+        int d = i / nc, c = i - d * nc;
+        cpx<T> v = EV[d * nc + c], g4 = EV[(12 + d) * nc + c], gc = EV[(15 + d) * nc + c];
+        v.x = fma(c4, g4.x, fma(-cc, gc.x, v.x));
+        v.y = fma(c4, g4.y, fma(-cc, gc.y, v.y));
+        EV[d * nc + c] = v;
+    }
 }
 
 // One thread per bead: L2P of the leaf's derived expansions and Eq. (2.8).
@@ -770,19 +784,20 @@ __global__ void k_eval_apply(int64_t n, const int *bead_leaf, const int *leaves,
     if (lvl[b] >= 2) {
         const int p = D.p, nc = ncoef(p);
         int sy = bsys[b];
-        const double C1 = sc.pc[sy].C1, C2 = sc.pc[sy].C2;
+        const double C1 = sc.pc[sy].C1;
         const double ih = sc.pc[sy].icube * pow2i(lvl[b]);   // 1 / side[b], exactly
         double xi[3] = {(pos[i] - ctr[3 * b]) * ih, (pos[n + i] - ctr[3 * b + 1]) * ih,
                         (pos[2 * n + i] - ctr[3 * b + 2]) * ih};
-        T acc[kNE];
+        // fields 0..2: the folded value terms; 3..11: gradients dL_k / dx_d at 3 + 3k + d
+        T acc[kNF];
 #pragma unroll
-        for (int q = 0; q < kNE; ++q) acc[q] = 0;
-        eval_fields<T, kNE, false>(T(xi[0]), T(xi[1]), T(xi[2]), p, EVg + size_t(li) * kNE * nc, nc, D.rec_a, D.rec_b,
+        for (int q = 0; q < kNF; ++q) acc[q] = 0;
+        eval_fields<T, kNF, false>(T(xi[0]), T(xi[1]), T(xi[2]), p, EVg + size_t(li) * kNE * nc, nc, D.rec_a, D.rec_b,
                                    D.rec_c, acc);
         for (int d = 0; d < 3; ++d) {
             double v = double(acc[d]);
             for (int k = 0; k < 3; ++k) v -= xi[k] * double(acc[3 + 3 * k + d]);
-            u[d] = C1 * ih * v + C1 * ih * ih * double(acc[12 + d]) - C2 * ih * ih * ih * double(acc[15 + d]);
+            u[d] = C1 * ih * v;
         }
     }
     for (int d = 0; d < 3; ++d) ufar[3 * i + d] = u[d];
