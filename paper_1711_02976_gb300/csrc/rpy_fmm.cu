@@ -39,61 +39,79 @@ __device__ __forceinline__ int deg_of(int idx) {
     return n;
 }
 
-// ---------------------------------------------------------------- harmonics per warp lane
-// Lane m (m <= P) fills column m of y (or z) for one point.
+// ---------------------------------------------------------------- harmonics, several points per warp
+// Lanes per point: columns m and P - m share a lane, so every lane runs P + 2
+// recurrence steps (a column per lane would leave the lanes of high m idle
+// while column 0 runs P + 1 steps, and lanes above P idle altogether; the
+// FP64 pipe is charged per warp instruction).
+__host__ __device__ constexpr int harm_lanes(int P) { return P / 2 + 1; }
+
+// Solid harmonics (regular, or irregular when IRREG) of one point into out[],
+// columns c and P - c of it.
 template <typename T, bool IRREG>
-__device__ void warp_harmonics(T x, T y, T z, int P, const T *ra, const T *rb, const T *cm, cpx<T> *out) {
-    int m = threadIdx.x & 31;
-    if (m > P) return;
-    T r2 = x * x + y * y + z * z;
-    T ir2 = IRREG ? T(1) / r2 : T(0);
-    cpx<T> w = IRREG ? mk(x * ir2, y * ir2) : mk(x, y);
-    cpx<T> d = IRREG ? mk<T>(sqrt(ir2), 0) : mk<T>(1, 0);
-    for (int k = 0; k < m; ++k) d = w * d;
-    d = cm[m] * d;
-    out[tri(m, m)] = d;
-    cpx<T> p2 = mk<T>(0, 0), p1 = d;
-    for (int n = m + 1; n <= P; ++n) {
-        int i = tri(n, m);
-        cpx<T> c;
-        if (IRREG)
-            c = mk((ra[i] * z * p1.x - rb[i] * p2.x) * ir2, (ra[i] * z * p1.y - rb[i] * p2.y) * ir2);
-        else
-            c = mk(ra[i] * z * p1.x - rb[i] * r2 * p2.x, ra[i] * z * p1.y - rb[i] * r2 * p2.y);
-        out[i] = c;
-        p2 = p1;
-        p1 = c;
+__device__ void lane_harmonics(T x, T y, T z, int P, const T *ra, const T *rb, const T *cm, cpx<T> *out, int c) {
+    const T r2 = fma(z, z, fma(y, y, x * x));
+    const T ir2 = IRREG ? T(1) / r2 : T(0);
+    const cpx<T> w = IRREG ? mk(x * ir2, y * ir2) : mk(x, y);
+    const T d0 = IRREG ? sqrt(ir2) : T(1);
+    const T zz = IRREG ? z * ir2 : z;   // factor of the a-coefficients
+    const T rr = IRREG ? ir2 : r2;      // factor of the b-coefficients
+    for (int h = 0; h < 2; ++h) {
+        const int m = h ? P - c : c;
+        if (h && m == c) break;
+        cpx<T> pw = mk<T>(1, 0), base = w;   // w^m by binary powering
+        for (int e = m; e; e >>= 1) {
+            if (e & 1) pw = pw * base;
+            base = base * base;
+        }
+        const T s0 = cm[m] * d0;
+        cpx<T> p1 = mk(s0 * pw.x, s0 * pw.y), p2 = mk<T>(0, 0);
+        out[tri(m, m)] = p1;
+        for (int n = m + 1; n <= P; ++n) {
+            const int i = tri(n, m);
+            const T A = ra[i] * zz, B = rb[i] * rr;
+            const cpx<T> cn = mk(fma(A, p1.x, -B * p2.x), fma(A, p1.y, -B * p2.y));
+            out[i] = cn;
+            p2 = p1;
+            p1 = cn;
+        }
     }
 }
 
-// Streaming per-thread evaluation of NE real fields f_q = sum_{n<=P,m} w_m Re(E_q[n,m] h_n^m(v)).
-template <typename T, int NE, bool IRREG>
+// Streaming per-thread evaluation of NE real fields f_q = sum_{n<=P,m} w_m Re(E_q[n,m] h_n^m(v)),
+// w_0 = 1, w_m = 2 (m > 0); W2: the coefficients already carry w_m.
+template <typename T, int NE, bool IRREG, bool W2 = false>
 __device__ void eval_fields(T x, T y, T z, int P, const cpx<T> *E, int stride, const T *ra, const T *rb,
                             const T *rc, T *acc) {
-    T r2 = x * x + y * y + z * z;
-    T ir2 = IRREG ? T(1) / r2 : T(0);
-    cpx<T> w = IRREG ? mk(x * ir2, y * ir2) : mk(x, y);
+    const T r2 = fma(z, z, fma(y, y, x * x));
+    const T ir2 = IRREG ? T(1) / r2 : T(0);
+    const cpx<T> w = IRREG ? mk(x * ir2, y * ir2) : mk(x, y);
+    const T zz = IRREG ? z * ir2 : z;
+    const T rr = IRREG ? ir2 : r2;
     cpx<T> diag = IRREG ? mk<T>(sqrt(ir2), 0) : mk<T>(1, 0);
     for (int m = 0; m <= P; ++m) {
         if (m > 0) diag = rc[m] * (w * diag);
-        T wm = m ? T(2) : T(1);
+        const T wm = (W2 || m == 0) ? T(1) : T(2);
         cpx<T> p2 = mk<T>(0, 0), p1 = diag;
         {
-            int i = tri(m, m);
-            cpx<T> hw = mk(wm * diag.x, wm * diag.y);
+            const int i = tri(m, m);
+            const cpx<T> hw = W2 ? diag : mk(wm * diag.x, wm * diag.y);
 #pragma unroll
-            for (int q = 0; q < NE; ++q) acc[q] += E[q * stride + i].x * hw.x - E[q * stride + i].y * hw.y;
+            for (int q = 0; q < NE; ++q) {
+                const cpx<T> e = E[q * stride + i];
+                acc[q] = fma(-e.y, hw.y, fma(e.x, hw.x, acc[q]));
+            }
         }
         for (int n = m + 1; n <= P; ++n) {
-            int i = tri(n, m);
-            cpx<T> c;
-            if (IRREG)
-                c = mk((ra[i] * z * p1.x - rb[i] * p2.x) * ir2, (ra[i] * z * p1.y - rb[i] * p2.y) * ir2);
-            else
-                c = mk(ra[i] * z * p1.x - rb[i] * r2 * p2.x, ra[i] * z * p1.y - rb[i] * r2 * p2.y);
-            cpx<T> hw = mk(wm * c.x, wm * c.y);
+            const int i = tri(n, m);
+            const T A = ra[i] * zz, B = rb[i] * rr;
+            const cpx<T> c = mk(fma(A, p1.x, -B * p2.x), fma(A, p1.y, -B * p2.y));
+            const cpx<T> hw = W2 ? c : mk(wm * c.x, wm * c.y);
 #pragma unroll
-            for (int q = 0; q < NE; ++q) acc[q] += E[q * stride + i].x * hw.x - E[q * stride + i].y * hw.y;
+            for (int q = 0; q < NE; ++q) {
+                const cpx<T> e = E[q * stride + i];
+                acc[q] = fma(-e.y, hw.y, fma(e.x, hw.x, acc[q]));
+            }
             p2 = p1;
             p1 = c;
         }
@@ -221,16 +239,21 @@ __global__ void k_p2x(int b0, int nb, DevTables<T> D, const int *beg, const int 
     double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
     double ih = 1.0 / side[b];
     int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    // harmonics: hG points per warp, lane -> (point hg, column pair hc)
+    const int hL = harm_lanes(p), hG = 32 / hL, hg = (threadIdx.x & 31) / hL, hc = (threadIdx.x & 31) - hg * hL;
     __syncthreads();
     for (int si = 0; si < nsrc; ++si) {
         int src = MODE == 0 ? b : xidx[xoff[b] + si];
         int j0 = beg[src], j1 = end[src];
         for (int jc = j0; jc < j1; jc += kChunkB) {
             int cnt = min(kChunkB, j1 - jc);
-            for (int t = warp; t < cnt; t += nwarp) {
-                int j = jc + t;
-                T ex = T((pos[j] - cx) * ih), ey = T((pos[n + j] - cy) * ih), ez = T((pos[2 * n + j] - cz) * ih);
-                warp_harmonics<T, MODE == 1>(ex, ey, ez, p, R.a, R.b, R.cm, ybuf + t * nc);
+            for (int t0 = warp * hG; t0 < cnt; t0 += nwarp * hG) {
+                const int t = t0 + hg;
+                if (hg < hG && t < cnt) {
+                    int j = jc + t;
+                    T ex = T((pos[j] - cx) * ih), ey = T((pos[n + j] - cy) * ih), ez = T((pos[2 * n + j] - cz) * ih);
+                    lane_harmonics<T, MODE == 1>(ex, ey, ez, p, R.a, R.b, R.cm, ybuf + t * nc, hc);
+                }
             }
             for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
                 int j = jc + t;
@@ -769,6 +792,15 @@ __global__ void k_eval_prep(const int *leaves, DevTables<T> D, const double *ctr
         v.y = fma(c4, g4.y, fma(-cc, gc.y, v.y));
         EV[d * nc + c] = v;
     }
+    __syncthreads();
+    // fields 0..11 carry the factor 2 of the m > 0 terms of Re(sum E h)
+    for (int i = threadIdx.x; i < kNF * nc; i += blockDim.x) {
+        int c = i % nc, n = deg_of(c);
+        if (c != tri(n, 0)) {
+            cpx<T> v = EV[i];
+            EV[i] = mk(2 * v.x, 2 * v.y);
+        }
+    }
 }
 
 // One thread per bead: L2P of the leaf's derived expansions and Eq. (2.8).
@@ -792,7 +824,7 @@ __global__ void k_eval_apply(int64_t n, const int *bead_leaf, const int *leaves,
         T acc[kNF];
 #pragma unroll
         for (int q = 0; q < kNF; ++q) acc[q] = 0;
-        eval_fields<T, kNF, false>(T(xi[0]), T(xi[1]), T(xi[2]), p, EVg + size_t(li) * kNE * nc, nc, D.rec_a, D.rec_b,
+        eval_fields<T, kNF, false, true>(T(xi[0]), T(xi[1]), T(xi[2]), p, EVg + size_t(li) * kNE * nc, nc, D.rec_a, D.rec_b,
                                    D.rec_c, acc);
         for (int d = 0; d < 3; ++d) {
             double v = double(acc[d]);
