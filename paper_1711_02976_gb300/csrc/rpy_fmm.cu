@@ -467,23 +467,29 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
             // A_k^m split by parity of n + m (the - direction is the reflection (-1)^{n+m}),
             // stored as 2 i^m A_k^m so that the wave sum below needs no sign logic:
             // even m feed the real part, odd m the imaginary part.
-            for (int e = threadIdx.x; e < s * P1; e += blockDim.x) {
-                int k = e / P1, m = e - k * P1;
-                T evx = 0, evy = 0, odx = 0, ody = 0;
+            // one thread per node k and column pair (m, p - m): p + 2 terms each
+            const int hP = harm_lanes(p);
+            for (int e = threadIdx.x; e < s * hP; e += blockDim.x) {
+                const int k = e / hP, c = e - k * hP;
                 const T *cc = D.m2x_c + size_t(k) * nc;
-                for (int n = m; n <= p; n += 2) {
-                    int i = tri(n, m);
-                    evx += cc[i] * Mu[st * nc + i].x;
-                    evy += cc[i] * Mu[st * nc + i].y;
+                for (int h = 0; h < 2; ++h) {
+                    const int m = h ? p - c : c;
+                    if (h && m == c) break;
+                    T evx = 0, evy = 0, odx = 0, ody = 0;
+                    for (int n = m; n <= p; n += 2) {
+                        const int i = tri(n, m);
+                        evx = fma(cc[i], Mu[st * nc + i].x, evx);
+                        evy = fma(cc[i], Mu[st * nc + i].y, evy);
+                    }
+                    for (int n = m + 1; n <= p; n += 2) {
+                        const int i = tri(n, m);
+                        odx = fma(cc[i], Mu[st * nc + i].x, odx);
+                        ody = fma(cc[i], Mu[st * nc + i].y, ody);
+                    }
+                    const T sg = m == 0 ? T(1) : (((m >> 1) & 1) ? T(-2) : T(2));   // 2 i^m up to i for odd m
+                    AE[k * P1 + m] = mk(sg * evx, sg * evy);
+                    AO[k * P1 + m] = mk(sg * odx, sg * ody);
                 }
-                for (int n = m + 1; n <= p; n += 2) {
-                    int i = tri(n, m);
-                    odx += cc[i] * Mu[st * nc + i].x;
-                    ody += cc[i] * Mu[st * nc + i].y;
-                }
-                T sg = m == 0 ? T(1) : (((m >> 1) & 1) ? T(-2) : T(2));   // 2 i^m up to the factor i for odd m
-                AE[e] = mk(sg * evx, sg * evy);
-                AO[e] = mk(sg * odx, sg * ody);
             }
             __syncthreads();
             // W_j = (w_k/M_k) [A^0 + 2 sum_m i^m Re(A^m e^{i m a_j})], A = AE +- AO
