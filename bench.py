@@ -186,12 +186,12 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
     a_list = sysm.a_list if forest else [sysm.a]
     s_list = sysm.s_list if forest else [sysm.s]
     tune = None
-    bp = {"leaf_cap": cfg["leaf_cap"], "order_p": 0, "direct_w": 0, "direct_x": 0}
+    bp = {"leaf_cap": cfg["leaf_cap"], "order_p": 0, "direct_w": 0, "direct_x": 0, "quad": 0}
     if args.autotune:
         # parameter search (untimed): order p, leaf capacity and direct-substitution
         # thresholds, by sampled-target error against the GPU direct sum and timed matvecs
         tune = rp.rpy_autotune(P, off, a_list, F, s_list, cfg["digits"], cfg["precision"])
-        bp = {k: tune["best"][k] for k in ("leaf_cap", "order_p", "direct_w", "direct_x")}
+        bp = {k: tune["best"][k] for k in ("leaf_cap", "order_p", "direct_w", "direct_x", "quad")}
     tree = rp.rpy_forest_build(P, off, a_list, cfg["digits"], precision=cfg["precision"], **bp)
     matvec = lambda: rp.rpy_forest_matvec(tree, F, s_list, U)
 
@@ -258,7 +258,7 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
                    "precision": "fp64" if cfg["precision"] == 0 else "fp32", "parallelism": f"replicas x{ws}",
                    "l2": "flushed between timed steps (256 MB write)", "step": "tree build + matvec",
                    "leaf_cap": stats["leaf_cap"], "order_p": stats["order_p"], "exp_terms": stats["exp_terms"],
-                   "direct_w": bp["direct_w"], "direct_x": bp["direct_x"],
+                   "direct_w": bp["direct_w"], "direct_x": bp["direct_x"], "quad_rule": stats["quad"],
                    "params": "autotuned" if tune is not None else "defaults"},
         "build_ms": round(statistics.median(tb), 4), "matvec_ms": round(statistics.median(tm), 4),
         "matvec_only_mbeads_s": round(ws * n / (statistics.median(tm) * 1e-3) / 1e6, 4),
@@ -270,7 +270,8 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
         "autotune": None if tune is None else {
             "chosen": bp, "est_rel_l2": tune["est_rel_l2"], "goal": tune["goal"], "tune_ms": round(tune["tune_ms"], 1),
             "n_trials": len(tune["trials"]), "samples": 256,
-            "method": "order: smallest p with sampled error <= goal; then leaf cap and direct thresholds by timed matvecs"},
+            "method": "per plane-wave rule, smallest p with sampled error <= goal; fastest (rule, p); then leaf cap "
+                      "and direct thresholds by timed matvecs"},
     }
     tree.close()
     return result, sysm, u_dev, stats, stage_ms, None
@@ -519,7 +520,8 @@ def main():
     result["roofline"] = roofline(result, stats, stage_ms, peaks)
     if not args.no_e2e:
         c = result["config"]
-        bp = {k: c[k] for k in ("leaf_cap", "order_p", "direct_w", "direct_x")} if c["params"] == "autotuned" else None
+        bp = ({k: c[k] for k in ("leaf_cap", "order_p", "direct_w", "direct_x")} | {"quad": c["quad_rule"]}
+              if c["params"] == "autotuned" else None)
         result["e2e"] = e2e_host(args, sysm, CONFIGS[args.config], bp)
     if rank == 0:
         import oracle

@@ -82,6 +82,11 @@ typedef struct {
     int direct_x;     /* X-list pairs whose target box holds at most this many beads are
                          summed directly instead of by source-to-local expansion:
                          0 = automatic (about 0.6 (p+1)(p+2)/2), -1 = never */
+    int quad;         /* plane-wave quadrature rule of M2X / X2X / X2L: 0 = the rule of
+                         `digits`; 3, 4, 5 or 6 = the rule built for that many digits
+                         (max relative error of the 1/r representation 3.6e-4, 3.6e-5,
+                         2.8e-6, 4.0e-7 over the V-list region; 134, 218, 323, 464 stored
+                         plane waves per direction) */
 } rpy_build_params;
 
 enum { RPY_FLAG_NO_GRAPH = 1 };
@@ -107,6 +112,7 @@ typedef struct {
     int64_t d_pairs;            /* bead pairs summed directly in place of W / X */
     int64_t device_bytes;       /* device memory held by the handle */
     double build_ms;            /* host-measured wall time of the last build */
+    int32_t quad;               /* plane-wave quadrature rule in use (3..6) */
 } rpy_stats;
 
 /*
@@ -254,7 +260,8 @@ const char *rpy_last_cuda_error(void);
 
 /*
  * Host-only inspection of the operator tables for expansion order p and a
- * digit setting (no device needed): which = 1 M2M, 2 L2L (transposed real
+ * plane-wave quadrature rule `digits` (3..6, as rpy_build_params.quad; no
+ * device needed): which = 1 M2M, 2 L2L (transposed real
  * matrices per child octant), 3 / 4 frame rotations world->frame / frame->world,
  * 5 M2X coefficients, 6 X2L coefficients, 7 stored plane waves (k, cos, sin,
  * w/M), 8 shift factors, 9 merge-and-shift groups, 10 rotation block offsets,
@@ -303,6 +310,7 @@ typedef struct {
 
 typedef struct {
     int leaf_cap, order_p, direct_w, direct_x;   /* the candidate */
+    int quad;                                    /* its plane-wave quadrature rule */
     int status;                                  /* RPY_OK, or why it was skipped */
     double est_rel_l2;                           /* sampled relative L2 error vs rpy_direct_sampled */
     double matvec_ms;                            /* median timed matvec; < 0 when not timed */
@@ -324,9 +332,11 @@ typedef struct {
  * of small W / X interactions for the matvec at `digits` / `precision`.
  *   1. draws n_samples distinct targets and sums RPY there directly
  *      (rpy_direct_sampled, FP64);
- *   2. order p: starting from the default, the smallest p whose sampled
- *      relative L2 error (default leaf capacity) is at most margin x bound;
- *      if none up to the largest candidate, the p of least error;
+ *   2. order p: for each plane-wave quadrature rule (6 digits: the rules of
+ *      6, 5 and 4 digits; 3 digits: its own), the smallest p whose sampled
+ *      relative L2 error (default leaf capacity) is at most margin x bound,
+ *      then the (rule, p) pair with the fastest timed matvec; if no pair
+ *      meets the goal, the one of least error;
  *   3. leaf capacity in {0.5, 0.7, 1, 1.4, 2} x default, then the thresholds
  *      {never, half, automatic, double}: the fastest median matvec (CUDA events
  *      on `stream`) among candidates that keep the error within the goal.

@@ -61,7 +61,7 @@ class RpyError(RuntimeError):
 class BuildParams(ctypes.Structure):
     _fields_ = [("digits", ctypes.c_int), ("precision", ctypes.c_int), ("leaf_cap", ctypes.c_int),
                 ("order_p", ctypes.c_int), ("max_level", ctypes.c_int), ("flags", ctypes.c_int),
-                ("direct_w", ctypes.c_int), ("direct_x", ctypes.c_int)]
+                ("direct_w", ctypes.c_int), ("direct_x", ctypes.c_int), ("quad", ctypes.c_int)]
 
 
 class RpyStats(ctypes.Structure):
@@ -72,7 +72,7 @@ class RpyStats(ctypes.Structure):
                 ("leaves_over_cap", ctypes.c_int32), ("u_pairs", ctypes.c_int64), ("n_ulist", ctypes.c_int64),
                 ("n_wlist", ctypes.c_int64), ("n_xlist", ctypes.c_int64), ("n_vpairs", ctypes.c_int64),
                 ("n_dlist", ctypes.c_int64), ("d_pairs", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double)]
+                ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double), ("quad", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -85,7 +85,8 @@ class AutotuneParams(ctypes.Structure):
 
 class AutotuneTrial(ctypes.Structure):
     _fields_ = [("leaf_cap", ctypes.c_int), ("order_p", ctypes.c_int), ("direct_w", ctypes.c_int),
-                ("direct_x", ctypes.c_int), ("status", ctypes.c_int), ("est_rel_l2", ctypes.c_double),
+                ("direct_x", ctypes.c_int), ("quad", ctypes.c_int), ("status", ctypes.c_int),
+                ("est_rel_l2", ctypes.c_double),
                 ("matvec_ms", ctypes.c_double)]
 
 
@@ -260,12 +261,12 @@ def rpy_tree_build(pos, n, a, digits, leaf_cap=0, precision=RPY_FP64, stream=Non
 
 
 def rpy_forest_build(pos, sys_offsets, a, digits, leaf_cap=0, precision=RPY_FP64, order_p=0, max_level=0,
-                     direct_w=0, direct_x=0, flags=0, stream=None) -> Tree:
+                     direct_w=0, direct_x=0, flags=0, quad=0, stream=None) -> Tree:
     lib = load()
     off = np.ascontiguousarray(sys_offsets, dtype=np.int64)
     av = np.ascontiguousarray(a, dtype=np.float64)
     prm = BuildParams(int(digits), int(precision), int(leaf_cap), int(order_p), int(max_level), int(flags),
-                      int(direct_w), int(direct_x))
+                      int(direct_w), int(direct_x), int(quad))
     out = ctypes.c_void_p()
     _check(lib.rpy_forest_build(_dev_f64(pos, "pos"), off.ctypes.data, int(av.size), av.ctypes.data,
                                 ctypes.byref(prm), _stream(stream), ctypes.byref(out)), "rpy_forest_build")

@@ -148,6 +148,9 @@ SETTINGS = [
     # name, digits, target max relative error of the lambda rule, s range
     ("D3", 3, 3.0e-4, (8, 12)),
     ("D6", 6, 3.0e-7, (14, 22)),
+    # intermediate rules the autotuner may pair with a 6-digit accuracy target
+    ("D4", 4, 3.0e-5, (10, 16)),
+    ("D5", 5, 3.0e-6, (12, 19)),
 ]
 
 

@@ -125,8 +125,8 @@ struct DevTableSet {
 };
 
 static std::mutex g_mu;
-static std::map<std::tuple<int, int, int>, OpTables *> g_host_tabs;      // (p, digits, 0)
-static std::map<std::tuple<int, int, int>, DevTableSet *> g_dev_tabs;    // (device, p, digits)
+static std::map<std::tuple<int, int, int>, OpTables *> g_host_tabs;      // (p, quadrature rule, 0)
+static std::map<std::tuple<int, int, int>, DevTableSet *> g_dev_tabs;    // (device, p, quadrature rule)
 
 static int host_tables(int p, int digits, OpTables **out) {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -342,10 +342,10 @@ static int do_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     RPY_TRY(alloc_tree_arrays(t, st));
     RPY_TRY(tree_build(t, pos_dev, st));
     OpTables *h = nullptr;
-    RPY_TRY(host_tables(t.p, t.params.digits, &h));
+    RPY_TRY(host_tables(t.p, t.params.quad, &h));
     t.tabs = *h;   // small copy of the host description (sizes used by workspace / stats)
     DevTableSet *ds = nullptr;
-    RPY_TRY(device_tables(t.device, t.p, t.params.digits, &ds));
+    RPY_TRY(device_tables(t.device, t.p, t.params.quad, &ds));
     t.dt64 = ds->d64;
     t.dt32 = ds->d32;
     RPY_TRY(tree_alloc_workspace(t, st));
@@ -476,6 +476,7 @@ static int check_params(const rpy_build_params &p) {
         return RPY_ERR_INVALID;
     if (p.order_p != 0 && (p.order_p < 2 || p.order_p > kMaxP)) return RPY_ERR_INVALID;
     if (p.direct_w < -1 || p.direct_x < -1) return RPY_ERR_INVALID;
+    if (p.quad != 0 && (p.quad < 3 || p.quad > 6)) return RPY_ERR_INVALID;
     return RPY_OK;
 }
 
@@ -527,6 +528,7 @@ int rpy_forest_build(const double *pos_dev, const int64_t *sys_offsets, int nsys
     t.params = *params;
     if (t.params.leaf_cap == 0) t.params.leaf_cap = default_leaf_cap(params->digits);
     if (t.params.max_level == 0) t.params.max_level = kMaxLevel;
+    if (t.params.quad == 0) t.params.quad = params->digits;
     t.p = params->order_p ? params->order_p : default_order(params->digits);
     t.direct_w = params->direct_w < 0 ? 0 : (params->direct_w > 0 ? params->direct_w : int(1.8 * ncoef(t.p + 2)));
     t.direct_x = params->direct_x < 0 ? 0 : (params->direct_x > 0 ? params->direct_x : int(0.6 * ncoef(t.p)));
@@ -744,6 +746,7 @@ int rpy_tree_stats(rpy_tree h, rpy_stats *o) {
     o->d_pairs = t.d_pairs;
     o->device_bytes = t.device_bytes;
     o->build_ms = t.build_ms;
+    o->quad = t.params.quad;
     return RPY_OK;
 }
 
@@ -853,7 +856,7 @@ int rpy_alu_peak(int precision, double *flops_per_s, void *stream) {
 }
 
 int rpy_debug_table(int p, int digits, int which, double *dst, int64_t capacity, int64_t *count) {
-    if (p < 2 || p > kMaxP || (digits != 3 && digits != 6)) return RPY_ERR_INVALID;
+    if (p < 2 || p > kMaxP || digits < 3 || digits > 6) return RPY_ERR_INVALID;
     OpTables *h = nullptr;
     RPY_TRY(host_tables(p, digits, &h));
     std::vector<double> tmp;

@@ -1,13 +1,15 @@
-// Parameter search for the matvec (leaf capacity, expansion order p and the
-// direct-substitution thresholds of small W / X interactions), and the FP64
-// direct sum on sampled targets that it measures accuracy against.
+// Parameter search for the matvec (plane-wave quadrature rule, expansion
+// order p, leaf capacity and the direct-substitution thresholds of small W / X
+// interactions), and the FP64 direct sum on sampled targets that it measures
+// accuracy against.
 //
 // The accuracy of the FMM at a setting is estimated, not assumed: the tuner
 // draws K targets, sums RPY over all beads of their systems directly on the
 // GPU in FP64 (the definition of Sec. 1: self term, r >= 2a branch, r < 2a
-// overlap branch, coincident beads), and compares the matvec there.  Order p
-// is the smallest that keeps the sampled relative L2 error under
-// margin x bound (bound 1e-3 or 1e-6 for 3 or 6 digits); leaf capacity and
+// overlap branch, coincident beads), and compares the matvec there.  For each
+// candidate quadrature rule the order p is the smallest that keeps the sampled
+// relative L2 error under margin x bound (bound 1e-3 or 1e-6 for 3 or 6
+// digits), and the fastest (rule, p) pair is kept; leaf capacity and
 // the direct-substitution thresholds are then chosen by timed matvecs
 // (CUDA events on the caller's stream) among the settings that still meet it.
 #include <algorithm>
@@ -313,6 +315,7 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
             o.order_p = T.prm.order_p;
             o.direct_w = T.prm.direct_w;
             o.direct_x = T.prm.direct_x;
+            o.quad = T.prm.quad;
             o.est_rel_l2 = T.err;
             o.matvec_ms = T.ms;
             o.status = T.status;
@@ -323,44 +326,97 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
     base.digits = digits;
     base.precision = precision;
     const int pdef = default_order(digits), capdef = default_leaf_cap(digits);
-    const int plo = digits == 3 ? 4 : 10, phi = digits == 3 ? 12 : 24;
+    const int plo = digits == 3 ? 4 : 8, phi = digits == 3 ? 12 : 24;
     base.leaf_cap = capdef;
 
-    // order: the smallest p whose sampled error meets the goal
-    auto err_at = [&](int p) -> Trial {
-        rpy_build_params q = base;
-        q.order_p = p;
+    auto err_at = [&](int q, int p) -> Trial {
+        rpy_build_params b = base;
+        b.quad = q;
+        b.order_p = p;
         Trial T;
-        run(q, false, T);
+        run(b, false, T);
         record(T);
         return T;
     };
-    int p = pdef;
-    Trial Tp = err_at(p);
-    RPY_TRY(Tp.status);
-    if (Tp.err <= goal) {
-        while (p - 1 >= plo) {
-            Trial T = err_at(p - 1);
-            RPY_TRY(T.status);
-            if (T.err > goal) break;
-            --p;
+    // order for one quadrature rule: the smallest p whose sampled error meets
+    // the goal, searched from p0; ok = false when no p does (the rule's own
+    // error floor is above the goal), then p is the order of least error
+    struct OrderPick {
+        int p;
+        double err;
+        bool ok;
+        int status;
+    };
+    auto search_p = [&](int q, int p0) -> OrderPick {
+        int p = p0;
+        Trial T0 = err_at(q, p);
+        if (T0.status != RPY_OK) return {p, T0.err, false, T0.status};
+        if (T0.err <= goal) {
+            double e = T0.err;
+            while (p - 1 >= plo) {
+                Trial T = err_at(q, p - 1);
+                if (T.status != RPY_OK) return {p, e, true, T.status};
+                if (T.err > goal) break;
+                --p;
+                e = T.err;
+            }
+            return {p, e, true, RPY_OK};
         }
-    } else {
-        double best_err = Tp.err;
+        double best_err = T0.err, prev = T0.err;
         int best_p = p;
         while (p + 1 <= phi) {
             ++p;
-            Trial T = err_at(p);
-            RPY_TRY(T.status);
+            Trial T = err_at(q, p);
+            if (T.status != RPY_OK) return {best_p, best_err, false, T.status};
             if (T.err < best_err) {
                 best_err = T.err;
                 best_p = p;
             }
-            if (T.err <= goal) break;
+            if (T.err <= goal) return {p, T.err, true, RPY_OK};
+            if (T.err > 0.8 * prev) break;   // the rule's floor: a higher order no longer helps
+            prev = T.err;
         }
-        if (best_err > goal) p = best_p;
+        return {best_p, best_err, false, RPY_OK};
+    };
+
+    // quadrature rule and order: for a 6-digit target the cheaper rules are
+    // tried as well; among the (rule, order) pairs that meet the goal the
+    // fastest timed matvec wins
+    std::vector<int> rules = digits == 3 ? std::vector<int>{3} : std::vector<int>{6, 5, 4};
+    int best_q = rules[0], best_p = pdef;
+    double best_ms = INFINITY, best_err = INFINITY;
+    bool best_ok = false;
+    int pstart = pdef;
+    for (int q : rules) {
+        OrderPick pk = search_p(q, pstart);
+        RPY_TRY(pk.status);
+        if (!pk.ok) {
+            if (!best_ok && pk.err < best_err) {
+                best_q = q;
+                best_p = pk.p;
+                best_err = pk.err;
+            }
+            continue;
+        }
+        rpy_build_params b = base;
+        b.quad = q;
+        b.order_p = pk.p;
+        Trial T;
+        int r = run(b, true, T);
+        record(T);
+        RPY_TRY(r);
+        if (T.err <= goal && (!best_ok || T.ms < best_ms)) {
+            best_q = q;
+            best_p = pk.p;
+            best_ms = T.ms;
+            best_err = T.err;
+            best_ok = true;
+        }
+        pstart = pk.p;
     }
-    base.order_p = p;
+    base.quad = best_q;
+    base.order_p = best_p;
+    const int p = best_p;
 
     // leaf capacity, then the direct-substitution thresholds, by timed matvecs
     Trial best;

@@ -22,6 +22,7 @@
 //   groups      merge-and-shift bookkeeping: which children of a parent's
 //               colleagues feed which children of the parent, per direction.
 #include <cmath>
+#include <mutex>
 #include <complex>
 #include <cstring>
 #include <map>
@@ -362,19 +363,23 @@ static void build_groups(OpTables &t) {
     }
 }
 
-const ExpQuad &exp_quadrature(int digits) {
-    static ExpQuad q3, q6;
-    if (q3.s == 0) {
-        q3.s = RPY_EXPQ_D3_S;
-        q3.lambda.assign(rpy_expq_d3_lambda, rpy_expq_d3_lambda + q3.s);
-        q3.weight.assign(rpy_expq_d3_weight, rpy_expq_d3_weight + q3.s);
-        q3.m.assign(rpy_expq_d3_m, rpy_expq_d3_m + q3.s);
-        q6.s = RPY_EXPQ_D6_S;
-        q6.lambda.assign(rpy_expq_d6_lambda, rpy_expq_d6_lambda + q6.s);
-        q6.weight.assign(rpy_expq_d6_weight, rpy_expq_d6_weight + q6.s);
-        q6.m.assign(rpy_expq_d6_m, rpy_expq_d6_m + q6.s);
-    }
-    return digits <= 3 ? q3 : q6;
+// Plane-wave rule `qd` (3..6): the rule generated for that many digits.
+const ExpQuad &exp_quadrature(int qd) {
+    static ExpQuad q[4];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        auto set = [](ExpQuad &e, int s, const double *l, const double *w, const int *m) {
+            e.s = s;
+            e.lambda.assign(l, l + s);
+            e.weight.assign(w, w + s);
+            e.m.assign(m, m + s);
+        };
+        set(q[0], RPY_EXPQ_D3_S, rpy_expq_d3_lambda, rpy_expq_d3_weight, rpy_expq_d3_m);
+        set(q[1], RPY_EXPQ_D4_S, rpy_expq_d4_lambda, rpy_expq_d4_weight, rpy_expq_d4_m);
+        set(q[2], RPY_EXPQ_D5_S, rpy_expq_d5_lambda, rpy_expq_d5_weight, rpy_expq_d5_m);
+        set(q[3], RPY_EXPQ_D6_S, rpy_expq_d6_lambda, rpy_expq_d6_weight, rpy_expq_d6_m);
+    });
+    return q[qd <= 3 ? 0 : (qd >= 6 ? 3 : qd - 3)];
 }
 
 // Expansion order per setting, chosen from measured rel-L2 against the oracle
@@ -384,12 +389,12 @@ const ExpQuad &exp_quadrature(int digits) {
 int default_order(int digits) { return digits <= 3 ? 8 : 18; }
 int default_leaf_cap(int digits) { return digits <= 3 ? 40 : 100; }
 
-int build_tables(int p, int digits, OpTables &t) {
+int build_tables(int p, int qd, OpTables &t) {
     if (p < 2 || p > kMaxP) return RPY_ERR_INVALID;
-    const ExpQuad &q = exp_quadrature(digits);
+    const ExpQuad &q = exp_quadrature(qd);
     t.p = p;
     t.nc = ncoef(p);
-    t.digits = digits;
+    t.digits = qd;
     t.s = q.s;
     t.S = q.half();
     build_m2m(p, t.m2m_t);

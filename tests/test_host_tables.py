@@ -151,7 +151,7 @@ def _quad(digits, p):
     return s, lam, w, M
 
 
-@pytest.mark.parametrize("digits,tol", [(3, 3.0e-4), (6, 4.5e-7)])
+@pytest.mark.parametrize("digits,tol", [(3, 3.0e-4), (4, 4.0e-5), (5, 3.5e-6), (6, 4.5e-7)])
 def test_lambda_quadrature(digits, tol):
     from scipy.special import j0
     s, lam, w, M = _quad(digits, 10)
@@ -225,7 +225,7 @@ def _plane_wave_chain(M, d, off, p, digits):
     return Lf if f == 0 else _rot_apply(bwd, offs, p, f - 1, Lf)
 
 
-@pytest.mark.parametrize("digits,p,tol", [(3, 10, 2e-3), (6, 20, 3e-6)])
+@pytest.mark.parametrize("digits,p,tol", [(3, 10, 2e-3), (5, 16, 2e-5), (6, 20, 3e-6)])
 @pytest.mark.parametrize("d", range(6))
 def test_plane_wave_m2l_chain(d, digits, p, tol):
     off = np.array(OFFSETS[d], float)
