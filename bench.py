@@ -50,6 +50,9 @@ CONFIGS = {
     "sphere200k_6digit_fp32": dict(gen="sphere200k", digits=6, precision=1, leaf_cap=0,
                                    desc="200,000 beads: sphere surface + 10% cube (seed 2), a=1e-4, 6-digit, FP32 "
                                         "precision form (small case for ncu captures)"),
+    "batch24_3digit_fp32": dict(gen="config4_24", digits=3, precision=1, leaf_cap=0,
+                                desc="24 systems in one forest drawn like the 256-system batch (seed 4), 3-digit, "
+                                     "FP32 precision form (small case for ncu captures)"),
     "batch256_3digit_fp32": dict(gen="config4", digits=3, precision=1, leaf_cap=0,
                                  desc="256 systems in one forest, sizes log-uniform 1e3..2e5 (seed 4), uniform "
                                       "cube or Plummer cluster, a=0.5/N^(1/3), 3-digit, FP32 precision form"),
@@ -146,6 +149,8 @@ def make_workload(name):
     gen = CONFIGS[name]["gen"]
     if gen == "sphere200k":
         return synth.sphere_plus_cube(200000, 2, 1e-4)
+    if gen == "config4_24":
+        return Forest(synth.config4(nsys=24))
     w = getattr(synth, gen)()
     return Forest(w) if isinstance(w, list) else w
 

@@ -80,6 +80,7 @@ constexpr int kSets = 4;          // Laplace charge sets L1..L4 (Sec. 2)
 constexpr int kDirs = 6;          // +z -z +x -x +y -y plane-wave directions
 constexpr int kMaxP = 29;         // largest supported expansion order (p + 2 < 32 warp lanes)
 constexpr int kMaxLevel = 21;
+constexpr int kItemTargets = 256;   // targets per near-field work item
 
 struct ExpQuad {                  // plane-wave quadrature (box units)
     int s = 0;                    // lambda nodes
@@ -200,6 +201,10 @@ struct Tree {
     int n_x2x_par = 0, *x2x_par = nullptr;
     // direct (P2P) substitutes for small W and X interactions, per leaf
     int *d_off = nullptr, *d_idx = nullptr;
+    // near-field work items (leaf, first target) of at most kItemTargets targets, in
+    // decreasing cost order for the U-list pass and for the direct-substitute pass
+    int n_items = 0;
+    int2 *u_items = nullptr, *d_items = nullptr;
     int64_t n_d = 0, d_pairs = 0;
     int direct_w = 0, direct_x = 0;    // bead-count thresholds in use (0 = none)
     // expansions and matvec workspace

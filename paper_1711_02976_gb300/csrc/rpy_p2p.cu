@@ -110,26 +110,28 @@ __device__ __forceinline__ SrcCursor cursor_advance(SrcCursor c, int u1, int t, 
 // G = blockDim / R groups; group g takes every G-th bead of each staged chunk.
 // Far pairs accumulate in units of s/(8 pi) (applied once per target) with
 // explicit FMAs: 24 FP64 operations per pair and no conversions.
-__global__ void __launch_bounds__(kP2PThreads) k_p2p(const int *leaves, const int *beg, const int *end,
-                                                     const int *bsys, const int *uoff, const int *uidx,
-                                                     const double *pos, const double *fs, int64_t n, SysConst sc,
-                                                     int add_self, double *out) {
+__global__ void __launch_bounds__(kP2PThreads) k_p2p(const int2 *items, const int *leaves, const int *beg,
+                                                     const int *end, const int *bsys, const int *uoff,
+                                                     const int *uidx, const double *pos, const double *fs, int64_t n,
+                                                     SysConst sc, int add_self, double *out) {
     __shared__ double sx[kP2PThreads], sy[kP2PThreads], sz[kP2PThreads];
     __shared__ double sfx[kP2PThreads], sfy[kP2PThreads], sfz[kP2PThreads];
     __shared__ int sj[kP2PThreads];
     __shared__ double red[3][kP2PThreads];
-    const int li = blockIdx.x, b = leaves[li], sys = bsys[b];
+    const int2 item = items[blockIdx.x];
+    const int li = item.x, b = leaves[li], sys = bsys[b];
+    const int tb = item.y, te = min(end[b], item.y + kItemTargets);
     const PairConst &pc = sc.pc[sys];
     const double a = pc.a, co = pc.co, cf = pc.cf, k23 = pc.k23, nk2 = pc.nk2;
     const long long a2x4 = __double_as_longlong(pc.a2x4);   // r2 >= 4a^2 compared on the bit patterns
     const int u0 = uoff[li], u1 = uoff[li + 1];
-    const int nt = end[b] - beg[b];
+    const int nt = te - tb;
     const int Rn = nt < int(blockDim.x) ? nt : int(blockDim.x);
     const int G = int(blockDim.x) / Rn;
     const int tl = threadIdx.x % Rn, g = threadIdx.x / Rn;
-    for (int i0 = beg[b]; i0 < end[b]; i0 += Rn) {
+    for (int i0 = tb; i0 < te; i0 += Rn) {
         const int i = i0 + tl;
-        const bool act = i < end[b] && g < G;
+        const bool act = i < te && g < G;
         const double xi = act ? pos[i] : 0.0, yi = act ? pos[n + i] : 0.0, zi = act ? pos[2 * n + i] : 0.0;
         double ax = 0, ay = 0, az = 0;   // far pairs, units of s/(8 pi)
         double accd[3] = {0, 0, 0};      // overlapping pairs
@@ -272,7 +274,8 @@ constexpr size_t kP32Smem = sizeof(float4) * kP32Chunk + sizeof(float2) * kP32Ch
                             sizeof(float2) * 6 * kP32Threads + sizeof(double) * 6 * kP32Threads +
                             sizeof(int) * (2 * kP32List + 2) + sizeof(float) * 6 + sizeof(int) * (kP32Queue + 2);
 
-__global__ void __launch_bounds__(kP32Threads, 4) k_p2p32(const int *leaves, const int *beg, const int *end,
+__global__ void __launch_bounds__(kP32Threads, 4) k_p2p32(const int2 *items, const int *leaves, const int *beg,
+                                                         const int *end,
                                                          const int *bsys, const double *ctr, const int *uoff,
                                                          const int *uidx, const float *p32, const float *f32,
                                                          const double *pos, const double *fs, int64_t n, SysConst sc,
@@ -287,7 +290,8 @@ __global__ void __launch_bounds__(kP32Threads, 4) k_p2p32(const int *leaves, con
     float *sCtr = reinterpret_cast<float *>(lpre + kP32List + 2);   // target leaf centre, hi and lo floats
     int *sQn = reinterpret_cast<int *>(sCtr + 6);   // [0] queue length, [1] any FP64 pair in this pass
     int *sQ = sQn + 2;                              // queued pairs: thread << 11 | source slot << 1 | target
-    const int li = blockIdx.x, b = leaves[li], sys = bsys[b];
+    const int2 item = items[blockIdx.x];
+    const int li = item.x, b = leaves[li], sys = bsys[b];
     const PairConst &pc = sc.pc[sys];
     const double a = pc.a, cf = pc.cf, co = pc.co;
     P32Const k;
@@ -309,7 +313,7 @@ __global__ void __launch_bounds__(kP32Threads, 4) k_p2p32(const int *leaves, con
     const float chx = sCtr[0], chy = sCtr[1], chz = sCtr[2], clx = sCtr[3], cly = sCtr[4], clz = sCtr[5];
     const float *xh = p32, *yh = p32 + n, *zh = p32 + 2 * n, *xl = p32 + 3 * n, *yl = p32 + 4 * n, *zl = p32 + 5 * n;
     const int u0 = uoff[li], u1 = uoff[li + 1];
-    const int tb = beg[b], te = end[b], nt = te - tb;
+    const int tb = item.y, te = min(end[b], item.y + kItemTargets), nt = te - tb;
     const int half = (nt + 1) / 2;
     const int Rn = half < kP32Threads ? half : kP32Threads;
     const int G = kP32Threads / Rn;
@@ -490,14 +494,16 @@ int run_p2p(Tree &t, const double *fs, double *out, const SysConst &sc, cudaStre
     const int *off = direct_list ? t.d_off : t.u_off;
     const int *idx = direct_list ? t.d_idx : t.u_idx;
     int add_self = direct_list ? 0 : 1;
+    const int2 *items = direct_list ? t.d_items : t.u_items;
+    if (t.n_items == 0) return RPY_OK;
     if (t.params.precision == RPY_FP32) {
         RPY_CHECK(set_p2p32_smem());
-        k_p2p32<<<t.nleaf, kP32Threads, kP32Smem, st>>>(t.leaves, t.b_begin, t.b_end, t.b_sys, t.b_center, off, idx, t.p32,
-                                                 t.f32, t.pos, fs, t.n, sc, add_self, out);
+        k_p2p32<<<t.n_items, kP32Threads, kP32Smem, st>>>(items, t.leaves, t.b_begin, t.b_end, t.b_sys, t.b_center,
+                                                          off, idx, t.p32, t.f32, t.pos, fs, t.n, sc, add_self, out);
         RPY_LAUNCHED(1);
     } else {
-        k_p2p<<<t.nleaf, kP2PThreads, 0, st>>>(t.leaves, t.b_begin, t.b_end, t.b_sys, off, idx, t.pos, fs, t.n, sc,
-                                               add_self, out);
+        k_p2p<<<t.n_items, kP2PThreads, 0, st>>>(items, t.leaves, t.b_begin, t.b_end, t.b_sys, off, idx, t.pos, fs,
+                                                 t.n, sc, add_self, out);
         RPY_LAUNCHED(1);
     }
     RPY_CHECK(cudaGetLastError());

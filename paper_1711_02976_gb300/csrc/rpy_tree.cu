@@ -724,6 +724,55 @@ __global__ void k_leaf_stats(int nleaf, const int *leaves, const int *beg, const
     if (nb > cap) atomicAdd(over, 1);
 }
 
+// ---------------------------------------------------------------- near-field work items
+// One item per (leaf, block of up to kItemTargets targets).  Two orders list the
+// items by decreasing cost, targets x sources in powers of two (one radix pass),
+// for the U-list pass and for the direct-substitute pass: the block scheduler
+// then starts the long items first, and a leaf that the 2a rule left large is
+// spread over several CTAs instead of running alone at the end of the launch.
+__global__ void k_item_count(int nleaf, const int *leaves, const int *beg, const int *end, int *cnt) {
+    int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li > nleaf) return;
+    if (li == nleaf) {
+        cnt[li] = 0;
+        return;
+    }
+    int b = leaves[li];
+    cnt[li] = (end[b] - beg[b] + kItemTargets - 1) / kItemTargets;
+}
+
+__device__ __forceinline__ uint64_t cost_key(unsigned long long c) {
+    return uint64_t(63 - (c ? 63 - __clzll(c) : 0));   // larger cost, smaller key
+}
+
+__global__ void k_item_fill(int nleaf, const int *leaves, const int *beg, const int *end, const int *uoff,
+                            const int *uidx, const int *doff, const int *didx, const int *ioff, int2 *items,
+                            uint64_t *ku, uint32_t *vu, uint64_t *kd, uint32_t *vd) {
+    int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nleaf) return;
+    int b = leaves[li];
+    int t0 = beg[b], nt = end[b] - t0;
+    unsigned long long su = 0, sd = 0;
+    for (int k = uoff[li]; k < uoff[li + 1]; ++k) su += unsigned(end[uidx[k]] - beg[uidx[k]]);
+    for (int k = doff[li]; k < doff[li + 1]; ++k) sd += unsigned(end[didx[k]] - beg[didx[k]]);
+    for (int q = 0, it = ioff[li]; q * kItemTargets < nt; ++q, ++it) {
+        unsigned tc = unsigned(min(kItemTargets, nt - q * kItemTargets));
+        items[it] = make_int2(li, t0 + q * kItemTargets);
+        ku[it] = cost_key(su * tc);
+        vu[it] = uint32_t(it);
+        kd[it] = cost_key(sd * tc);
+        vd[it] = uint32_t(it);
+    }
+}
+
+__global__ void k_item_order(int n, const int2 *items, const uint32_t *ou, const uint32_t *od, int2 *u_items,
+                             int2 *d_items) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    u_items[i] = items[ou[i]];
+    d_items[i] = items[od[i]];
+}
+
 // ---------------------------------------------------------------- build driver
 
 static int grow_boxes(Tree &t, int need, cudaStream_t st) {
@@ -765,9 +814,14 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     }
     sco[nsys] = int(cb.size());
     int nch = int(cb.size());
-    // scratch for the build (returned to the tree's block cache at the end)
+    // scratch for the build (returned to the tree's block cache at the end, and
+    // on every early return)
     Tree scratch;
     scratch.owner = &t;
+    struct ScratchGuard {
+        Tree &s;
+        ~ScratchGuard() { tree_release(s); }
+    } scratch_guard{scratch};
     int64_t *d_cb, *d_ce;
     int *d_sco;
     double *d_part;
@@ -980,6 +1034,44 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     t.d_pairs = int64_t(pairs[1]);
     t.max_leaf_count = mx[0];
     t.leaves_over_cap = mx[1];
+    // -- near-field work items in decreasing cost order
+    {
+        int *icnt, *ioff;
+        RPY_TRY(dev_alloc(scratch, (void **)&icnt, sizeof(int) * (nleaf + 1)));
+        RPY_TRY(dev_alloc(scratch, (void **)&ioff, sizeof(int) * (nleaf + 1)));
+        k_item_count<<<nblk(nleaf + 1, 256), 256, 0, st>>>(nleaf, t.leaves, t.b_begin, t.b_end, icnt);
+        RPY_LAUNCHED(1);
+        int ni = 0;
+        if (scan_tmp_bytes(nleaf + 1) > sbytes) return RPY_ERR_INTERNAL;
+        RPY_TRY(exclusive_scan_i32(icnt, ioff, nleaf + 1, &ni, stmp, sbytes, st));
+        t.n_items = ni;
+        int2 *items;
+        uint64_t *ku, *kd, *kt;
+        uint32_t *vu, *vd, *vt;
+        int *icounts;
+        const int itiles = nblk(std::max(ni, 1), kSortTile);
+        RPY_TRY(dev_alloc(scratch, (void **)&items, sizeof(int2) * std::max(ni, 1)));
+        RPY_TRY(dev_alloc(scratch, (void **)&ku, sizeof(uint64_t) * std::max(ni, 1)));
+        RPY_TRY(dev_alloc(scratch, (void **)&kd, sizeof(uint64_t) * std::max(ni, 1)));
+        RPY_TRY(dev_alloc(scratch, (void **)&kt, sizeof(uint64_t) * std::max(ni, 1)));
+        RPY_TRY(dev_alloc(scratch, (void **)&vu, sizeof(uint32_t) * std::max(ni, 1)));
+        RPY_TRY(dev_alloc(scratch, (void **)&vd, sizeof(uint32_t) * std::max(ni, 1)));
+        RPY_TRY(dev_alloc(scratch, (void **)&vt, sizeof(uint32_t) * std::max(ni, 1)));
+        RPY_TRY(dev_alloc(scratch, (void **)&icounts, sizeof(int) * 256 * size_t(itiles)));
+        if (scan_tmp_bytes(256 * itiles) > sbytes) return RPY_ERR_INTERNAL;
+        RPY_TRY(dev_alloc(t, (void **)&t.u_items, sizeof(int2) * std::max(ni, 1)));
+        RPY_TRY(dev_alloc(t, (void **)&t.d_items, sizeof(int2) * std::max(ni, 1)));
+        if (ni > 0) {
+            k_item_fill<<<nblk(nleaf, 256), 256, 0, st>>>(nleaf, t.leaves, t.b_begin, t.b_end, t.u_off, t.u_idx,
+                                                          t.d_off, t.d_idx, ioff, items, ku, vu, kd, vd);
+            RPY_LAUNCHED(1);
+            RPY_TRY(radix_sort(ku, vu, kt, vt, ni, 8, icounts, stmp, sbytes, st));
+            RPY_TRY(radix_sort(kd, vd, kt, vt, ni, 8, icounts, stmp, sbytes, st));
+            k_item_order<<<nblk(ni, 256), 256, 0, st>>>(ni, items, vu, vd, t.u_items, t.d_items);
+            RPY_LAUNCHED(1);
+            RPY_CHECK(cudaGetLastError());
+        }
+    }
     tree_release(scratch);
     if (status & DEVERR_STACK) return RPY_ERR_INTERNAL;
     return RPY_OK;
