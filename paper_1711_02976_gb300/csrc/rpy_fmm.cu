@@ -450,12 +450,13 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
     const int p = D.p, nc = ncoef(p), s = D.s, S = D.S, P1 = p + 1;
     cpx<T> *Mw = reinterpret_cast<cpx<T> *>(smem_raw);
     cpx<T> *Mf = Mw + kSets * nc;
-    cpx<T> *AE = Mf + kSets * nc;       // [s][P1] for the current set
-    cpx<T> *AO = AE + s * P1;
+    cpx<T> *AE = Mf + kSets * nc;       // [s][P1][4 sets]
+    cpx<T> *AO = AE + kSets * s * P1;
     const cpx<T> *src = M + size_t(b) * kSets * nc;
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Mw[i] = src[i];
     __syncthreads();
     size_t base = size_t(b) * kDirs * kSets * S;
+    const int hP = harm_lanes(p);
     for (int f = 0; f < 3; ++f) {
         const cpx<T> *Mu = Mw;
         if (f > 0) {
@@ -463,71 +464,85 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
             __syncthreads();
             Mu = Mf;
         }
-        for (int st = 0; st < kSets; ++st) {
-            // A_k^m split by parity of n + m (the - direction is the reflection (-1)^{n+m}),
-            // stored as 2 i^m A_k^m so that the wave sum below needs no sign logic:
-            // even m feed the real part, odd m the imaginary part.
-            // one thread per node k and column pair (m, p - m): p + 2 terms each
-            const int hP = harm_lanes(p);
-            for (int e = threadIdx.x; e < s * hP; e += blockDim.x) {
-                const int k = e / hP, c = e - k * hP;
-                const T *cc = D.m2x_c + size_t(k) * nc;
-                for (int h = 0; h < 2; ++h) {
-                    const int m = h ? p - c : c;
-                    if (h && m == c) break;
-                    T evx = 0, evy = 0, odx = 0, ody = 0;
-                    for (int n = m; n <= p; n += 2) {
-                        const int i = tri(n, m);
-                        evx = fma(cc[i], Mu[st * nc + i].x, evx);
-                        evy = fma(cc[i], Mu[st * nc + i].y, evy);
-                    }
-                    for (int n = m + 1; n <= p; n += 2) {
-                        const int i = tri(n, m);
-                        odx = fma(cc[i], Mu[st * nc + i].x, odx);
-                        ody = fma(cc[i], Mu[st * nc + i].y, ody);
-                    }
-                    const T sg = m == 0 ? T(1) : (((m >> 1) & 1) ? T(-2) : T(2));   // 2 i^m up to i for odd m
-                    AE[k * P1 + m] = mk(sg * evx, sg * evy);
-                    AO[k * P1 + m] = mk(sg * odx, sg * ody);
+        // A_k^m split by parity of n + m (the - direction is the reflection (-1)^{n+m}),
+        // stored as 2 i^m A_k^m so that the wave sum below needs no sign logic:
+        // even m feed the real part, odd m the imaginary part.  One thread per
+        // (set, node k, column pair (m, p - m)): p + 2 terms each.
+        for (int e = threadIdx.x; e < kSets * s * hP; e += blockDim.x) {
+            const int st = e / (s * hP), r = e - st * s * hP, k = r / hP, c = r - k * hP;
+            const T *cc = D.m2x_c + size_t(k) * nc;
+            const cpx<T> *Ms = Mu + st * nc;
+            for (int h = 0; h < 2; ++h) {
+                const int m = h ? p - c : c;
+                if (h && m == c) break;
+                T evx = 0, evy = 0, odx = 0, ody = 0;
+                for (int n = m; n <= p; n += 2) {
+                    const int i = tri(n, m);
+                    evx = fma(cc[i], Ms[i].x, evx);
+                    evy = fma(cc[i], Ms[i].y, evy);
                 }
+                for (int n = m + 1; n <= p; n += 2) {
+                    const int i = tri(n, m);
+                    odx = fma(cc[i], Ms[i].x, odx);
+                    ody = fma(cc[i], Ms[i].y, ody);
+                }
+                const T sg = m == 0 ? T(1) : (((m >> 1) & 1) ? T(-2) : T(2));   // 2 i^m up to i for odd m
+                AE[(k * P1 + m) * kSets + st] = mk(sg * evx, sg * evy);
+                AO[(k * P1 + m) * kSets + st] = mk(sg * odx, sg * ody);
             }
-            __syncthreads();
-            // W_j = (w_k/M_k) [A^0 + 2 sum_m i^m Re(A^m e^{i m a_j})], A = AE +- AO
-            for (int j = threadIdx.x; j < S; j += blockDim.x) {
-                int k = D.e_k[j];
-                int j0 = D.k_start[k], jl = j - j0, Mk = 2 * (D.k_start[k + 1] - j0);
-                const cpx<T> *rt = D.roots + 2 * j0;
-                const cpx<T> *ae = AE + k * P1;
-                const cpx<T> *ao = AO + k * P1;
-                T er = ae[0].x, orr = ao[0].x, ei = 0, oi = 0;
-                int step2 = 2 * jl;
-                if (step2 >= Mk) step2 -= Mk;
-                int idx = 0;   // (m jl) mod Mk for even m
-                for (int m = 2; m <= p; m += 2) {
-                    idx += step2;
-                    if (idx >= Mk) idx -= Mk;
-                    cpx<T> z = rt[idx];
-                    er = fma(ae[m].x, z.x, er);
-                    er = fma(-ae[m].y, z.y, er);
-                    orr = fma(ao[m].x, z.x, orr);
-                    orr = fma(-ao[m].y, z.y, orr);
-                }
-                idx = jl;      // odd m, starting at m = 1
-                for (int m = 1; m <= p; m += 2) {
-                    cpx<T> z = rt[idx];
-                    ei = fma(ae[m].x, z.x, ei);
-                    ei = fma(-ae[m].y, z.y, ei);
-                    oi = fma(ao[m].x, z.x, oi);
-                    oi = fma(-ao[m].y, z.y, oi);
-                    idx += step2;
-                    if (idx >= Mk) idx -= Mk;
-                }
-                T wm = D.e_wm[j];
-                Xo[base + size_t(2 * f) * kSets * S + st * S + j] = mk(wm * (er + orr), wm * (ei + oi));
-                Xo[base + size_t(2 * f + 1) * kSets * S + st * S + j] = mk(wm * (er - orr), wm * (ei - oi));
-            }
-            __syncthreads();
         }
+        __syncthreads();
+        // W_j = (w_k/M_k) [A^0 + 2 sum_m i^m Re(A^m e^{i m a_j})], A = AE +- AO, all four
+        // sets per wave (one root lookup and index update serve four sets)
+        for (int j = threadIdx.x; j < S; j += blockDim.x) {
+            const int k = D.e_k[j];
+            const int j0 = D.k_start[k], jl = j - j0, Mk = 2 * (D.k_start[k + 1] - j0);
+            const cpx<T> *rt = D.roots + 2 * j0;
+            const cpx<T> *ae = AE + k * P1 * kSets;
+            const cpx<T> *ao = AO + k * P1 * kSets;
+            T er[kSets], orr[kSets], ei[kSets], oi[kSets];
+#pragma unroll
+            for (int st = 0; st < kSets; ++st) {
+                er[st] = ae[st].x;
+                orr[st] = ao[st].x;
+                ei[st] = 0;
+                oi[st] = 0;
+            }
+            int step2 = 2 * jl;
+            if (step2 >= Mk) step2 -= Mk;
+            int idx = 0;   // (m jl) mod Mk for even m
+            for (int m = 2; m <= p; m += 2) {
+                idx += step2;
+                if (idx >= Mk) idx -= Mk;
+                const cpx<T> z = rt[idx];
+#pragma unroll
+                for (int st = 0; st < kSets; ++st) {
+                    const cpx<T> a = ae[m * kSets + st], o = ao[m * kSets + st];
+                    er[st] = fma(-a.y, z.y, fma(a.x, z.x, er[st]));
+                    orr[st] = fma(-o.y, z.y, fma(o.x, z.x, orr[st]));
+                }
+            }
+            idx = jl;      // odd m, starting at m = 1
+            for (int m = 1; m <= p; m += 2) {
+                const cpx<T> z = rt[idx];
+#pragma unroll
+                for (int st = 0; st < kSets; ++st) {
+                    const cpx<T> a = ae[m * kSets + st], o = ao[m * kSets + st];
+                    ei[st] = fma(-a.y, z.y, fma(a.x, z.x, ei[st]));
+                    oi[st] = fma(-o.y, z.y, fma(o.x, z.x, oi[st]));
+                }
+                idx += step2;
+                if (idx >= Mk) idx -= Mk;
+            }
+            const T wm = D.e_wm[j];
+#pragma unroll
+            for (int st = 0; st < kSets; ++st) {
+                Xo[base + size_t(2 * f) * kSets * S + st * S + j] = mk(wm * (er[st] + orr[st]), wm * (ei[st] + oi[st]));
+                Xo[base + size_t(2 * f + 1) * kSets * S + st * S + j] =
+                    mk(wm * (er[st] - orr[st]), wm * (ei[st] - oi[st]));
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -925,7 +940,7 @@ static size_t smem_p2x(int p) {
 template <typename T>
 static size_t smem_m2x(int p, int s) {
     int nc = ncoef(p);
-    return sizeof(cpx<T>) * (2 * kSets * nc + 2 * s * (p + 1));
+    return sizeof(cpx<T>) * (2 * kSets * nc + 2 * kSets * s * (p + 1));
 }
 template <typename T>
 static size_t smem_x2l(int p, int s, int S) {
