@@ -682,6 +682,110 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) dst[i] += Lw[i];
 }
 
+// FP32 form of X2L: the four charge sets in one pass.  The incoming waves of a
+// frame are staged planar (real parts of the four sets in one float4, imaginary
+// parts in another), so that the real DFT, which takes the real parts for even m
+// and the imaginary parts for odd m, reads four sets with one 16-byte load per
+// wave and direction; one root lookup then serves sixteen FMAs.
+__global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi, cpx<float> *L) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int b = b0 + blockIdx.x;
+    const int p = D.p, nc = ncoef(p), s = D.s, S = D.S, P1 = p + 1;
+    float4 *PRe = reinterpret_cast<float4 *>(smem_raw);   // [S] + direction, real parts of sets 0..3
+    float4 *PIm = PRe + S;
+    float4 *MRe = PIm + S;                                  // - direction
+    float4 *MIm = MRe + S;
+    cpx<float> *Bs = reinterpret_cast<cpx<float> *>(MIm + S);   // [s][P1][4] b+ + b-
+    cpx<float> *Bd = Bs + kSets * s * P1;                         // [s][P1][4] b+ - b-
+    cpx<float> *Lf = Bd + kSets * s * P1;                         // [4][nc]
+    cpx<float> *Lw = Lf + kSets * nc;
+    cpx<float> *Lr = Lw + kSets * nc;
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] = mk<float>(0, 0);
+    for (int f = 0; f < 3; ++f) {
+        __syncthreads();
+        const cpx<float> *sp = Xi + (size_t(b) * kDirs + 2 * f) * kSets * S;
+        const cpx<float> *sm = Xi + (size_t(b) * kDirs + 2 * f + 1) * kSets * S;
+        for (int j = threadIdx.x; j < S; j += blockDim.x) {
+            const cpx<float> p0 = sp[j], p1 = sp[S + j], p2 = sp[2 * S + j], p3 = sp[3 * S + j];
+            const cpx<float> m0 = sm[j], m1 = sm[S + j], m2 = sm[2 * S + j], m3 = sm[3 * S + j];
+            PRe[j] = make_float4(p0.x, p1.x, p2.x, p3.x);
+            PIm[j] = make_float4(p0.y, p1.y, p2.y, p3.y);
+            MRe[j] = make_float4(m0.x, m1.x, m2.x, m3.x);
+            MIm[j] = make_float4(m0.y, m1.y, m2.y, m3.y);
+        }
+        __syncthreads();
+        // b_k^m = 2 sum_j Re(I_j) e^{-i m a_j} (m even), 2i sum_j Im(I_j) e^{-i m a_j} (m odd)
+        for (int e = threadIdx.x; e < s * P1; e += blockDim.x) {
+            const int k = e / P1, m = e - k * P1;
+            const int j0 = D.k_start[k], j1 = D.k_start[k + 1];
+            const int Mk = 2 * (j1 - j0), mm = m % Mk;
+            const cpx<float> *rt = D.roots + 2 * j0;
+            const float4 *vp = (m & 1) ? PIm : PRe;
+            const float4 *vm = (m & 1) ? MIm : MRe;
+            float bpx[kSets] = {0, 0, 0, 0}, bpy[kSets] = {0, 0, 0, 0};
+            float bmx[kSets] = {0, 0, 0, 0}, bmy[kSets] = {0, 0, 0, 0};
+            int idx = 0;
+            for (int j = j0; j < j1; ++j) {
+                const cpx<float> r = rt[idx];
+                const float4 a = vp[j], c = vm[j];
+                const float av[kSets] = {a.x, a.y, a.z, a.w}, cv[kSets] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int st = 0; st < kSets; ++st) {
+                    bpx[st] = fmaf(av[st], r.x, bpx[st]);
+                    bpy[st] = fmaf(-av[st], r.y, bpy[st]);
+                    bmx[st] = fmaf(cv[st], r.x, bmx[st]);
+                    bmy[st] = fmaf(-cv[st], r.y, bmy[st]);
+                }
+                idx += mm;
+                if (idx >= Mk) idx -= Mk;
+            }
+#pragma unroll
+            for (int st = 0; st < kSets; ++st) {
+                Bs[e * kSets + st] = mk(bpx[st] + bmx[st], bpy[st] + bmy[st]);
+                Bd[e * kSets + st] = mk(bpx[st] - bmx[st], bpy[st] - bmy[st]);
+            }
+        }
+        __syncthreads();
+        // L_n^m = i^m sum_k (-lambda_k)^n / sqrt((n-m)!(n+m)!) b_k^m, the - direction reflected
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+            const int n = deg_of(i), m = i - tri(n, 0);
+            const cpx<float> *Bx = ((n + m) & 1) ? Bd : Bs;
+            float ax[kSets] = {0, 0, 0, 0}, ay[kSets] = {0, 0, 0, 0};
+            for (int k = 0; k < s; ++k) {
+                const float c = D.x2l_c[size_t(k) * nc + i];
+                const float4 *bb = reinterpret_cast<const float4 *>(Bx + (k * P1 + m) * kSets);
+                const float4 b01 = bb[0], b23 = bb[1];
+                ax[0] = fmaf(c, b01.x, ax[0]);
+                ay[0] = fmaf(c, b01.y, ay[0]);
+                ax[1] = fmaf(c, b01.z, ax[1]);
+                ay[1] = fmaf(c, b01.w, ay[1]);
+                ax[2] = fmaf(c, b23.x, ax[2]);
+                ay[2] = fmaf(c, b23.y, ay[2]);
+                ax[3] = fmaf(c, b23.z, ax[3]);
+                ay[3] = fmaf(c, b23.w, ay[3]);
+            }
+#pragma unroll
+            for (int st = 0; st < kSets; ++st) Lf[st * nc + i] = mul_ipow(mk(2 * ax[st], 2 * ay[st]), m + (m & 1));
+        }
+        __syncthreads();
+        if (f == 0) {
+            for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lf[i];
+        } else {
+            rotate_sets(D.rot_bwd + size_t(f - 1) * D.rot_len, D.rot_off, p, Lf, Lr);
+            __syncthreads();
+            for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lr[i];
+        }
+    }
+    __syncthreads();
+    cpx<float> *dst = L + size_t(b) * kSets * nc;
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) dst[i] += Lw[i];
+}
+
+static size_t smem_x2l4(int p, int s, int S) {
+    const int nc = ncoef(p);
+    return sizeof(float4) * 4 * size_t(S) + sizeof(cpx<float>) * (2 * kSets * s * (p + 1) + 3 * kSets * nc);
+}
+
 // ---------------------------------------------------------------- far-field evaluation
 constexpr int kNE = 18;   // evaluation expansions of Eq. (2.8) per box
 constexpr int kNF = 12;   // of them evaluated per bead after the fold in k_eval_prep
@@ -1036,9 +1140,15 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
         RPY_CHECK(cudaGetLastError());
     }
     prof_mark(t, RPY_STAGE_X2L, st);
-    size_t sxl = smem_x2l<T>(p, D.s, D.S);
-    RPY_TRY(set_smem(k_x2l<T>, sxl));
-    k_x2l<T><<<n2, 256, sxl, st>>>(b2, n2, D, Xi, L);
+    if constexpr (sizeof(T) == 4) {
+        size_t sxl = smem_x2l4(p, D.s, D.S);
+        RPY_TRY(set_smem(k_x2l4, sxl));
+        k_x2l4<<<n2, 256, sxl, st>>>(b2, n2, D, Xi, L);
+    } else {
+        size_t sxl = smem_x2l<T>(p, D.s, D.S);
+        RPY_TRY(set_smem(k_x2l<T>, sxl));
+        k_x2l<T><<<n2, 256, sxl, st>>>(b2, n2, D, Xi, L);
+    }
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     // X list
