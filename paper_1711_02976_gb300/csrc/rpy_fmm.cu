@@ -551,6 +551,7 @@ template <typename T>
 __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const int *child, const int *leaf,
                       const cpx<T> *Xo, cpx<T> *Xi) {
     __shared__ int src[216];
+    __shared__ int vsrc[216], vsh[216], vpre[217];   // the present sources, compacted in slot order
     int P = parents[blockIdx.x];
     int d = blockIdx.y;
     const int S = D.S;
@@ -564,30 +565,51 @@ __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const
     const int *goff = D.grp_off + d * (kGroupMax + 1);
     const int *gmask = D.grp_mask + d * kGroupMax;
     const int *slots = D.slot_list + d * 216;
+    // warp 0: keep the slots whose source box exists; vpre[z] = present slots before z,
+    // so group g covers vsrc[vpre[goff[g]] .. vpre[goff[g + 1]])
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, nsl = goff[ng];
+        int carry = 0;
+        for (int z0 = 0; z0 < nsl; z0 += 32) {
+            const int z = z0 + lane;
+            int ent = 0, sb = -1;
+            if (z < nsl) {
+                ent = slots[z];
+                sb = src[ent & 255];
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, sb >= 0);
+            const int pos = carry + __popc(bal & ((1u << lane) - 1u));
+            if (z < nsl) vpre[z] = pos;
+            if (sb >= 0) {
+                vsrc[pos] = sb;
+                vsh[pos] = ent >> 8;
+            }
+            carry += __popc(bal);
+        }
+        if (lane == 0) vpre[nsl] = carry;
+    }
+    __syncthreads();
     int ch[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) ch[t] = child[8 * P + t];
+    const size_t dstride = size_t(kDirs) * kSets * S;
+    const cpx<T> *Xd = Xo + size_t(d) * kSets * S;
     for (int e = threadIdx.x; e < kSets * S; e += blockDim.x) {
         int j = e % S;
         cpx<T> acc[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) acc[t] = mk<T>(0, 0);
         for (int g = 0; g < ng; ++g) {
+            const int z0 = vpre[goff[g]], z1 = vpre[goff[g + 1]];
+            if (z0 == z1) continue;   // block-uniform: no source box of this group exists
             cpx<T> ga = mk<T>(0, 0);
-            bool any = false;
-            for (int z = goff[g]; z < goff[g + 1]; ++z) {
-                int ent = slots[z];
-                int sb = src[ent & 255];
-                if (sb < 0) continue;
-                any = true;
-                cpx<T> x = Xo[(size_t(sb) * kDirs + d) * kSets * S + e];
-                cpx<T> sh = D.shift[size_t(ent >> 8) * S + j];
-                ga.x = fma(x.x, sh.x, ga.x);
-                ga.x = fma(-x.y, sh.y, ga.x);
-                ga.y = fma(x.x, sh.y, ga.y);
-                ga.y = fma(x.y, sh.x, ga.y);
+#pragma unroll 4
+            for (int z = z0; z < z1; ++z) {
+                const cpx<T> x = Xd[size_t(vsrc[z]) * dstride + e];
+                const cpx<T> sh = D.shift[size_t(vsh[z]) * S + j];
+                ga.x = fma(-x.y, sh.y, fma(x.x, sh.x, ga.x));
+                ga.y = fma(x.y, sh.x, fma(x.x, sh.y, ga.y));
             }
-            if (!any) continue;   // the uniform src[] makes this branch block-uniform
             int mask = gmask[g];
 #pragma unroll
             for (int t = 0; t < 8; ++t)
