@@ -53,7 +53,7 @@ __global__ void k_pair_const(int nsys, const double *a_, const double *s_, const
     c.icube = 1.0 / cube[4 * k + 3];
     const double co_cf = c.co / c.cf;
     c.f_a2x4 = float(c.a2x4);
-    c.f_tiny2 = float(1e-6 * a * a);
+    c.f_tiny2 = fmaxf(float(1e-6 * a * a), 1e-36f);   // a normal FP32 number
     c.f_k23 = float(c.k23);
     c.f_nk2 = float(c.nk2);
     c.f_co_cf = float(co_cf);

@@ -235,6 +235,14 @@ __device__ __forceinline__ void pair_tiny64(int jg, int i, double a, double co, 
     overlap_pair(ddx, ddy, ddz, ddx * ddx + ddy * ddy + ddz * ddz, fs[jg], fs[n + jg], fs[2 * n + jg], a, co, acc);
 }
 
+// Hardware reciprocal square root, flushing subnormals (the argument here is at
+// least 1e-6 a^2, kept normal by k_pair_const).
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // One pair, both branches without divergence, in units of s/(8 pi), with
 // ri = 1/max(r, 1e-3 a):
 //   r >= 2a          :  t1 = ri + k23 ri^3,      c = ri^3 (1 - 2a^2 ri^2)
@@ -243,7 +251,7 @@ __device__ __forceinline__ void pair_tiny64(int jg, int i, double a, double co, 
 //   u += t1 F + c (R.F) R
 __device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, float fx, float fy, float fz,
                                        const P32Const &k, float &px, float &py, float &pz) {
-    const float ri = rsqrtf(fmaxf(r2, k.tiny2));
+    const float ri = rsqrt_ftz(fmaxf(r2, k.tiny2));
     const float ri2 = ri * ri;
     const float B = ri * ri2;
     const bool far = r2 >= k.a2x4, on = r2 > k.tiny2;
