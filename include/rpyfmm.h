@@ -284,6 +284,43 @@ enum {
 int rpy_tree_set_profiling(rpy_tree t, int enable);
 int rpy_tree_stage_times(rpy_tree t, double *ms_host, int n);
 
+/* ------------------------------------------------------------------ Brownian dynamics
+ * Consumers of repeated matvecs on a resident tree (Sec. 1: the drift D F and a
+ * random displacement with covariance 2 dt D of the Ermak-McCammon step).
+ *
+ * rpy_lanczos_sqrt: y = D^{1/2} z approximated by the Lanczos process on D
+ * (one matvec per step; Krylov basis kept on the device, m_max x 3N doubles):
+ * y_m = |z| V_m T_m^{1/2} e_1 with T_m the m x m Lanczos tridiagonal matrix.
+ * Stops when the relative change |y_m - y_(m-1)| / |y_m| <= tol or after m_max
+ * steps.
+ *   z_dev              device, N x 3 FP64 (caller order), e.g. N(0,1) samples
+ *   kT_over_eta_host   host, one value per system
+ *   m_max              1..1000; tol >= 0
+ *   y_dev              device, N x 3 FP64 (written)
+ *   iters, rel_change  host, may be NULL: steps taken, last relative change
+ * Allocates and frees device scratch; synchronises `stream`.
+ */
+int rpy_lanczos_sqrt(rpy_tree t, const double *z_dev, const double *kT_over_eta_host, int m_max, double tol,
+                     double *y_dev, int *iters, double *rel_change, void *stream);
+
+/*
+ * One Ermak-McCammon step (no divergence term: the RPY tensor is divergence
+ * free): r <- r + (dt / kT) D F + sqrt(2 dt) D^{1/2} xi, with D evaluated at the
+ * tree's current positions (kT/eta per system), D^{1/2} xi by rpy_lanczos_sqrt,
+ * then the tree is rebuilt for the new positions (rpy_tree_update_positions).
+ *   pos_dev    device, N x 3: on entry the positions the tree was built for,
+ *              on return the new positions
+ *   f_dev      device, N x 3 forces; xi_dev device, N x 3 N(0,1) samples
+ *              (drawn by the caller)
+ *   kT_host, eta_host   host, one value per system (> 0)
+ *   dt         time step (>= 0)
+ *   disp_dev   device, N x 3 displacement of the step (written), or NULL
+ * Synchronises `stream`.
+ */
+int rpy_bd_step(rpy_tree t, double *pos_dev, const double *f_dev, const double *xi_dev, const double *kT_host,
+                const double *eta_host, double dt, int m_max, double tol, double *disp_dev, int *iters,
+                void *stream);
+
 /* ------------------------------------------------------------------ tuning
  * FP64 direct sum of u_t = sum_j D_tj F_j at chosen targets t (caller
  * indices into the whole array), over all beads j of t's system (Sec. 1:

@@ -23,7 +23,8 @@ __all__ = [
     "rpy_matvec_oneshot", "rpy_matvec_host", "rpy_laplace_far", "rpy_tree_export", "rpy_tree_stats",
     "rpy_tree_sync", "rpy_tree_footprint", "rpy_tree_free", "rpy_strerror", "rpy_last_cuda_error",
     "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times", "rpy_launch_count",
-    "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_direct_sampled", "rpy_autotune", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
+    "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt",
+    "rpy_bd_step", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
     "RPY_PART_ALL", "EXPORTED_SYMBOLS",
 ]
 
@@ -44,7 +45,7 @@ EXPORTED_SYMBOLS = [
     "rpy_last_cuda_error", "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times",
     "rpy_launch_count", "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_server_create", "rpy_server_add_system",
     "rpy_server_submit", "rpy_server_wait", "rpy_server_cancel", "rpy_server_drain", "rpy_server_stats_get",
-    "rpy_server_destroy", "rpy_direct_sampled", "rpy_autotune",
+    "rpy_server_destroy", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt", "rpy_bd_step",
 ]
 STAGES = ["gather", "p2p", "p2m", "m2m", "m2x", "x2x", "x2l", "p2l", "l2l", "eval", "combine"]
 
@@ -156,6 +157,8 @@ def load(build_if_missing: bool = True):
             "rpy_direct_sampled": [vp, vp, i, vp, vp, vp, vp, i64, vp, vp],
             "rpy_autotune": [vp, vp, i, vp, vp, vp, i, i, ctypes.POINTER(AutotuneParams),
                              ctypes.POINTER(AutotuneResult), vp],
+            "rpy_lanczos_sqrt": [vp, vp, vp, i, d, vp, ctypes.POINTER(i), ctypes.POINTER(d), vp],
+            "rpy_bd_step": [vp, vp, vp, vp, vp, vp, d, i, d, vp, ctypes.POINTER(i), vp],
             "rpy_server_create": [ctypes.POINTER(ServerParams), ctypes.POINTER(vp)],
             "rpy_server_add_system": [vp, vp, i64, d, ctypes.POINTER(BuildParams), ctypes.POINTER(i)],
             "rpy_server_submit": [vp, i, vp, vp, d, vp, ctypes.POINTER(i64)],
@@ -304,6 +307,30 @@ def rpy_autotune(pos, sys_offsets, a, f, kT_over_eta, digits, precision=RPY_FP64
         "est_rel_l2": res.est_rel_l2, "matvec_ms": res.matvec_ms, "goal": res.goal, "tune_ms": res.tune_ms,
         "trials": [{k: getattr(res.trials[i], k) for k, _ in AutotuneTrial._fields_} for i in range(res.n_trials)],
     }
+
+
+def rpy_lanczos_sqrt(tree, z, kT_over_eta, y, m_max=60, tol=1e-8, stream=None):
+    """y = D^{1/2} z by Lanczos on the tree's D (device tensors, N x 3); returns (steps, last relative change)."""
+    nsys = tree.nsys if isinstance(tree, Tree) else 1
+    sv = np.ascontiguousarray(np.broadcast_to(np.asarray(kT_over_eta, dtype=np.float64), (nsys,)))
+    it, ch = ctypes.c_int(), ctypes.c_double()
+    _check(load().rpy_lanczos_sqrt(_h(tree), _dev_f64(z, "z"), sv.ctypes.data, int(m_max), float(tol),
+                                   _dev_f64(y, "y"), ctypes.byref(it), ctypes.byref(ch), _stream(stream)),
+           "rpy_lanczos_sqrt")
+    return it.value, ch.value
+
+
+def rpy_bd_step(tree, pos, f, xi, kT, eta, dt, m_max=60, tol=1e-8, disp=None, stream=None) -> int:
+    """One Ermak-McCammon step on device tensors (pos updated in place, tree rebuilt); returns Lanczos steps."""
+    nsys = tree.nsys if isinstance(tree, Tree) else 1
+    kt = np.ascontiguousarray(np.broadcast_to(np.asarray(kT, dtype=np.float64), (nsys,)))
+    et = np.ascontiguousarray(np.broadcast_to(np.asarray(eta, dtype=np.float64), (nsys,)))
+    it = ctypes.c_int()
+    _check(load().rpy_bd_step(_h(tree), _dev_f64(pos, "pos"), _dev_f64(f, "f"), _dev_f64(xi, "xi"), kt.ctypes.data,
+                              et.ctypes.data, float(dt), int(m_max), float(tol),
+                              _dev_f64(disp, "disp") if disp is not None else None, ctypes.byref(it),
+                              _stream(stream)), "rpy_bd_step")
+    return it.value
 
 
 def rpy_tree_update_positions(tree, pos, stream=None):

@@ -265,17 +265,6 @@ static int device_tables(int dev, int p, int digits, DevTableSet **out) {
 
 // ---------------------------------------------------------------- helpers
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 static int have_device() {
     int n = 0;
@@ -297,6 +286,8 @@ static void mark_done(Tree &t, cudaStream_t st) {
 static cudaError_t wait_done(Tree &t) { return t.done ? cudaEventSynchronize(t.done) : cudaSuccess; }
 
 static bool valid(rpy_tree t) { return t && t->magic == 0x52505954u; }
+
+Tree *tree_of(rpy_tree h) { return valid(h) ? &h->t : nullptr; }
 
 static int alloc_tree_arrays(Tree &t, cudaStream_t st) {
     int64_t n = t.n;

@@ -279,6 +279,22 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
               const SysConst &sc, cudaStream_t st);
 int run_p2p(Tree &t, const double *fs, double *out, const SysConst &sc, cudaStream_t st, bool direct_list);
 int split_positions_f32(Tree &t, cudaStream_t st);
+// the tree of a valid handle, else nullptr
+Tree *tree_of(rpy_tree h);
+
+// Makes `dev` current for the scope, restoring the caller's device after.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 const char *last_cuda_error_text();
 
 // matvec stages (rpy_fmm.cu / rpy_p2p.cu)

@@ -60,6 +60,11 @@ def test_strerror_and_validation_without_device():
                             ctypes.byref(res), None) == -2
     assert lib.rpy_autotune(fake, off.ctypes.data, 1, av.ctypes.data, fake, sv.ctypes.data, 3, 0, None,
                             None, None) == -1
+    it, ch = ctypes.c_int(), ctypes.c_double()
+    assert lib.rpy_lanczos_sqrt(None, fake, sv.ctypes.data, 10, 1e-8, fake, ctypes.byref(it), ctypes.byref(ch),
+                                None) == -1
+    assert lib.rpy_bd_step(None, fake, fake, fake, sv.ctypes.data, sv.ctypes.data, 1e-3, 10, 1e-8, None,
+                           ctypes.byref(it), None) == -1
     if not has_gpu:
         assert lib.rpy_direct_sampled(fake, off.ctypes.data, 1, av.ctypes.data, fake, sv.ctypes.data,
                                       tg.ctypes.data, 2, u.ctypes.data, None) == -8
