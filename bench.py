@@ -192,7 +192,10 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
     s_list = sysm.s_list if forest else [sysm.s]
     tune = None
     bp = {"leaf_cap": cfg["leaf_cap"], "order_p": 0, "direct_w": 0, "direct_x": 0, "quad": 0}
-    if args.autotune:
+    if getattr(args, "params", None):
+        vals = [int(v) for v in args.params.split(",")]
+        bp = dict(zip(("leaf_cap", "order_p", "direct_w", "direct_x", "quad"), vals))
+    elif args.autotune:
         # parameter search (untimed): order p, leaf capacity and direct-substitution
         # thresholds, by sampled-target error against the GPU direct sum and timed matvecs
         tune = rp.rpy_autotune(P, off, a_list, F, s_list, cfg["digits"], cfg["precision"])
@@ -264,7 +267,8 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
                    "l2": "flushed between timed steps (256 MB write)", "step": "tree build + matvec",
                    "leaf_cap": stats["leaf_cap"], "order_p": stats["order_p"], "exp_terms": stats["exp_terms"],
                    "direct_w": bp["direct_w"], "direct_x": bp["direct_x"], "quad_rule": stats["quad"],
-                   "params": "autotuned" if tune is not None else "defaults"},
+                   "params": "autotuned" if tune is not None else ("fixed" if getattr(args, "params", None)
+                                                                    else "defaults")},
         "build_ms": round(statistics.median(tb), 4), "matvec_ms": round(statistics.median(tm), 4),
         "matvec_only_mbeads_s": round(ws * n / (statistics.median(tm) * 1e-3) / 1e6, 4),
         "resident_tree_matvec_ms": round(statistics.median(reps), 4),
@@ -467,6 +471,49 @@ def serve(args, local):
     return out
 
 
+def bd(args, local):
+    """Brownian-dynamics form: Ermak-McCammon steps (drift D F and Lanczos D^{1/2} xi on the
+    resident tree, then the rebuild for the new positions) on the default workload, with the
+    autotuned parameters; fresh N(0,1) forces and xi every step."""
+    import torch
+    import paper_1711_02976_gb300 as rp
+    torch.cuda.set_device(local)
+    cfg = CONFIGS[args.config]
+    sysm = make_workload(args.config)
+    forest = isinstance(sysm, Forest)
+    n = sysm.n
+    off = sysm.off if forest else [0, n]
+    a_list = sysm.a_list if forest else [sysm.a]
+    s_list = sysm.s_list if forest else [sysm.s]
+    P = torch.from_numpy(sysm.pos).cuda()
+    F = torch.from_numpy(sysm.f).cuda()
+    tune = rp.rpy_autotune(P, off, a_list, F, s_list, cfg["digits"], cfg["precision"])
+    bp = {k: tune["best"][k] for k in ("leaf_cap", "order_p", "direct_w", "direct_x", "quad")}
+    tree = rp.rpy_forest_build(P, off, a_list, cfg["digits"], precision=cfg["precision"], **bp)
+    rng = torch.Generator(device="cuda").manual_seed(77)
+    a0 = float(np.min(a_list))
+    kT, eta = 1.0, 1.0 / (6 * math.pi * a0)   # kT/eta = 6 pi a: D_ii = 1 for the smallest bead
+    dt = 1e-3 * a0 * a0                        # rms step sqrt(2 dt) ~ 0.045 a
+    tol = 1e-3   # relative change of the Lanczos noise vector between steps
+    its, ts = [], []
+    for k in range(args.warmup + args.steps):
+        F.normal_(generator=rng)
+        xi = torch.randn(P.shape, dtype=torch.float64, device="cuda", generator=rng)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it = rp.rpy_bd_step(tree, P, F, xi, kT, eta, dt, m_max=60, tol=tol)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ts.append(time.perf_counter() - t0)
+            its.append(it)
+    t = statistics.median(ts)
+    return {"mode": "bd", "metric": "Ermak-McCammon steps/s (drift + Lanczos noise + rebuild)",
+            "value": round(1.0 / t, 4), "unit": "steps/s", "ms_per_step": round(t * 1e3, 2),
+            "Mbead_steps_per_s": round(n / t / 1e6, 4), "lanczos_iters_median": statistics.median(its),
+            "lanczos_tol": tol, "dt": dt, "n_beads": n, "workload": args.config, "params": bp,
+            "matvecs_per_step": 1 + statistics.median(its)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -479,7 +526,10 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32 precision-form measurement")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="build with the default leaf capacity / order instead of the autotuner's choice")
-    ap.add_argument("--mode", default="bench", choices=["bench", "serve"])
+    ap.add_argument("--params", default=None,
+                    help="fixed build parameters leaf_cap,order_p,direct_w,direct_x,quad (no autotuning), "
+                         "e.g. to profile the autotuned configuration")
+    ap.add_argument("--mode", default="bench", choices=["bench", "serve", "bd"])
     ap.add_argument("--serve-systems", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -518,6 +568,10 @@ def main():
         if rank == 0:
             print(json.dumps(serve(args, local)), flush=True)
         return
+    if args.mode == "bd":
+        if rank == 0:
+            print(json.dumps(bd(args, local)), flush=True)
+        return
     result, sysm, u_dev, stats, stage_ms, _ = run_ours(args, ws, rank, local)
     import paper_1711_02976_gb300 as rp
     peaks = {"fp64": rp.rpy_alu_peak(rp.RPY_FP64), "fp32": rp.rpy_alu_peak(rp.RPY_FP32)}
@@ -526,7 +580,7 @@ def main():
     if not args.no_e2e:
         c = result["config"]
         bp = ({k: c[k] for k in ("leaf_cap", "order_p", "direct_w", "direct_x")} | {"quad": c["quad_rule"]}
-              if c["params"] == "autotuned" else None)
+              if c["params"] in ("autotuned", "fixed") else None)
         result["e2e"] = e2e_host(args, sysm, CONFIGS[args.config], bp)
     if rank == 0:
         import oracle
