@@ -44,6 +44,9 @@ CONFIGS = {
                                  desc="4,096 beads uniform cube, a=0.004, 3-digit, FP64, leaf cap 40"),
     "cube15m_3digit_fp32": dict(gen="config3", digits=3, precision=1, leaf_cap=0,
                                 desc="15,000,000 beads uniform cube, a=2e-5, 3-digit, FP32 precision form"),
+    "cube15m_3digit_fp64": dict(gen="config3", digits=3, precision=0, leaf_cap=0,
+                                desc="15,000,000 beads uniform cube, a=2e-5, 3-digit, FP64 (the FP32 precision "
+                                     "form of the same workload is measured beside it)"),
     "sphere200k_6digit_fp64": dict(gen="sphere200k", digits=6, precision=0, leaf_cap=0,
                                    desc="200,000 beads: sphere surface + 10% cube (seed 2), a=1e-4, 6-digit, FP64 "
                                         "(small case for ncu captures)"),

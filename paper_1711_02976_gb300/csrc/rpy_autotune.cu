@@ -325,7 +325,8 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
     rpy_build_params base{};
     base.digits = digits;
     base.precision = precision;
-    const int pdef = default_order(digits), capdef = default_leaf_cap(digits);
+    const int pdef = default_order(digits);
+    int capdef = default_leaf_cap(digits);   // doubled below while its tree does not fit on the device
     const int plo = digits == 3 ? 4 : 8, phi = digits == 3 ? 12 : 24;
     base.leaf_cap = capdef;
 
@@ -367,6 +368,7 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
         while (p + 1 <= phi) {
             ++p;
             Trial T = err_at(q, p);
+            if (T.status == RPY_ERR_OOM) break;   // a higher order does not fit either
             if (T.status != RPY_OK) return {best_p, best_err, false, T.status};
             if (T.err < best_err) {
                 best_err = T.err;
@@ -389,6 +391,13 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
     int pstart = pdef;
     for (int q : rules) {
         OrderPick pk = search_p(q, pstart);
+        // small leaf capacities on large uniform systems make millions of boxes, each
+        // with its plane-wave expansions: double the capacity until the tree fits
+        while (pk.status == RPY_ERR_OOM && capdef < 4096) {
+            capdef *= 2;
+            base.leaf_cap = capdef;
+            pk = search_p(q, pstart);
+        }
         RPY_TRY(pk.status);
         if (!pk.ok) {
             if (!best_ok && pk.err < best_err) {
