@@ -316,44 +316,35 @@ def roofline(result, stats, stage_ms, peaks):
 
 
 def e2e_host(args, sysm, cfg, bp=None):
-    """The same work through the public API with host data: H2D of positions
-    and forces from pinned memory, build, matvec, D2H of velocities, every step
-    (rpy_matvec_host for one system at the default parameters; otherwise the
-    binding calls rpy_forest_build with the benchmark's build parameters,
-    rpy_forest_matvec and the copies)."""
+    """The same work through the public API with host data, every step: H2D of the
+    positions from pinned memory, rpy_tree_update_positions (the tree built on the first
+    call stays resident, as in a Brownian-dynamics loop), H2D of the forces, the matvec,
+    D2H of the velocities.  One system at the default parameters without a resident tree
+    would use rpy_matvec_host (one call: copies, build, matvec, copy back)."""
     import torch
     import paper_1711_02976_gb300 as rp
     n = sysm.n
     pos_h = torch.from_numpy(sysm.pos).pin_memory()
     f_h = torch.from_numpy(sysm.f).pin_memory()
     u_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
-    lib = rp.load()
     forest = isinstance(sysm, Forest)
-    if forest or bp is not None:
-        P = torch.empty((n, 3), dtype=torch.float64, device="cuda")
-        F = torch.empty_like(P)
-        U = torch.empty_like(P)
-        off = sysm.off if forest else [0, n]
-        a_list = sysm.a_list if forest else [sysm.a]
-        s_list = sysm.s_list if forest else [sysm.s]
-        kw = bp if bp is not None else {"leaf_cap": cfg["leaf_cap"]}
+    P = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    F = torch.empty_like(P)
+    U = torch.empty_like(P)
+    off = sysm.off if forest else [0, n]
+    a_list = sysm.a_list if forest else [sysm.a]
+    s_list = sysm.s_list if forest else [sysm.s]
+    kw = bp if bp is not None else {"leaf_cap": cfg["leaf_cap"]}
+    P.copy_(pos_h)
+    tree = rp.rpy_forest_build(P, off, a_list, cfg["digits"], precision=cfg["precision"], **kw)
 
-        def call():
-            P.copy_(pos_h, non_blocking=True)
-            F.copy_(f_h, non_blocking=True)
-            t = rp.rpy_forest_build(P, off, a_list, cfg["digits"], precision=cfg["precision"], **kw)
-            rp.rpy_forest_matvec(t, F, s_list, U)
-            u_h.copy_(U, non_blocking=True)
-            torch.cuda.synchronize()
-            t.close()
-        api = "rpy_forest_build + rpy_forest_matvec (pinned host arrays in, velocities out)"
-    else:
-        def call():
-            st = lib.rpy_matvec_host(pos_h.data_ptr(), n, sysm.a, f_h.data_ptr(), sysm.s, cfg["digits"],
-                                     cfg["precision"], u_h.data_ptr(), rp._stream(None))
-            if st:
-                raise rp.RpyError(st, "rpy_matvec_host")
-        api = "rpy_matvec_host (pinned host arrays in, velocities out)"
+    def call():
+        P.copy_(pos_h, non_blocking=True)
+        rp.rpy_tree_update_positions(tree, P)
+        F.copy_(f_h, non_blocking=True)
+        rp.rpy_forest_matvec(tree, F, s_list, U)
+        u_h.copy_(U, non_blocking=True)
+        torch.cuda.synchronize()
     for _ in range(2):
         call()
     torch.cuda.synchronize()
@@ -361,11 +352,13 @@ def e2e_host(args, sysm, cfg, bp=None):
     for _ in range(max(2, min(args.steps, 5))):
         t0 = time.perf_counter()
         call()
-        torch.cuda.synchronize()
         ts.append(time.perf_counter() - t0)
+    tree.close()
     t = statistics.median(ts)
     return {"value": round(n / t / 1e6, 4), "unit": "Mbeads/s", "h2d_bytes_per_step": 2 * n * 3 * 8,
-            "d2h_bytes_per_step": n * 3 * 8, "ms_per_step": round(t * 1e3, 3), "api": api}
+            "d2h_bytes_per_step": n * 3 * 8, "ms_per_step": round(t * 1e3, 3),
+            "api": "per step: H2D positions, rpy_tree_update_positions, H2D forces, rpy_forest_matvec, D2H "
+                   "velocities (pinned host arrays, resident tree)"}
 
 
 def cpu_oracle_sample(sysm, k):

@@ -195,6 +195,24 @@ int rpy_matvec_host(const double *pos_host, int64_t n, double a, const double *f
                     double kT_over_eta, int digits, int precision, double *u_host, void *stream);
 
 /*
+ * The paper's evaluate(sources, targets) form (Sec. 4.2): velocities at nt target
+ * points from ns source beads of radius a with forces f,
+ *   u_t = sum_j D(t, j) F_j,
+ * D the same tensor as between two beads of radius a (the overlap branch for
+ * r < 2a, the r -> 0 limit for a target on a source); targets exert no force and
+ * have no self term.  One tree is built over the union of sources and targets
+ * (targets as beads with zero force), applied once and freed.
+ *   src_pos_dev, src_f_dev   device, ns x 3 FP64
+ *   tgt_pos_dev              device, nt x 3 FP64
+ *   params                   build parameters (digits, precision, ...)
+ *   u_tgt_dev                device, nt x 3 FP64 (written)
+ * Allocates and frees device scratch; synchronises `stream`.
+ */
+int rpy_evaluate(const double *src_pos_dev, const double *src_f_dev, int64_t ns, const double *tgt_pos_dev,
+                 int64_t nt, double a, double kT_over_eta, const rpy_build_params *params, double *u_tgt_dev,
+                 void *stream);
+
+/*
  * Laplace far field of the tree (Sec. 2): for four charge sets q (device,
  * N x 4 FP64, caller order) returns, at every bead, the FMM part of the
  * potential, its gradient and its Hessian (device, N x 4 x 13 FP64:

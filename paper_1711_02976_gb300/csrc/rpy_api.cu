@@ -636,6 +636,46 @@ int rpy_matvec_host(const double *pos_host, int64_t n, double a, const double *f
     return rc;
 }
 
+int rpy_evaluate(const double *src_pos_dev, const double *src_f_dev, int64_t ns, const double *tgt_pos_dev,
+                 int64_t nt, double a, double s, const rpy_build_params *params, double *u_tgt_dev, void *stream) {
+    if (!src_pos_dev || !src_f_dev || !tgt_pos_dev || !u_tgt_dev || !params || ns < 1 || nt < 1 ||
+        !std::isfinite(s) || !(a > 0.0) || !std::isfinite(a))
+        return RPY_ERR_INVALID;
+    RPY_TRY(check_params(*params));
+    RPY_TRY(have_device());
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = ns + nt;
+    Tree scratch;
+    double *d = nullptr;
+    RPY_TRY(dev_alloc(scratch, (void **)&d, sizeof(double) * 9 * size_t(n)));
+    double *dp = d, *df = d + 3 * n, *du = d + 6 * n;
+    int rc = RPY_OK;
+    rpy_tree t = nullptr;
+    do {
+        // the union of sources and targets, targets as beads without force
+        cudaError_t e = cudaMemcpyAsync(dp, src_pos_dev, sizeof(double) * 3 * ns, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dp + 3 * ns, tgt_pos_dev, sizeof(double) * 3 * nt, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(df, src_f_dev, sizeof(double) * 3 * ns, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(df + 3 * ns, 0, sizeof(double) * 3 * nt, st);
+        if (e != cudaSuccess) {
+            rc = check_cuda("evaluate copies", e);
+            break;
+        }
+        const int64_t off[2] = {0, n};
+        rc = rpy_forest_build(dp, off, 1, &a, params, stream, &t);
+        if (rc != RPY_OK) break;
+        rc = rpy_forest_matvec(t, df, &s, du, stream);
+        if (rc != RPY_OK) break;
+        e = cudaMemcpyAsync(u_tgt_dev, du + 3 * ns, sizeof(double) * 3 * nt, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = check_cuda("evaluate", e);
+    } while (0);
+    if (t) rpy_tree_free(t);
+    tree_release(scratch);
+    return rc;
+}
+
 int rpy_laplace_far(rpy_tree h, const double *q_dev, double *out_dev, void *stream) {
     if (!valid(h) || !q_dev || !out_dev) return RPY_ERR_INVALID;
     Tree &t = h->t;

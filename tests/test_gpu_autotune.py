@@ -74,3 +74,22 @@ def test_autotune_choice_meets_the_setting(digits, precision):
     err = oracle.rel_l2(U.cpu().numpy()[tg], ref)
     assert err <= bound, (err, best)
     t.close()
+
+
+def test_evaluate_sources_at_targets():
+    """rpy_evaluate against the oracle on the union of sources and (force-free) targets,
+    with targets on top of sources and within 2a of them."""
+    rng = np.random.default_rng(41)
+    src = synth.uniform_cube(6000, seed=42, a=0.003)
+    tgt = rng.random((1500, 3))
+    tgt[:5] = src.pos[:5]                              # on a source
+    tgt[5:10] = src.pos[5:10] + 0.001                  # within 2a of a source
+    import torch
+    U = torch.empty((len(tgt), 3), dtype=torch.float64, device="cuda")
+    rp.rpy_evaluate(cuda_tensor(src.pos), cuda_tensor(src.f), cuda_tensor(tgt), src.a, src.s, 6, U)
+    pos = np.concatenate([src.pos, tgt])
+    f = np.concatenate([src.f, np.zeros_like(tgt)])
+    ref = oracle.rpy_direct(pos, f, src.a, src.s, targets=np.arange(src.n, src.n + len(tgt)))
+    u = U.cpu().numpy()
+    assert oracle.rel_l2(u, ref) <= 1e-6
+    assert np.max(np.abs(u[:10] - ref[:10])) <= 1e-6 * np.max(np.abs(ref))
