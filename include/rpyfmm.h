@@ -170,6 +170,16 @@ int rpy_forest_matvec(rpy_tree t, const double *f_dev, const double *kT_over_eta
                       void *stream);
 
 /*
+ * Matvecs of several separately built trees, issued back to back on one stream
+ * (each replays its own captured graph): tree k reads f_dev[k] and writes
+ * u_dev[k] with kT_over_eta[k].  All arguments are checked before the first
+ * launch.  For many small systems a forest (rpy_forest_build) is faster: it
+ * runs every system in the same launches.  Asynchronous on `stream`.
+ */
+int rpy_matvec_batched(rpy_tree const *trees, int ntrees, const double *const *f_dev, const double *kT_over_eta,
+                       double *const *u_dev, void *stream);
+
+/*
  * Diagnostic split of rpy_matvec: parts = RPY_PART_NEAR (direct pairs of
  * adjacent leaves, self term included), RPY_PART_FAR (everything else, via
  * the FMM), or both.  u_dev receives the sum of the selected parts.

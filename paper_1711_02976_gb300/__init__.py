@@ -24,7 +24,7 @@ __all__ = [
     "rpy_tree_sync", "rpy_tree_footprint", "rpy_tree_free", "rpy_strerror", "rpy_last_cuda_error",
     "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times", "rpy_launch_count",
     "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt",
-    "rpy_bd_step", "rpy_evaluate", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
+    "rpy_bd_step", "rpy_evaluate", "rpy_matvec_batched", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
     "RPY_PART_ALL", "EXPORTED_SYMBOLS",
 ]
 
@@ -46,6 +46,7 @@ EXPORTED_SYMBOLS = [
     "rpy_launch_count", "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_server_create", "rpy_server_add_system",
     "rpy_server_submit", "rpy_server_wait", "rpy_server_cancel", "rpy_server_drain", "rpy_server_stats_get",
     "rpy_server_destroy", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt", "rpy_bd_step", "rpy_evaluate",
+    "rpy_matvec_batched",
 ]
 STAGES = ["gather", "p2p", "p2m", "m2m", "m2x", "x2x", "x2l", "p2l", "l2l", "eval", "combine"]
 
@@ -159,6 +160,7 @@ def load(build_if_missing: bool = True):
                              ctypes.POINTER(AutotuneResult), vp],
             "rpy_lanczos_sqrt": [vp, vp, vp, i, d, vp, ctypes.POINTER(i), ctypes.POINTER(d), vp],
             "rpy_evaluate": [vp, vp, i64, vp, i64, d, d, ctypes.POINTER(BuildParams), vp, vp],
+            "rpy_matvec_batched": [vp, i, vp, vp, vp, vp],
             "rpy_bd_step": [vp, vp, vp, vp, vp, vp, d, i, d, vp, ctypes.POINTER(i), vp],
             "rpy_server_create": [ctypes.POINTER(ServerParams), ctypes.POINTER(vp)],
             "rpy_server_add_system": [vp, vp, i64, d, ctypes.POINTER(BuildParams), ctypes.POINTER(i)],
@@ -318,6 +320,16 @@ def rpy_evaluate(src_pos, src_f, tgt_pos, a, kT_over_eta, digits, u_tgt, precisi
     _check(load().rpy_evaluate(_dev_f64(src_pos, "src_pos"), _dev_f64(src_f, "src_f"), ns, _dev_f64(tgt_pos, "tgt_pos"),
                                nt, float(a), float(kT_over_eta), ctypes.byref(prm), _dev_f64(u_tgt, "u_tgt"),
                                _stream(stream)), "rpy_evaluate")
+
+
+def rpy_matvec_batched(trees, fs, kT_over_eta, us, stream=None):
+    """Matvecs of several trees on one stream (device tensors f_k, u_k)."""
+    k = len(trees)
+    th = (ctypes.c_void_p * k)(*[t.handle if isinstance(t, Tree) else t for t in trees])
+    fp = (ctypes.c_void_p * k)(*[_dev_f64(f, "f") for f in fs])
+    up = (ctypes.c_void_p * k)(*[_dev_f64(u, "u") for u in us])
+    sv = np.ascontiguousarray(np.broadcast_to(np.asarray(kT_over_eta, dtype=np.float64), (k,)))
+    _check(load().rpy_matvec_batched(th, k, fp, sv.ctypes.data, up, _stream(stream)), "rpy_matvec_batched")
 
 
 def rpy_lanczos_sqrt(tree, z, kT_over_eta, y, m_max=60, tol=1e-8, stream=None):

@@ -434,6 +434,10 @@ int run_matvec(Tree &t, const double *f_dev, const double *s_host, double *u_dev
 
 int run_laplace_far(Tree &t, const double *q_dev, double *out_dev, cudaStream_t st) {
     if (!t.built) return RPY_ERR_STATE;
+    if (!std::isfinite(t.sys_s_h[0])) {   // per-system constants (their geometric part) for a tree never applied
+        std::vector<double> one(t.nsys, 1.0);
+        RPY_TRY(upload_s(t, one.data(), st));
+    }
     if (!t.lap_q) {
         RPY_TRY(dev_alloc(t, (void **)&t.lap_q, sizeof(double) * 4 * t.n));
     }
@@ -595,6 +599,15 @@ int rpy_matvec_parts(rpy_tree h, const double *f_dev, double s, double *u_dev, i
 
 int rpy_matvec(rpy_tree h, const double *f_dev, double s, double *u_dev, void *stream) {
     return rpy_matvec_parts(h, f_dev, s, u_dev, RPY_PART_ALL, stream);
+}
+
+int rpy_matvec_batched(rpy_tree const *trees, int ntrees, const double *const *f_dev, const double *kT_over_eta,
+                       double *const *u_dev, void *stream) {
+    if (!trees || ntrees < 0 || (ntrees > 0 && (!f_dev || !kT_over_eta || !u_dev))) return RPY_ERR_INVALID;
+    for (int k = 0; k < ntrees; ++k)
+        if (!valid(trees[k]) || !f_dev[k] || !u_dev[k] || !std::isfinite(kT_over_eta[k])) return RPY_ERR_INVALID;
+    for (int k = 0; k < ntrees; ++k) RPY_TRY(rpy_matvec(trees[k], f_dev[k], kT_over_eta[k], u_dev[k], stream));
+    return RPY_OK;
 }
 
 int rpy_matvec_oneshot(const double *pos_dev, int64_t n, double a, const double *f_dev, double s, int digits,

@@ -211,7 +211,8 @@ __host__ __device__ inline int tab_floats(int p) {   // recurrences + ladders, r
 
 // ---------------------------------------------------------------- P2M / P2L
 
-constexpr int kChunkB = 16;
+// Beads per chunk of P2M / P2L: one round of harmonics, (warps x points per warp).
+__host__ __device__ inline int p2x_chunk(int p, int threads) { return (threads / 32) * (32 / harm_lanes(p)); }
 
 // MODE 0: P2M over the leaf's own beads (multipole about its centre)
 // MODE 1: P2L over the beads of every box in X(b) (local about b's centre)
@@ -220,6 +221,7 @@ __global__ void k_p2x(int b0, int nb, DevTables<T> D, const int *beg, const int 
                       const double *side, const int *lvl, const int *leaf, const int *bsys, const int *xoff,
                       const int *xidx, const double *pos, const double *fs, const double *lapq, int64_t n,
                       SysConst sc, cpx<T> *out) {
+    const int kChunkB = p2x_chunk(D.p, blockDim.x);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = b0 + blockIdx.x;
     if (b >= b0 + nb) return;
@@ -237,7 +239,7 @@ __global__ void k_p2x(int b0, int nb, DevTables<T> D, const int *beg, const int 
     int sy = bsys[b];
     double c0x = sc.cube[4 * sy], c0y = sc.cube[4 * sy + 1], c0z = sc.cube[4 * sy + 2];
     double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
-    double ih = 1.0 / side[b];
+    const double ih = sc.pc[sy].icube * pow2i(lvl[b]);   // 1 / side[b], exactly
     int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     // harmonics: hG points per warp, lane -> (point hg, column pair hc)
     const int hL = harm_lanes(p), hG = 32 / hL, hg = (threadIdx.x & 31) / hL, hc = (threadIdx.x & 31) - hg * hL;
@@ -1058,10 +1060,10 @@ __global__ void k_lap_eval(const int *leaves, DevTables<T> D, const int *beg, co
 // ---------------------------------------------------------------- driver
 
 template <typename T>
-static size_t smem_p2x(int p) {
-    int nc = ncoef(p);
-    return sizeof(T) * ((rec_floats<T>(p) + 1) & ~1) + sizeof(cpx<T>) * (kChunkB * nc + kSets * nc) +
-           sizeof(T) * 4 * kChunkB + 64;
+static size_t smem_p2x(int p, int threads) {
+    const int nc = ncoef(p), chunk = p2x_chunk(p, threads);
+    return sizeof(T) * ((rec_floats<T>(p) + 1) & ~1) + sizeof(cpx<T>) * (chunk * nc + kSets * nc) +
+           sizeof(T) * 4 * chunk + 64;
 }
 template <typename T>
 static size_t smem_m2x(int p, int s) {
@@ -1121,7 +1123,7 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     int b2 = t.level_off[2];
     int n2 = nbx - b2;
     // upward pass
-    size_t sp = smem_p2x<T>(p);
+    size_t sp = smem_p2x<T>(p, 128);
     RPY_TRY(set_smem(k_p2x<T, 0>, sp));
     RPY_TRY(set_smem(k_p2x<T, 1>, sp));
     k_p2x<T, 0><<<n2, 128, sp, st>>>(b2, n2, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level, t.b_leaf,

@@ -373,3 +373,19 @@ def test_graph_replay_matches_plain_launches():
         rp.rpy_matvec(t_plain, 2.0 * F, sysm.s, U1)
         torch.cuda.synchronize()
         assert torch.equal(U0, U1), rep
+
+
+def test_matvec_batched_equals_separate_calls():
+    import torch
+    A = synth.uniform_cube(5000, seed=51, a=0.003)
+    B = synth.sphere_plus_cube(7000, seed=52, a=0.002)
+    ta = rp.rpy_tree_build(cuda_tensor(A.pos), A.n, A.a, 6)
+    tb = rp.rpy_tree_build(cuda_tensor(B.pos), B.n, B.a, 3)
+    Fa, Fb = cuda_tensor(A.f), cuda_tensor(B.f)
+    Ua, Ub = torch.empty_like(Fa), torch.empty_like(Fb)
+    rp.rpy_matvec_batched([ta, tb], [Fa, Fb], [A.s, 2.0 * B.s], [Ua, Ub])
+    Va, Vb = torch.empty_like(Fa), torch.empty_like(Fb)
+    rp.rpy_matvec(ta, Fa, A.s, Va)
+    rp.rpy_matvec(tb, Fb, 2.0 * B.s, Vb)
+    torch.cuda.synchronize()
+    assert torch.equal(Ua, Va) and torch.equal(Ub, Vb)
