@@ -190,6 +190,11 @@ static void pack_tables(const OpTables &h, std::vector<char> &blob, std::vector<
     putT(h.orot_bwd); // 25
     putT(h.zm2m);     // 26
     putT(h.zl2l);     // 27
+    putT(h.frot_fwd); // 28
+    putT(h.frot_bwd); // 29
+    putT(h.forot_fwd);// 30
+    putT(h.forot_bwd);// 31
+    putI(h.frot_off); // 32
 }
 
 template <typename T>
@@ -228,6 +233,12 @@ static DevTables<T> bind_tables(const OpTables &h, char *base, const std::vector
     d.orot_bwd = reinterpret_cast<const T *>(base + o[25]);
     d.zm2m = reinterpret_cast<const T *>(base + o[26]);
     d.zl2l = reinterpret_cast<const T *>(base + o[27]);
+    d.frot_fwd = reinterpret_cast<const T *>(base + o[28]);
+    d.frot_bwd = reinterpret_cast<const T *>(base + o[29]);
+    d.forot_fwd = reinterpret_cast<const T *>(base + o[30]);
+    d.forot_bwd = reinterpret_cast<const T *>(base + o[31]);
+    d.frot_off = reinterpret_cast<const int *>(base + o[32]);
+    d.frot_len = h.frot_off.back();
     return d;
 }
 

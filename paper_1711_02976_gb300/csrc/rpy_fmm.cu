@@ -357,6 +357,35 @@ __global__ void k_l2l(int b0, int nb, DevTables<T> D, const int *par, const int 
 
 // ---------------------------------------------------------------- rotations
 // dst[s] = R src[s] per degree block (real 2-layout, block size 2(n+1)).
+// The factorized rotation of the four sets: tmp <- za (src) (one 2x2 rotation per
+// coefficient), then dst <- zc (Y tmp), Y acting on real and imaginary parts
+// separately.  src and dst may not alias tmp; the caller synchronises after.
+template <typename T>
+__device__ void rotate_sets_f(const T *rf, const int *foff, int p, const cpx<T> *src, cpx<T> *tmp, cpx<T> *dst) {
+    const int nc = ncoef(p);
+    for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
+        const int st = e / nc, i = e - st * nc, n = deg_of(i), m = i - tri(n, 0);
+        const T *za = rf + foff[n];
+        const T c = za[2 * m], sn = za[2 * m + 1];
+        const cpx<T> v = src[st * nc + i];
+        tmp[e] = mk(fma(c, v.x, -sn * v.y), fma(sn, v.x, c * v.y));
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
+        const int st = e / nc, i = e - st * nc, n = deg_of(i), m = i - tri(n, 0), q = n + 1;
+        const T *o = rf + foff[n];
+        const T *yre = o + 4 * q + m * q, *yim = o + 4 * q + q * q + m * q;
+        const cpx<T> *in = tmp + st * nc + tri(n, 0);
+        T re = 0, im = 0;
+        for (int k = 0; k < q; ++k) {
+            re = fma(yre[k], in[k].x, re);
+            im = fma(yim[k], in[k].y, im);
+        }
+        const T c = o[2 * q + 2 * m], sn = o[2 * q + 2 * m + 1];
+        dst[st * nc + i] = mk(fma(c, re, -sn * im), fma(sn, re, c * im));
+    }
+}
+
 template <typename T>
 __device__ void rotate_sets(const T *rot, const int *roff, int p, const cpx<T> *src, cpx<T> *dst) {
     const int nc = ncoef(p);
@@ -387,6 +416,7 @@ __global__ void k_m2m_rot(int b0, int nb, DevTables<T> D, const int *leaf, const
     cpx<T> *X = reinterpret_cast<cpx<T> *>(smem_raw);
     cpx<T> *Y = X + kSets * nc;
     cpx<T> *acc = Y + kSets * nc;
+    cpx<T> *Tm = acc + kSets * nc;   // rotation scratch
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) acc[i] = mk<T>(0, 0);
     for (int o = 0; o < 8; ++o) {
         int c = child[8 * b + o];
@@ -395,7 +425,7 @@ __global__ void k_m2m_rot(int b0, int nb, DevTables<T> D, const int *leaf, const
         const cpx<T> *src = M + size_t(c) * kSets * nc;
         for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) X[i] = src[i];
         __syncthreads();
-        rotate_sets(D.orot_fwd + size_t(o) * D.rot_len, D.rot_off, p, X, Y);
+        rotate_sets_f(D.forot_fwd + size_t(o) * D.frot_len, D.frot_off, p, X, Tm, Y);
         __syncthreads();
         for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
             int st = e / nc, i = e - st * nc;
@@ -406,7 +436,7 @@ __global__ void k_m2m_rot(int b0, int nb, DevTables<T> D, const int *leaf, const
             X[e] = a;
         }
         __syncthreads();
-        rotate_sets(D.orot_bwd + size_t(o) * D.rot_len, D.rot_off, p, X, Y);
+        rotate_sets_f(D.forot_bwd + size_t(o) * D.frot_len, D.frot_off, p, X, Tm, Y);
         __syncthreads();
         for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) acc[i] += Y[i];
     }
@@ -423,11 +453,12 @@ __global__ void k_l2l_rot(int b0, int nb, DevTables<T> D, const int *par, const 
     const int p = D.p, nc = ncoef(p), P1 = p + 1;
     cpx<T> *X = reinterpret_cast<cpx<T> *>(smem_raw);
     cpx<T> *Y = X + kSets * nc;
+    cpx<T> *Tm = Y + kSets * nc;   // rotation scratch
     int o = (cell[3 * b] & 1) | ((cell[3 * b + 1] & 1) << 1) | ((cell[3 * b + 2] & 1) << 2);
     const cpx<T> *src = L + size_t(P) * kSets * nc;
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) X[i] = src[i];
     __syncthreads();
-    rotate_sets(D.orot_fwd + size_t(o) * D.rot_len, D.rot_off, p, X, Y);
+    rotate_sets_f(D.forot_fwd + size_t(o) * D.frot_len, D.frot_off, p, X, Tm, Y);
     __syncthreads();
     for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
         int st = e / nc, i = e - st * nc;
@@ -438,7 +469,7 @@ __global__ void k_l2l_rot(int b0, int nb, DevTables<T> D, const int *par, const 
         X[e] = a;
     }
     __syncthreads();
-    rotate_sets(D.orot_bwd + size_t(o) * D.rot_len, D.rot_off, p, X, Y);
+    rotate_sets_f(D.forot_bwd + size_t(o) * D.frot_len, D.frot_off, p, X, Tm, Y);
     __syncthreads();
     cpx<T> *dst = L + size_t(b) * kSets * nc;
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) dst[i] += Y[i];
@@ -454,6 +485,7 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
     cpx<T> *Mf = Mw + kSets * nc;
     cpx<T> *AE = Mf + kSets * nc;       // [s][P1][4 sets]
     cpx<T> *AO = AE + kSets * s * P1;
+    cpx<T> *Tm = AO + kSets * s * P1;   // rotation scratch
     const cpx<T> *src = M + size_t(b) * kSets * nc;
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Mw[i] = src[i];
     __syncthreads();
@@ -462,7 +494,7 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
     for (int f = 0; f < 3; ++f) {
         const cpx<T> *Mu = Mw;
         if (f > 0) {
-            rotate_sets(D.rot_fwd + size_t(f - 1) * D.rot_len, D.rot_off, p, Mw, Mf);
+            rotate_sets_f(D.frot_fwd + size_t(f - 1) * D.frot_len, D.frot_off, p, Mw, Tm, Mf);
             __syncthreads();
             Mu = Mf;
         }
@@ -639,6 +671,7 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
     cpx<T> *Lf = Bm + s * P1;                             // [4][nc] frame accumulation
     cpx<T> *Lw = Lf + kSets * nc;                         // [4][nc] world accumulation
     cpx<T> *Lr = Lw + kSets * nc;                         // [4][nc] rotated
+    cpx<T> *Tm = Lr + kSets * nc;                         // [4][nc] rotation scratch
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] = mk<T>(0, 0);
     for (int f = 0; f < 3; ++f) {
         for (int st = 0; st < kSets; ++st) {
@@ -696,7 +729,7 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
         if (f == 0) {
             for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lf[i];
         } else {
-            rotate_sets(D.rot_bwd + size_t(f - 1) * D.rot_len, D.rot_off, p, Lf, Lr);
+            rotate_sets_f(D.frot_bwd + size_t(f - 1) * D.frot_len, D.frot_off, p, Lf, Tm, Lr);
             __syncthreads();
             for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lr[i];
         }
@@ -724,6 +757,7 @@ __global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi,
     cpx<float> *Lf = Bd + kSets * s * P1;                         // [4][nc]
     cpx<float> *Lw = Lf + kSets * nc;
     cpx<float> *Lr = Lw + kSets * nc;
+    cpx<float> *Tm = Lr + kSets * nc;                             // rotation scratch
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] = mk<float>(0, 0);
     for (int f = 0; f < 3; ++f) {
         __syncthreads();
@@ -795,7 +829,7 @@ __global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi,
         if (f == 0) {
             for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lf[i];
         } else {
-            rotate_sets(D.rot_bwd + size_t(f - 1) * D.rot_len, D.rot_off, p, Lf, Lr);
+            rotate_sets_f(D.frot_bwd + size_t(f - 1) * D.frot_len, D.frot_off, p, Lf, Tm, Lr);
             __syncthreads();
             for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lr[i];
         }
@@ -807,7 +841,7 @@ __global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi,
 
 static size_t smem_x2l4(int p, int s, int S) {
     const int nc = ncoef(p);
-    return sizeof(float4) * 4 * size_t(S) + sizeof(cpx<float>) * (2 * kSets * s * (p + 1) + 3 * kSets * nc);
+    return sizeof(float4) * 4 * size_t(S) + sizeof(cpx<float>) * (2 * kSets * s * (p + 1) + 4 * kSets * nc);
 }
 
 // ---------------------------------------------------------------- far-field evaluation
@@ -1068,12 +1102,12 @@ static size_t smem_p2x(int p, int threads) {
 template <typename T>
 static size_t smem_m2x(int p, int s) {
     int nc = ncoef(p);
-    return sizeof(cpx<T>) * (2 * kSets * nc + 2 * kSets * s * (p + 1));
+    return sizeof(cpx<T>) * (3 * kSets * nc + 2 * kSets * s * (p + 1));
 }
 template <typename T>
 static size_t smem_x2l(int p, int s, int S) {
     int nc = ncoef(p);
-    return sizeof(cpx<T>) * (2 * S + 2 * s * (p + 1) + 3 * kSets * nc);
+    return sizeof(cpx<T>) * (2 * S + 2 * s * (p + 1) + 4 * kSets * nc);
 }
 template <typename T>
 static size_t smem_far(int p) {
@@ -1133,7 +1167,7 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     prof_mark(t, RPY_STAGE_M2M, st);
     // FP64: rotation-based (fewer FP64 operations); FP32: dense operator
     const bool rot = sizeof(T) == 8;
-    size_t smr3 = sizeof(cpx<T>) * 3 * kSets * nc, smr2 = sizeof(cpx<T>) * 2 * kSets * nc;
+    size_t smr3 = sizeof(cpx<T>) * 4 * kSets * nc, smr2 = sizeof(cpx<T>) * 3 * kSets * nc;
     int Dd = 2 * nc, thr = ((Dd + 31) / 32) * 32;
     size_t smd = sizeof(T) * kSets * Dd;
     RPY_TRY(set_smem(k_m2m_rot<T>, smr3));

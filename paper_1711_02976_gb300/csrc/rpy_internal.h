@@ -124,6 +124,10 @@ struct OpTables {
     // rotation-based M2M / L2L: per child octant, rotations world -> frame whose z axis is
     // the shift direction and back, and the m-diagonal z-shift coefficients
     std::vector<double> orot_fwd, orot_bwd;   // [8][rot_len]
+    // the same rotations factored through z-y-z Euler angles (layout in rpy_tables.cu)
+    std::vector<double> frot_fwd, frot_bwd;   // [2 frames][frot_len]
+    std::vector<double> forot_fwd, forot_bwd; // [8 octants][frot_len]
+    std::vector<int> frot_off;                // [p+2] offset of degree n
     std::vector<double> zm2m, zl2l;           // [ncoef(p)][p+1]: output (n,m), input degree k
 };
 constexpr int kGroupMax = 32;
@@ -139,6 +143,9 @@ struct DevTables {
     const T *rec_a, *rec_b, *rec_c, *rec_cm;
     const T *lad;
     const T *orot_fwd, *orot_bwd, *zm2m, *zl2l;
+    const T *frot_fwd, *frot_bwd, *forot_fwd, *forot_bwd;
+    const int *frot_off;
+    int frot_len;
     const cpx<T> *roots;
     const T *m2x_c, *x2l_c;
     const int *e_k, *k_start;
