@@ -75,7 +75,10 @@ typedef struct {
     int order_p;      /* expansion order p; 0 = default for the setting */
     int max_level;    /* deepest level allowed, 1..21; 0 = 21 */
     int flags;        /* bit 0 (RPY_FLAG_NO_GRAPH): never replay the matvec as a CUDA graph;
-                         other bits must be 0 */
+                         bit 1 (RPY_FLAG_FRAME_PASSES): run M2X / X2X / X2L one plane-wave
+                         frame (two of the six directions) at a time, with a third of the
+                         plane-wave memory; chosen automatically when the buffers of all
+                         six directions would exceed 64 GB; other bits must be 0 */
     int direct_w;     /* W-list boxes with at most this many beads are summed directly
                          instead of by multipole evaluation: 0 = automatic
                          (about 1.8 (p+3)(p+4)/2), -1 = never */
@@ -89,7 +92,7 @@ typedef struct {
                          plane waves per direction) */
 } rpy_build_params;
 
-enum { RPY_FLAG_NO_GRAPH = 1 };
+enum { RPY_FLAG_NO_GRAPH = 1, RPY_FLAG_FRAME_PASSES = 2 };
 
 /* Statistics of a built tree (host struct filled by rpy_tree_stats). */
 typedef struct {

@@ -324,8 +324,9 @@ int tree_alloc_workspace(Tree &t, cudaStream_t) {
     size_t nb = size_t(t.nbox);
     RPY_TRY(dev_alloc(t, &t.M, es * nb * kSets * h.nc));
     RPY_TRY(dev_alloc(t, &t.L, es * nb * kSets * h.nc));
-    RPY_TRY(dev_alloc(t, &t.Xo, es * nb * kDirs * kSets * h.S));
-    RPY_TRY(dev_alloc(t, &t.Xi, es * nb * kDirs * kSets * h.S));
+    t.x_frames = (t.params.flags & RPY_FLAG_FRAME_PASSES) ? 1 : plane_wave_frames(double(nb), double(es), h.S);
+    RPY_TRY(dev_alloc(t, &t.Xo, es * nb * 2 * t.x_frames * kSets * h.S));
+    RPY_TRY(dev_alloc(t, &t.Xi, es * nb * 2 * t.x_frames * kSets * h.S));
     RPY_TRY(dev_alloc(t, &t.EVg, es * size_t(t.nleaf) * 18 * h.nc));
     RPY_TRY(dev_alloc(t, (void **)&t.fs, sizeof(double) * 3 * t.n));
     if (t.params.precision == RPY_FP32) {
@@ -478,7 +479,7 @@ static int check_params(const rpy_build_params &p) {
     if (p.digits != 3 && p.digits != 6) return RPY_ERR_DIGITS;
     if (p.precision != RPY_FP64 && p.precision != RPY_FP32) return RPY_ERR_INVALID;
     if (p.leaf_cap < 0 || p.order_p < 0 || p.max_level < 0 || p.max_level > kMaxLevel ||
-        (p.flags & ~RPY_FLAG_NO_GRAPH) != 0)
+        (p.flags & ~(RPY_FLAG_NO_GRAPH | RPY_FLAG_FRAME_PASSES)) != 0)
         return RPY_ERR_INVALID;
     if (p.order_p != 0 && (p.order_p < 2 || p.order_p > kMaxP)) return RPY_ERR_INVALID;
     if (p.direct_w < -1 || p.direct_x < -1) return RPY_ERR_INVALID;
@@ -813,7 +814,8 @@ int rpy_tree_footprint(int64_t n, int digits, int precision, int leaf_cap, int64
     double es = precision == RPY_FP32 ? 8.0 : 16.0;
     // boxes: leaves ~ 2n/cap on clustered data, plus internal boxes (< leaves/7 * 8)
     double nbox = 4.0 * double(n) / double(leaf_cap) + 64.0;
-    double per_box = es * (2.0 * kSets * ncoef(p) + 2.0 * kDirs * kSets * q.half() + 18.0 * ncoef(p)) +
+    const int xf = plane_wave_frames(nbox, es, q.half());
+    double per_box = es * (2.0 * kSets * ncoef(p) + 2.0 * 2 * xf * kSets * q.half() + 18.0 * ncoef(p)) +
                      4.0 * (8 + 27 + 3 + 12) + 32.0;
     double per_bead = 3 * 8 /*pos*/ + 8 /*key*/ + 4 + 4 + 9 * 8 /*fs, unear, ufar*/ + 27 * 4 /*U list share*/ +
                       (precision == RPY_FP32 ? 9 * 4 /*p32, f32*/ : 0);

@@ -477,7 +477,7 @@ __global__ void k_l2l_rot(int b0, int nb, DevTables<T> D, const int *par, const 
 
 // ---------------------------------------------------------------- M2X
 template <typename T>
-__global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *Xo) {
+__global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *Xo, int f0, int nf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = b0 + blockIdx.x;
     const int p = D.p, nc = ncoef(p), s = D.s, S = D.S, P1 = p + 1;
@@ -489,9 +489,9 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
     const cpx<T> *src = M + size_t(b) * kSets * nc;
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Mw[i] = src[i];
     __syncthreads();
-    size_t base = size_t(b) * kDirs * kSets * S;
+    size_t base = size_t(b) * (2 * nf) * kSets * S;   // frames f0 .. f0 + nf - 1 of this pass
     const int hP = harm_lanes(p);
-    for (int f = 0; f < 3; ++f) {
+    for (int f = f0; f < f0 + nf; ++f) {
         const cpx<T> *Mu = Mw;
         if (f > 0) {
             rotate_sets_f(D.frot_fwd + size_t(f - 1) * D.frot_len, D.frot_off, p, Mw, Tm, Mf);
@@ -571,8 +571,9 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
             const T wm = D.e_wm[j];
 #pragma unroll
             for (int st = 0; st < kSets; ++st) {
-                Xo[base + size_t(2 * f) * kSets * S + st * S + j] = mk(wm * (er[st] + orr[st]), wm * (ei[st] + oi[st]));
-                Xo[base + size_t(2 * f + 1) * kSets * S + st * S + j] =
+                Xo[base + size_t(2 * (f - f0)) * kSets * S + st * S + j] =
+                    mk(wm * (er[st] + orr[st]), wm * (ei[st] + oi[st]));
+                Xo[base + size_t(2 * (f - f0) + 1) * kSets * S + st * S + j] =
                     mk(wm * (er[st] - orr[st]), wm * (ei[st] - oi[st]));
             }
         }
@@ -583,11 +584,11 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
 // ---------------------------------------------------------------- X2X merge-and-shift
 template <typename T>
 __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const int *child, const int *leaf,
-                      const cpx<T> *Xo, cpx<T> *Xi) {
+                      const cpx<T> *Xo, cpx<T> *Xi, int f0, int nf) {
     __shared__ int src[216];
     __shared__ int vsrc[216], vsh[216], vpre[217];   // the present sources, compacted in slot order
     int P = parents[blockIdx.x];
-    int d = blockIdx.y;
+    const int dl = blockIdx.y, d = 2 * f0 + dl;   // direction, and its slot in this pass's buffers
     const int S = D.S;
     for (int sl = threadIdx.x; sl < 216; sl += blockDim.x) {
         int q = sl >> 3, o = sl & 7;
@@ -626,8 +627,8 @@ __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const
     int ch[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) ch[t] = child[8 * P + t];
-    const size_t dstride = size_t(kDirs) * kSets * S;
-    const cpx<T> *Xd = Xo + size_t(d) * kSets * S;
+    const size_t dstride = size_t(2 * nf) * kSets * S;
+    const cpx<T> *Xd = Xo + size_t(dl) * kSets * S;
     for (int e = threadIdx.x; e < kSets * S; e += blockDim.x) {
         int j = e % S;
         cpx<T> acc[8];
@@ -653,14 +654,14 @@ __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const
         for (int t = 0; t < 8; ++t) {
             if (ch[t] < 0) continue;
             cpx<T> sh = D.shift[size_t(D.child_shift[d * 8 + t]) * S + j];
-            Xi[(size_t(ch[t]) * kDirs + d) * kSets * S + e] = acc[t] * sh;
+            Xi[(size_t(ch[t]) * (2 * nf) + dl) * kSets * S + e] = acc[t] * sh;
         }
     }
 }
 
 // ---------------------------------------------------------------- X2L
 template <typename T>
-__global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *L) {
+__global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *L, int f0, int nf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = b0 + blockIdx.x;
     const int p = D.p, nc = ncoef(p), s = D.s, S = D.S, P1 = p + 1;
@@ -673,11 +674,11 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
     cpx<T> *Lr = Lw + kSets * nc;                         // [4][nc] rotated
     cpx<T> *Tm = Lr + kSets * nc;                         // [4][nc] rotation scratch
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] = mk<T>(0, 0);
-    for (int f = 0; f < 3; ++f) {
+    for (int f = f0; f < f0 + nf; ++f) {
         for (int st = 0; st < kSets; ++st) {
             __syncthreads();
-            const cpx<T> *sp = Xi + ((size_t(b) * kDirs + 2 * f) * kSets + st) * S;
-            const cpx<T> *sm = Xi + ((size_t(b) * kDirs + 2 * f + 1) * kSets + st) * S;
+            const cpx<T> *sp = Xi + ((size_t(b) * (2 * nf) + 2 * (f - f0)) * kSets + st) * S;
+            const cpx<T> *sm = Xi + ((size_t(b) * (2 * nf) + 2 * (f - f0) + 1) * kSets + st) * S;
             for (int i = threadIdx.x; i < S; i += blockDim.x) {
                 Ip[i] = sp[i];
                 Im[i] = sm[i];
@@ -744,7 +745,7 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
 // parts in another), so that the real DFT, which takes the real parts for even m
 // and the imaginary parts for odd m, reads four sets with one 16-byte load per
 // wave and direction; one root lookup then serves sixteen FMAs.
-__global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi, cpx<float> *L) {
+__global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi, cpx<float> *L, int f0, int nf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int b = b0 + blockIdx.x;
     const int p = D.p, nc = ncoef(p), s = D.s, S = D.S, P1 = p + 1;
@@ -759,10 +760,10 @@ __global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi,
     cpx<float> *Lr = Lw + kSets * nc;
     cpx<float> *Tm = Lr + kSets * nc;                             // rotation scratch
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] = mk<float>(0, 0);
-    for (int f = 0; f < 3; ++f) {
+    for (int f = f0; f < f0 + nf; ++f) {
         __syncthreads();
-        const cpx<float> *sp = Xi + (size_t(b) * kDirs + 2 * f) * kSets * S;
-        const cpx<float> *sm = Xi + (size_t(b) * kDirs + 2 * f + 1) * kSets * S;
+        const cpx<float> *sp = Xi + (size_t(b) * (2 * nf) + 2 * (f - f0)) * kSets * S;
+        const cpx<float> *sm = Xi + (size_t(b) * (2 * nf) + 2 * (f - f0) + 1) * kSets * S;
         for (int j = threadIdx.x; j < S; j += blockDim.x) {
             const cpx<float> p0 = sp[j], p1 = sp[S + j], p2 = sp[2 * S + j], p3 = sp[3 * S + j];
             const cpx<float> m0 = sm[j], m1 = sm[S + j], m2 = sm[2 * S + j], m3 = sm[3 * S + j];
@@ -1183,32 +1184,34 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
         }
     }
     RPY_CHECK(cudaGetLastError());
-    // plane-wave M2L
-    prof_mark(t, RPY_STAGE_M2X, st);
+    // plane-wave M2L: all three frames in one pass, or (large trees, where the
+    // plane-wave buffers of six directions would not fit) one frame per pass,
+    // each pass adding its frame's share into L.  With one frame per pass the
+    // stage times of frames 1 and 2 are counted under X2L.
+    const int nf = t.x_frames;
     size_t smx = smem_m2x<T>(p, D.s);
     RPY_TRY(set_smem(k_m2x<T>, smx));
-    k_m2x<T><<<n2, 256, smx, st>>>(b2, n2, D, M, Xo);
-    RPY_LAUNCHED(1);
-    RPY_CHECK(cudaGetLastError());
-    prof_mark(t, RPY_STAGE_X2X, st);
-    if (t.n_x2x_par > 0) {
-        dim3 g(t.n_x2x_par, kDirs);
-        k_x2x<T><<<g, 256, 0, st>>>(t.x2x_par, D, t.b_coll, t.b_child, t.b_leaf, Xo, Xi);
+    size_t sxl = sizeof(T) == 4 ? smem_x2l4(p, D.s, D.S) : smem_x2l<T>(p, D.s, D.S);
+    if constexpr (sizeof(T) == 4) RPY_TRY(set_smem(k_x2l4, sxl));
+    else RPY_TRY(set_smem(k_x2l<T>, sxl));
+    for (int f0 = 0; f0 < 3; f0 += nf) {
+        if (f0 == 0) prof_mark(t, RPY_STAGE_M2X, st);
+        k_m2x<T><<<n2, 256, smx, st>>>(b2, n2, D, M, Xo, f0, nf);
+        RPY_LAUNCHED(1);
+        RPY_CHECK(cudaGetLastError());
+        if (f0 == 0) prof_mark(t, RPY_STAGE_X2X, st);
+        if (t.n_x2x_par > 0) {
+            dim3 g(t.n_x2x_par, 2 * nf);
+            k_x2x<T><<<g, 256, 0, st>>>(t.x2x_par, D, t.b_coll, t.b_child, t.b_leaf, Xo, Xi, f0, nf);
+            RPY_LAUNCHED(1);
+            RPY_CHECK(cudaGetLastError());
+        }
+        if (f0 == 0) prof_mark(t, RPY_STAGE_X2L, st);
+        if constexpr (sizeof(T) == 4) k_x2l4<<<n2, 256, sxl, st>>>(b2, n2, D, Xi, L, f0, nf);
+        else k_x2l<T><<<n2, 256, sxl, st>>>(b2, n2, D, Xi, L, f0, nf);
         RPY_LAUNCHED(1);
         RPY_CHECK(cudaGetLastError());
     }
-    prof_mark(t, RPY_STAGE_X2L, st);
-    if constexpr (sizeof(T) == 4) {
-        size_t sxl = smem_x2l4(p, D.s, D.S);
-        RPY_TRY(set_smem(k_x2l4, sxl));
-        k_x2l4<<<n2, 256, sxl, st>>>(b2, n2, D, Xi, L);
-    } else {
-        size_t sxl = smem_x2l<T>(p, D.s, D.S);
-        RPY_TRY(set_smem(k_x2l<T>, sxl));
-        k_x2l<T><<<n2, 256, sxl, st>>>(b2, n2, D, Xi, L);
-    }
-    RPY_LAUNCHED(1);
-    RPY_CHECK(cudaGetLastError());
     // X list
     prof_mark(t, RPY_STAGE_P2L, st);
     k_p2x<T, 1><<<n2, 128, sp, st>>>(b2, n2, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level, t.b_leaf,

@@ -78,6 +78,13 @@ RPY_HD int ncoef(int p) { return (p + 1) * (p + 2) / 2; }
 
 constexpr int kSets = 4;          // Laplace charge sets L1..L4 (Sec. 2)
 constexpr int kDirs = 6;          // +z -z +x -x +y -y plane-wave directions
+// Plane-wave frames handled per M2X / X2X / X2L pass: all three while the
+// outgoing and incoming buffers of six directions take at most kXAllFramesBytes,
+// else one frame (two directions) per pass, which needs a third of the memory.
+constexpr double kXAllFramesBytes = 64e9;
+inline int plane_wave_frames(double nbox, double elem_bytes, int S) {
+    return 2.0 * nbox * kDirs * 4 * double(S) * elem_bytes <= kXAllFramesBytes ? 3 : 1;
+}
 constexpr int kMaxP = 29;         // largest supported expansion order (p + 2 < 32 warp lanes)
 constexpr int kMaxLevel = 21;
 constexpr int kItemTargets = 256;   // targets per near-field work item
@@ -216,6 +223,7 @@ struct Tree {
     int direct_w = 0, direct_x = 0;    // bead-count thresholds in use (0 = none)
     // expansions and matvec workspace
     void *M = nullptr, *L = nullptr, *Xo = nullptr, *Xi = nullptr;
+    int x_frames = 3;                 // plane-wave frames per pass (3 or 1)
     void *EVg = nullptr;              // [nleaf][18][ncoef(p)] derived local expansions of Eq. (2.8)
     double *fs = nullptr;             // sorted forces SoA [3][n]
     float *p32 = nullptr;             // FP32 form: sorted positions as hi + lo floats, [6][n] (x,y,z hi; x,y,z lo)

@@ -389,3 +389,29 @@ def test_matvec_batched_equals_separate_calls():
     rp.rpy_matvec(tb, Fb, 2.0 * B.s, Vb)
     torch.cuda.synchronize()
     assert torch.equal(Ua, Va) and torch.equal(Ub, Vb)
+
+
+@pytest.mark.parametrize("precision,digits", [(rp.RPY_FP64, 6), (rp.RPY_FP32, 3)])
+def test_one_frame_per_pass_matches_all_frames(precision, digits):
+    """RPY_FLAG_FRAME_PASSES (M2X / X2X / X2L one plane-wave frame at a time, the
+    layout of trees too large for the six-direction buffers) gives the result of
+    the single pass up to the order in which the three frames' local expansions
+    are added, and meets the digit setting against the oracle."""
+    import torch
+    sysm = synth.sphere_plus_cube(20000, 61, 2e-4)
+    P, F = cuda_tensor(sysm.pos), cuda_tensor(sysm.f)
+    U0, U1 = torch.empty_like(F), torch.empty_like(F)
+    t0 = rp.rpy_forest_build(P, [0, sysm.n], [sysm.a], digits, leaf_cap=30, precision=precision)
+    t1 = rp.rpy_forest_build(P, [0, sysm.n], [sysm.a], digits, leaf_cap=30, precision=precision,
+                             flags=rp.RPY_FLAG_FRAME_PASSES)
+    assert rp.rpy_tree_stats(t1)["device_bytes"] < rp.rpy_tree_stats(t0)["device_bytes"]
+    for rep in range(2):   # plain launches, then the captured graph
+        rp.rpy_matvec(t0, F, sysm.s, U0)
+        rp.rpy_matvec(t1, F, sysm.s, U1)
+        torch.cuda.synchronize()
+        u0, u1 = U0.cpu().numpy(), U1.cpu().numpy()
+        tol = 1e-13 if precision == rp.RPY_FP64 else 1e-6
+        assert np.max(np.abs(u1 - u0)) <= tol * np.max(np.abs(u0)), rep
+    tg = synth.sample_targets(sysm.n, 500)
+    ref = oracle.rpy_direct(sysm.pos, sysm.f, sysm.a, sysm.s, targets=tg)
+    assert oracle.rel_l2(u1[tg], ref) <= (1e-6 if digits == 6 else 1e-3)
