@@ -138,6 +138,32 @@ def test_near_part_matches_oracle_on_u_lists():
     assert np.abs(u - ref).max() < 1e-12 * np.abs(ref).max()
 
 
+def _close_pairs(n, a, seed):
+    """Uniform beads plus partners closer than 2a: 300 in (0, 2a), 20 within 1e-4 a,
+    10 coincident."""
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, 3)) * 0.9 + 0.05
+    k = 0
+    for cnt, lo, hi in ((300, 0.0, 2.0 * a), (20, 0.0, 1e-4 * a), (10, 0.0, 0.0)):
+        for _ in range(cnt):
+            d = rng.standard_normal(3)
+            pos[n - 1 - k] = pos[k] + (lo + (hi - lo) * rng.random()) * d / np.linalg.norm(d)
+            k += 1
+    return pos, rng.standard_normal((n, 3))
+
+
+@pytest.mark.parametrize("a", [0.002, 0.01])   # leaves ~60a and ~12a wide
+def test_fp32_near_part_matches_oracle_on_u_lists(a):
+    """FP32 near field (compensated FP32 sums, FP64 for pairs within 1e-3 a)
+    against the oracle on the U lists, with many overlapping, nearly coincident
+    and coincident pairs."""
+    pos, f = _close_pairs(6000, a, 71)
+    s = 6 * math.pi * a
+    u, t = matvec(pos, f, a, s, 3, leaf_cap=40, precision=rp.RPY_FP32, parts=rp.RPY_PART_NEAR)
+    ref = _near_oracle(t, pos, f, a, s)
+    assert np.abs(u - ref).max() < 2e-6 * np.abs(ref).max()
+
+
 # ---------------------------------------------------------------- far field operators
 
 @pytest.mark.parametrize("digits,tol", [(3, 1e-3), (6, 1e-6)])
