@@ -78,7 +78,11 @@ typedef struct {
                          bit 1 (RPY_FLAG_FRAME_PASSES): run M2X / X2X / X2L one plane-wave
                          frame (two of the six directions) at a time, with a third of the
                          plane-wave memory; chosen automatically when the buffers of all
-                         six directions would exceed 64 GB; other bits must be 0 */
+                         six directions would exceed 64 GB;
+                         bit 2 (RPY_FLAG_EVAL_PER_POTENTIAL): evaluate Eq. (2.8) at the beads
+                         per Laplace potential (approach 1 of Sec. 2: 12 expansions per
+                         bead) instead of one expansion per velocity component (approach 2,
+                         the default: 6 expansions per bead); other bits must be 0 */
     int direct_w;     /* W-list boxes with at most this many beads are summed directly
                          instead of by multipole evaluation: 0 = automatic
                          (about 1.8 (p+3)(p+4)/2), -1 = never */
@@ -92,7 +96,7 @@ typedef struct {
                          plane waves per direction) */
 } rpy_build_params;
 
-enum { RPY_FLAG_NO_GRAPH = 1, RPY_FLAG_FRAME_PASSES = 2 };
+enum { RPY_FLAG_NO_GRAPH = 1, RPY_FLAG_FRAME_PASSES = 2, RPY_FLAG_EVAL_PER_POTENTIAL = 4 };
 
 /* Statistics of a built tree (host struct filled by rpy_tree_stats). */
 typedef struct {

@@ -25,12 +25,13 @@ __all__ = [
     "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times", "rpy_launch_count",
     "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt",
     "rpy_bd_step", "rpy_evaluate", "rpy_matvec_batched", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
-    "RPY_PART_ALL", "RPY_FLAG_NO_GRAPH", "RPY_FLAG_FRAME_PASSES", "EXPORTED_SYMBOLS",
+    "RPY_PART_ALL", "RPY_FLAG_NO_GRAPH", "RPY_FLAG_FRAME_PASSES",
+    "RPY_FLAG_EVAL_PER_POTENTIAL", "EXPORTED_SYMBOLS",
 ]
 
 RPY_FP64, RPY_FP32 = 0, 1
 RPY_PART_NEAR, RPY_PART_FAR, RPY_PART_ALL = 1, 2, 3
-RPY_FLAG_NO_GRAPH, RPY_FLAG_FRAME_PASSES = 1, 2
+RPY_FLAG_NO_GRAPH, RPY_FLAG_FRAME_PASSES, RPY_FLAG_EVAL_PER_POTENTIAL = 1, 2, 4
 FIELDS = {
     "perm": (1, np.int32), "keys": (2, np.uint64), "box_level": (3, np.int32), "box_range": (4, np.int32),
     "box_parent": (5, np.int32), "box_center": (6, np.float64), "box_leaf": (7, np.int32),

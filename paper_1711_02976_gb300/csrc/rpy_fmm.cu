@@ -167,6 +167,33 @@ __device__ void d_multipole(const cpx<T> *src, int ps, cpx<T> *dx, cpx<T> *dy, c
     }
 }
 
+// Coefficient i of one component c (0 = x, 1 = y, 2 = z) of the gradient of a
+// local (d_loc_one) or multipole (d_mul_one) expansion of degree ps: the
+// single-output forms of d_local and d_multipole.
+template <typename T>
+__device__ __forceinline__ cpx<T> d_loc_one(const cpx<T> *src, int ps, int c, int i, const Lad<T> &G) {
+    const int k = deg_of(i), m = i - tri(k, 0);
+    if (k > ps - 1) return mk<T>(0, 0);
+    if (c == 2) return G.lz[i] * src[tri(k + 1, m)];
+    const cpx<T> Pv = m >= 1 ? G.lp[i] * src[tri(k + 1, m - 1)] : (-G.lq[i]) * conj(src[tri(k + 1, 1)]);
+    const cpx<T> Qv = (-G.lq[i]) * src[tri(k + 1, m + 1)];
+    return c == 0 ? mk(T(0.5) * (Pv.x + Qv.x), T(0.5) * (Pv.y + Qv.y))
+                  : mk(T(0.5) * (Pv.y - Qv.y), T(-0.5) * (Pv.x - Qv.x));
+}
+
+template <typename T>
+__device__ __forceinline__ cpx<T> d_mul_one(const cpx<T> *src, int ps, int c, int i, const Lad<T> &G) {
+    const int k = deg_of(i), m = i - tri(k, 0);
+    if (k < 1 || k > ps + 1) return mk<T>(0, 0);
+    if (c == 2) return m <= k - 1 ? (-G.mz[i]) * src[tri(k - 1, m)] : mk<T>(0, 0);
+    cpx<T> Pv = mk<T>(0, 0), Qv = mk<T>(0, 0);
+    if (m >= 1) Pv = G.mp[i] * src[tri(k - 1, m - 1)];
+    else if (k >= 2) Pv = (-G.mp[i]) * conj(src[tri(k - 1, 1)]);
+    if (m + 1 <= k - 1) Qv = (-G.mq[i]) * src[tri(k - 1, m + 1)];
+    return c == 0 ? mk(T(0.5) * (Pv.x + Qv.x), T(0.5) * (Pv.y + Qv.y))
+                  : mk(T(0.5) * (Pv.y - Qv.y), T(-0.5) * (Pv.x - Qv.x));
+}
+
 // ---------------------------------------------------------------- table access
 template <typename T>
 struct Rec {
@@ -847,7 +874,8 @@ static size_t smem_x2l4(int p, int s, int S) {
 
 // ---------------------------------------------------------------- far-field evaluation
 constexpr int kNE = 18;   // evaluation expansions of Eq. (2.8) per box
-constexpr int kNF = 12;   // of them evaluated per bead after the fold in k_eval_prep
+constexpr int kNF = 12;   // evaluated per bead after the fold of k_eval_prep (per-potential form)
+constexpr int kNF2 = 6;   // evaluated per bead in the one-expansion-per-component form
 
 // Build the 18 evaluation expansions of Eq. (2.8) from 4 source expansions.
 // IRREG = multipole source (degrees grow by one per derivative), else local.
@@ -947,7 +975,7 @@ __global__ void k_far_eval(const int *leaves, DevTables<T> D, const int *beg, co
 // written to global memory for the bead-parallel evaluation.
 template <typename T>
 __global__ void k_eval_prep(const int *leaves, DevTables<T> D, const double *ctr, const int *lvl, const int *bsys,
-                            SysConst sc, const cpx<T> *L, cpx<T> *EVg) {
+                            SysConst sc, const cpx<T> *L, cpx<T> *EVg, int per_component) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int li = blockIdx.x;
     int b = leaves[li];
@@ -976,9 +1004,44 @@ __global__ void k_eval_prep(const int *leaves, DevTables<T> D, const double *ctr
         v.y = fma(c4, g4.y, fma(-cc, gc.y, v.y));
         EV[d * nc + c] = v;
     }
+    int nf = kNF;
+    if (per_component) {
+        // Approach 2 of Sec. 2: one expansion per velocity component.  With
+        // G_kd = dL_k/dx_d (fields 3 + 3k + d, degree <= p - 1) and x the bead
+        // offset in box units, sum_k x_k G_kd = A_d + |x|^2 B_d with A_d, B_d
+        // harmonic: for each degree-n part h of G_kd, with g = h / (2n + 1),
+        //   x_k h = [x_k h - |x|^2 d_k g] + |x|^2 d_k g,
+        // where the bracket is -|x|^(2n+3) d_k(g / |x|^(2n+1)) (Kelvin transform:
+        // the same coefficients read as a multipole expansion), so
+        //   A_d = -sum_k [d_k of g as a multipole, read as a local expansion],
+        //   B_d =  sum_k [d_k of g as a local expansion].
+        // Fields become H_d = F_d - A_d (0..2, degree <= p) and B_d (3..5).
+        __syncthreads();
+        for (int i = threadIdx.x; i < 9 * nc; i += blockDim.x) {
+            const int c = i % nc;
+            const T w = T(1) / T(2 * deg_of(c) + 1);
+            cpx<T> v = EV[3 * nc + i];
+            EV[3 * nc + i] = mk(w * v.x, w * v.y);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * nc; i += blockDim.x) {
+            const int d = i / nc, c = i - d * nc;
+            cpx<T> a = mk<T>(0, 0), bb = mk<T>(0, 0);
+            for (int k = 0; k < 3; ++k) {
+                const cpx<T> *g = EV + (3 + 3 * k + d) * nc;
+                a += d_mul_one(g, p - 1, k, c, G);
+                bb += d_loc_one(g, p - 1, k, c, G);
+            }
+            EV[d * nc + c] += a;
+            EV[(12 + d) * nc + c] = bb;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * nc; i += blockDim.x) EV[3 * nc + i] = EV[12 * nc + i];
+        nf = kNF2;
+    }
     __syncthreads();
-    // fields 0..11 carry the factor 2 of the m > 0 terms of Re(sum E h)
-    for (int i = threadIdx.x; i < kNF * nc; i += blockDim.x) {
+    // the evaluated fields carry the factor 2 of the m > 0 terms of Re(sum E h)
+    for (int i = threadIdx.x; i < nf * nc; i += blockDim.x) {
         int c = i % nc, n = deg_of(c);
         if (c != tri(n, 0)) {
             cpx<T> v = EV[i];
@@ -987,8 +1050,10 @@ __global__ void k_eval_prep(const int *leaves, DevTables<T> D, const double *ctr
     }
 }
 
-// One thread per bead: L2P of the leaf's derived expansions and Eq. (2.8).
-template <typename T>
+// One thread per bead: L2P of the leaf's derived expansions and Eq. (2.8),
+// per potential (NF = 12: folded values and nine gradients) or per velocity
+// component (NF = 6: u_d = H_d - |x|^2 B_d).
+template <typename T, int NF>
 __global__ void k_eval_apply(int64_t n, const int *bead_leaf, const int *leaves, DevTables<T> D, const double *ctr,
                              const double *side, const int *lvl, const int *bsys, const double *pos, SysConst sc,
                              const cpx<T> *EVg, double *ufar) {
@@ -1004,16 +1069,22 @@ __global__ void k_eval_apply(int64_t n, const int *bead_leaf, const int *leaves,
         const double ih = sc.pc[sy].icube * pow2i(lvl[b]);   // 1 / side[b], exactly
         double xi[3] = {(pos[i] - ctr[3 * b]) * ih, (pos[n + i] - ctr[3 * b + 1]) * ih,
                         (pos[2 * n + i] - ctr[3 * b + 2]) * ih};
-        // fields 0..2: the folded value terms; 3..11: gradients dL_k / dx_d at 3 + 3k + d
-        T acc[kNF];
+        T acc[NF];
 #pragma unroll
-        for (int q = 0; q < kNF; ++q) acc[q] = 0;
-        eval_fields<T, kNF, false, true>(T(xi[0]), T(xi[1]), T(xi[2]), p, EVg + size_t(li) * kNE * nc, nc, D.rec_a, D.rec_b,
-                                   D.rec_c, acc);
-        for (int d = 0; d < 3; ++d) {
-            double v = double(acc[d]);
-            for (int k = 0; k < 3; ++k) v -= xi[k] * double(acc[3 + 3 * k + d]);
-            u[d] = C1 * ih * v;
+        for (int q = 0; q < NF; ++q) acc[q] = 0;
+        eval_fields<T, NF, false, true>(T(xi[0]), T(xi[1]), T(xi[2]), p, EVg + size_t(li) * kNE * nc, nc, D.rec_a,
+                                        D.rec_b, D.rec_c, acc);
+        if constexpr (NF == kNF2) {
+            // fields 0..2: H_d; 3..5: B_d
+            const double r2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+            for (int d = 0; d < 3; ++d) u[d] = C1 * ih * (double(acc[d]) - r2 * double(acc[3 + d]));
+        } else {
+            // fields 0..2: the folded value terms; 3..11: gradients dL_k / dx_d at 3 + 3k + d
+            for (int d = 0; d < 3; ++d) {
+                double v = double(acc[d]);
+                for (int k = 0; k < 3; ++k) v -= xi[k] * double(acc[3 + 3 * k + d]);
+                u[d] = C1 * ih * v;
+            }
         }
     }
     for (int d = 0; d < 3; ++d) ufar[3 * i + d] = u[d];
@@ -1234,10 +1305,17 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
         cpx<T> *EVg = static_cast<cpx<T> *>(t.EVg);
         size_t sp2 = sizeof(T) * (((6 * ncoef(p + 2) + 1) & ~1)) + sizeof(cpx<T>) * 2 * kSets * nc + 64;
         RPY_TRY(set_smem(k_eval_prep<T>, sp2));
-        k_eval_prep<T><<<t.nleaf, 128, sp2, st>>>(t.leaves, D, t.b_center, t.b_level, t.b_sys, sc, L, EVg);
+        // one expansion per velocity component unless the per-potential form is asked for
+        const int per_comp = (t.params.flags & RPY_FLAG_EVAL_PER_POTENTIAL) ? 0 : 1;
+        k_eval_prep<T><<<t.nleaf, 128, sp2, st>>>(t.leaves, D, t.b_center, t.b_level, t.b_sys, sc, L, EVg, per_comp);
         RPY_LAUNCHED(1);
-        k_eval_apply<T><<<int((t.n + 127) / 128), 128, 0, st>>>(t.n, t.bead_leaf, t.leaves, D, t.b_center, t.b_side,
-                                                               t.b_level, t.b_sys, t.pos, sc, EVg, ufar);
+        const int ga = int((t.n + 127) / 128);
+        if (per_comp)
+            k_eval_apply<T, kNF2><<<ga, 128, 0, st>>>(t.n, t.bead_leaf, t.leaves, D, t.b_center, t.b_side, t.b_level,
+                                                      t.b_sys, t.pos, sc, EVg, ufar);
+        else
+            k_eval_apply<T, kNF><<<ga, 128, 0, st>>>(t.n, t.bead_leaf, t.leaves, D, t.b_center, t.b_side, t.b_level,
+                                                     t.b_sys, t.pos, sc, EVg, ufar);
         RPY_LAUNCHED(1);
         size_t sf = smem_far<T>(p);
         RPY_TRY(set_smem(k_far_eval<T>, sf));

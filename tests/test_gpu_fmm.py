@@ -441,3 +441,23 @@ def test_one_frame_per_pass_matches_all_frames(precision, digits):
     tg = synth.sample_targets(sysm.n, 500)
     ref = oracle.rpy_direct(sysm.pos, sysm.f, sysm.a, sysm.s, targets=tg)
     assert oracle.rel_l2(u1[tg], ref) <= (1e-6 if digits == 6 else 1e-3)
+
+
+@pytest.mark.parametrize("precision,digits", [(rp.RPY_FP64, 6), (rp.RPY_FP32, 3)])
+def test_per_component_evaluation_equals_per_potential(precision, digits):
+    """Approach 2 of Sec. 2 (the default: six expansions per bead, u_d = H_d -
+    |x|^2 B_d) against approach 1 (RPY_FLAG_EVAL_PER_POTENTIAL: folded values and
+    nine gradients per bead): the same far field up to rounding."""
+    import torch
+    sysm = synth.sphere_plus_cube(20000, 63, 2e-4)
+    P, F = cuda_tensor(sysm.pos), cuda_tensor(sysm.f)
+    U2, U1 = torch.empty_like(F), torch.empty_like(F)
+    t2 = rp.rpy_forest_build(P, [0, sysm.n], [sysm.a], digits, leaf_cap=30, precision=precision)
+    t1 = rp.rpy_forest_build(P, [0, sysm.n], [sysm.a], digits, leaf_cap=30, precision=precision,
+                             flags=rp.RPY_FLAG_EVAL_PER_POTENTIAL)
+    rp.rpy_matvec_parts(t2, F, sysm.s, U2, rp.RPY_PART_FAR)
+    rp.rpy_matvec_parts(t1, F, sysm.s, U1, rp.RPY_PART_FAR)
+    torch.cuda.synchronize()
+    u2, u1 = U2.cpu().numpy(), U1.cpu().numpy()
+    tol = 1e-11 if precision == rp.RPY_FP64 else 2e-5
+    assert np.max(np.abs(u2 - u1)) <= tol * np.max(np.abs(u1))

@@ -326,3 +326,37 @@ def test_rotation_m2m_l2l_equal_dense_operators(p):
         np.testing.assert_allclose(ym, from_real(dense_m[o].T @ as_real(x)), rtol=0, atol=1e-12 * np.abs(x).max())
         yl = _rot_apply(b, offs, p, 0, zshift(zl, _rot_apply(f, offs, p, 0, x), False))
         np.testing.assert_allclose(yl, from_real(dense_l[o].T @ as_real(x)), rtol=0, atol=1e-12 * np.abs(x).max())
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 6])
+def test_coordinate_times_harmonic_splits_by_kelvin_transform(n):
+    """The identity behind the one-expansion-per-component evaluation (approach 2
+    of Sec. 2): for a harmonic polynomial h of degree n and g = h / (2n + 1),
+        x_k h(x) = H(x) + |x|^2 d_k g(x),   H(x) = -|x|^(2n+3) d_k[g^K](x),
+    where g^K is g with its coefficients read in the irregular basis (the Kelvin
+    transform g / |x|^(2n+1)), and H is harmonic.  Checked by central differences
+    with the test-side harmonics."""
+    rng = np.random.default_rng(100 + n)
+    c = np.zeros(ncoef(n), dtype=complex)
+    for m in range(n + 1):
+        c[tri(n, m)] = rng.standard_normal() + (1j * rng.standard_normal() if m else 0)
+    g = c / (2 * n + 1)
+    h = lambda x: eval_real(c, regular(x, n))
+    gr = lambda x: eval_real(g, regular(x, n))
+    gk = lambda x: eval_real(g, irregular(x, n))
+    x = rng.uniform(-0.6, 0.6, (20, 3))
+    e = 1e-5
+    I = np.eye(3)
+    r = np.linalg.norm(x, axis=1)
+    for k in range(3):
+        dg = (gr(x + e * I[k]) - gr(x - e * I[k])) / (2 * e)
+        dgk = (gk(x + e * I[k]) - gk(x - e * I[k])) / (2 * e)
+        H = -r ** (2 * n + 3) * dgk
+        lhs = x[:, k] * h(x)
+        assert np.max(np.abs(lhs - (H + r ** 2 * dg))) <= 1e-8 * max(1.0, np.max(np.abs(lhs)))
+        # H is harmonic: its Laplacian by second differences vanishes
+        Hf = lambda y: -np.linalg.norm(y, axis=1) ** (2 * n + 3) * (
+            gk(y + e * I[k]) - gk(y - e * I[k])) / (2 * e)
+        E = 1e-3
+        lap = sum(Hf(x + E * I[a]) - 2 * Hf(x) + Hf(x - E * I[a]) for a in range(3)) / E ** 2
+        assert np.max(np.abs(lap)) <= 1e-3 * max(1.0, np.max(np.abs(H)))
