@@ -39,10 +39,18 @@ import scipy.optimize as so
 from scipy.special import j0, j1
 
 RHO_MAX = 4.0 * math.sqrt(2.0)
-ZS = np.linspace(1.0, 4.0, 31)
-RS = np.linspace(0.0, RHO_MAX, 41)
-Z, RH = [a.ravel() for a in np.meshgrid(ZS, RS, indexing="ij")]
-F = 1.0 / np.sqrt(Z ** 2 + RH ** 2)
+
+
+def set_grid(nz, nrho):
+    """Fit grid over the V-list region: nz values of z in [1, 4], nrho of rho."""
+    global ZS, RS, Z, RH, F
+    ZS = np.linspace(1.0, 4.0, nz)
+    RS = np.linspace(0.0, RHO_MAX, nrho)
+    Z, RH = [a.ravel() for a in np.meshgrid(ZS, RS, indexing="ij")]
+    F = 1.0 / np.sqrt(Z ** 2 + RH ** 2)
+
+
+set_grid(31, 41)
 
 
 def _unpack(p, s):
@@ -145,18 +153,23 @@ def total_error(lam, w, ms):
 
 
 SETTINGS = [
-    # name, digits, target max relative error of the lambda rule, s range
+    # name, digits, target max relative error of the lambda rule, s range[, fine phase]
     ("D3", 3, 3.0e-4, (8, 12)),
     ("D6", 6, 3.0e-7, (14, 22)),
     # intermediate rules the autotuner may pair with a 6-digit accuracy target
     ("D4", 4, 3.0e-5, (10, 16)),
     ("D5", 5, 3.0e-6, (12, 19)),
+    # the 9-digit setting: its largest nodes oscillate across rho faster than the
+    # default grid resolves, so the rule met on that grid is refined (and s raised
+    # by continuation) on a finer grid until it meets the second target there
+    ("D9", 9, 7.0e-10, (22, 31), (3.5e-10, 36, (41, 161))),
 ]
 
 
 def main(out_path):
     blocks = []
-    for name, digits, target, (s_lo, s_hi) in SETTINGS:
+    for name, digits, target, (s_lo, s_hi), *fine in SETTINGS:
+        set_grid(31, 41)
         chosen = None
         for s, err, lam, w in lambda_rules(s_lo, s_hi):
             print(f"{name}: s={s} lambda-rule max rel err {err:.3e}", flush=True)
@@ -166,6 +179,20 @@ def main(out_path):
         if chosen is None:
             raise SystemExit(f"{name}: no rule met {target}")
         s, err, lam, w = chosen
+        if fine:
+            ftarget, fs_hi, (nz, nrho) = fine[0]
+            set_grid(nz, nrho)
+            while True:
+                err, pp = _refine(np.concatenate([np.log(lam), np.log(w)]), s)
+                lam, w = _unpack(pp, s)
+                o = np.argsort(lam)
+                lam, w = lam[o], w[o]
+                print(f"{name}: s={s} fine-grid lambda-rule max rel err {err:.3e}", flush=True)
+                if err <= ftarget:
+                    break
+                if s >= fs_hi:
+                    raise SystemExit(f"{name}: no rule met {ftarget} on the fine grid")
+                lam, w, s = np.append(lam, lam[-1] + (lam[-1] - lam[-2])), np.append(w, 0.5 * w[-1]), s + 1
         ms = choose_m(lam, w, err / s)
         tot = total_error(lam, w, ms)
         print(f"{name}: s={s} M={ms} S={sum(ms)} total max rel err {tot:.3e}", flush=True)

@@ -21,6 +21,7 @@
 //                     gradients and Hessians of Theorems 1-2 formed as
 //                     derivative expansions per box, combined by Eq. (2.8):
 //                     u = C1 [L1 L2 L3] - C1 sum_k x_k grad L_k + C1 grad L4 - C2 grad L_C.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <map>
@@ -1212,6 +1213,15 @@ static int set_smem(K kernel, size_t bytes) {
     return RPY_OK;
 }
 
+// Threads of an X2X block: each handles elements e, e + blockDim, ... of the
+// 4 S merged plane waves; the fewest warps that keep the number of rounds of
+// 256 threads, so that the last round is not left nearly empty.
+static int even_threads(int items) {
+    const int rounds = (items + 255) / 256;
+    return std::max(64, ((items + rounds - 1) / rounds + 31) / 32 * 32);
+}
+static int x2x_threads(int S) { return even_threads(kSets * S); }
+
 template <typename T>
 int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *lapq, double *ufar, double *lapout,
               const SysConst &sc, cudaStream_t st) {
@@ -1267,18 +1277,22 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     else RPY_TRY(set_smem(k_x2l<T>, sxl));
     for (int f0 = 0; f0 < 3; f0 += nf) {
         if (f0 == 0) prof_mark(t, RPY_STAGE_M2X, st);
-        k_m2x<T><<<n2, 256, smx, st>>>(b2, n2, D, M, Xo, f0, nf);
+        k_m2x<T><<<n2, even_threads(D.S), smx, st>>>(b2, n2, D, M, Xo, f0, nf);
         RPY_LAUNCHED(1);
         RPY_CHECK(cudaGetLastError());
         if (f0 == 0) prof_mark(t, RPY_STAGE_X2X, st);
         if (t.n_x2x_par > 0) {
             dim3 g(t.n_x2x_par, 2 * nf);
-            k_x2x<T><<<g, 256, 0, st>>>(t.x2x_par, D, t.b_coll, t.b_child, t.b_leaf, Xo, Xi, f0, nf);
+            k_x2x<T><<<g, x2x_threads(D.S), 0, st>>>(t.x2x_par, D, t.b_coll, t.b_child, t.b_leaf, Xo, Xi, f0, nf);
             RPY_LAUNCHED(1);
             RPY_CHECK(cudaGetLastError());
         }
         if (f0 == 0) prof_mark(t, RPY_STAGE_X2L, st);
-        if constexpr (sizeof(T) == 4) k_x2l4<<<n2, 256, sxl, st>>>(b2, n2, D, Xi, L, f0, nf);
+        // FP32 X2L: blocks sized to the (node, m) items of its widest phase at low
+        // order; at high order the shared memory already limits the blocks per SM
+        // and 256 threads hide latency better
+        const int tx = D.s * (p + 1) <= 256 ? even_threads(D.s * (p + 1)) : 256;
+        if constexpr (sizeof(T) == 4) k_x2l4<<<n2, tx, sxl, st>>>(b2, n2, D, Xi, L, f0, nf);
         else k_x2l<T><<<n2, 256, sxl, st>>>(b2, n2, D, Xi, L, f0, nf);
         RPY_LAUNCHED(1);
         RPY_CHECK(cudaGetLastError());
