@@ -615,6 +615,7 @@ __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const
                       const cpx<T> *Xo, cpx<T> *Xi, int f0, int nf) {
     __shared__ int src[216];
     __shared__ int vsrc[216], vsh[216], vpre[217];   // the present sources, compacted in slot order
+    __shared__ int vend[216];   // child mask of its group at the last present source of a group, else 0
     int P = parents[blockIdx.x];
     const int dl = blockIdx.y, d = 2 * f0 + dl;   // direction, and its slot in this pass's buffers
     const int S = D.S;
@@ -652,6 +653,14 @@ __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const
         if (lane == 0) vpre[nsl] = carry;
     }
     __syncthreads();
+    const int nz = vpre[goff[ng]];
+    for (int z = threadIdx.x; z < nz; z += blockDim.x) vend[z] = 0;
+    __syncthreads();
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        const int z1 = vpre[goff[g + 1]];
+        if (z1 > vpre[goff[g]]) vend[z1 - 1] = gmask[g];
+    }
+    __syncthreads();
     int ch[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) ch[t] = child[8 * P + t];
@@ -662,21 +671,22 @@ __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const
         cpx<T> acc[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) acc[t] = mk<T>(0, 0);
-        for (int g = 0; g < ng; ++g) {
-            const int z0 = vpre[goff[g]], z1 = vpre[goff[g + 1]];
-            if (z0 == z1) continue;   // block-uniform: no source box of this group exists
-            cpx<T> ga = mk<T>(0, 0);
+        // one pass over all present sources (group boundaries marked by vend), so
+        // that the unrolled loads run ahead across groups
+        cpx<T> ga = mk<T>(0, 0);
 #pragma unroll 4
-            for (int z = z0; z < z1; ++z) {
-                const cpx<T> x = Xd[size_t(vsrc[z]) * dstride + e];
-                const cpx<T> sh = D.shift[size_t(vsh[z]) * S + j];
-                ga.x = fma(-x.y, sh.y, fma(x.x, sh.x, ga.x));
-                ga.y = fma(x.y, sh.x, fma(x.x, sh.y, ga.y));
-            }
-            int mask = gmask[g];
+        for (int z = 0; z < nz; ++z) {
+            const cpx<T> x = Xd[size_t(vsrc[z]) * dstride + e];
+            const cpx<T> sh = D.shift[size_t(vsh[z]) * S + j];
+            ga.x = fma(-x.y, sh.y, fma(x.x, sh.x, ga.x));
+            ga.y = fma(x.y, sh.x, fma(x.x, sh.y, ga.y));
+            const int mask = vend[z];   // block-uniform
+            if (mask) {
 #pragma unroll
-            for (int t = 0; t < 8; ++t)
-                if ((mask >> t) & 1) acc[t] += ga;
+                for (int t = 0; t < 8; ++t)
+                    if ((mask >> t) & 1) acc[t] += ga;
+                ga = mk<T>(0, 0);
+            }
         }
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
