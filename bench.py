@@ -40,6 +40,9 @@ CONFIGS = {
     "sphere1m_6digit_fp64": dict(gen="config2", digits=6, precision=0, leaf_cap=0,
                                  desc="1,000,000 beads: sphere surface r=0.5 + 10% uniform cube, a=1e-4, "
                                       "6-digit, FP64"),
+    "sphere1m_9digit_fp64": dict(gen="config2", digits=9, precision=0, leaf_cap=0,
+                                 desc="1,000,000 beads: sphere surface r=0.5 + 10% uniform cube, a=1e-4, "
+                                      "9-digit, FP64 (the paper's third accuracy setting)"),
     "cube4096_3digit_fp64": dict(gen="config1", digits=3, precision=0, leaf_cap=40,
                                  desc="4,096 beads uniform cube, a=0.004, 3-digit, FP64, leaf cap 40"),
     "cube15m_3digit_fp32": dict(gen="config3", digits=3, precision=1, leaf_cap=0,

@@ -49,7 +49,7 @@ typedef struct rpy_tree_s *rpy_tree;
 typedef enum {
     RPY_OK = 0,
     RPY_ERR_INVALID = -1,    /* bad argument (n < 1, a <= 0, NULL pointer, ...) */
-    RPY_ERR_DIGITS = -2,     /* digits not in {3, 6} */
+    RPY_ERR_DIGITS = -2,     /* digits not in {3, 6, 9}, or 9 with RPY_FP32 */
     RPY_ERR_OOM = -3,        /* device allocation failed */
     RPY_ERR_CUDA = -4,       /* a CUDA call failed; see rpy_last_cuda_error() */
     RPY_ERR_TIMEOUT = -5,    /* a bounded device wait gave up */
@@ -68,7 +68,7 @@ typedef enum {
 
 /* Build parameters.  Zero fields take the defaults listed. */
 typedef struct {
-    int digits;       /* 3 or 6: relative-L2 accuracy setting (required) */
+    int digits;       /* 3, 6 or 9: relative-L2 accuracy setting (required) */
     int precision;    /* rpy_precision; default RPY_FP64 */
     int leaf_cap;     /* refinement limit: a box splits while it holds more beads
                          (Sec. 4.2 "threshold"); 0 = default for the setting */
@@ -90,10 +90,10 @@ typedef struct {
                          summed directly instead of by source-to-local expansion:
                          0 = automatic (about 0.6 (p+1)(p+2)/2), -1 = never */
     int quad;         /* plane-wave quadrature rule of M2X / X2X / X2L: 0 = the rule of
-                         `digits`; 3, 4, 5 or 6 = the rule built for that many digits
+                         `digits`; 3, 4, 5, 6 or 9 = the rule built for that many digits
                          (max relative error of the 1/r representation 3.6e-4, 3.6e-5,
-                         2.8e-6, 4.0e-7 over the V-list region; 134, 218, 323, 464 stored
-                         plane waves per direction) */
+                         2.8e-6, 4.0e-7, 2.3e-10 over the V-list region; 134, 218, 323,
+                         464, 1168 stored plane waves per direction) */
 } rpy_build_params;
 
 enum { RPY_FLAG_NO_GRAPH = 1, RPY_FLAG_FRAME_PASSES = 2, RPY_FLAG_EVAL_PER_POTENTIAL = 4 };
@@ -127,8 +127,8 @@ typedef struct {
  *   pos_dev   device, n x 3 FP64, caller order
  *   n         number of beads, >= 1
  *   a         bead radius, > 0 and finite
- *   digits    3 or 6
- *   leaf_cap  refinement limit, 0 = default (40 for 3 digits, 100 for 6)
+ *   digits    3, 6 or 9
+ *   leaf_cap  refinement limit, 0 = default (40 for 3 digits, 100 for 6, 120 for 9)
  *   precision rpy_precision
  *   out       receives the handle (NULL on failure)
  * Boxes split while they hold more than leaf_cap beads and their children
@@ -295,7 +295,7 @@ const char *rpy_last_cuda_error(void);
 
 /*
  * Host-only inspection of the operator tables for expansion order p and a
- * plane-wave quadrature rule `digits` (3..6, as rpy_build_params.quad; no
+ * plane-wave quadrature rule `digits` (3..6 or 9, as rpy_build_params.quad; no
  * device needed): which = 1 M2M, 2 L2L (transposed real
  * matrices per child octant), 3 / 4 frame rotations world->frame / frame->world,
  * 5 M2X coefficients, 6 X2L coefficients, 7 stored plane waves (k, cos, sin,
@@ -376,7 +376,8 @@ typedef struct {
     int n_samples;       /* sampled targets of the error estimate; 0 = 256 */
     int timed_reps;      /* timed matvecs per candidate (median kept); 0 = 3 */
     double margin;       /* accept settings whose sampled relative L2 error is at most
-                            margin x bound (bound 1e-3 at 3 digits, 1e-6 at 6); 0 = 0.3 */
+                            margin x bound (bound 1e-3 at 3 digits, 1e-6 at 6, 1e-9 at 9);
+                            0 = 0.3 */
     uint64_t seed;       /* sample seed; 0 = a fixed default */
 } rpy_autotune_params;
 
@@ -405,7 +406,7 @@ typedef struct {
  *   1. draws n_samples distinct targets and sums RPY there directly
  *      (rpy_direct_sampled, FP64);
  *   2. order p: for each plane-wave quadrature rule (6 digits: the rules of
- *      6, 5 and 4 digits; 3 digits: its own), the smallest p whose sampled
+ *      6, 5 and 4 digits; 3 and 9 digits: their own), the smallest p whose sampled
  *      relative L2 error (default leaf capacity) is at most margin x bound,
  *      then the (rule, p) pair with the fastest timed matvec; if no pair
  *      meets the goal, the one of least error;

@@ -476,14 +476,15 @@ int run_laplace_far(Tree &t, const double *q_dev, double *out_dev, cudaStream_t 
 }
 
 static int check_params(const rpy_build_params &p) {
-    if (p.digits != 3 && p.digits != 6) return RPY_ERR_DIGITS;
+    if (p.digits != 3 && p.digits != 6 && p.digits != 9) return RPY_ERR_DIGITS;
     if (p.precision != RPY_FP64 && p.precision != RPY_FP32) return RPY_ERR_INVALID;
+    if (p.digits == 9 && p.precision != RPY_FP64) return RPY_ERR_DIGITS;   // beyond FP32 arithmetic
     if (p.leaf_cap < 0 || p.order_p < 0 || p.max_level < 0 || p.max_level > kMaxLevel ||
         (p.flags & ~(RPY_FLAG_NO_GRAPH | RPY_FLAG_FRAME_PASSES | RPY_FLAG_EVAL_PER_POTENTIAL)) != 0)
         return RPY_ERR_INVALID;
     if (p.order_p != 0 && (p.order_p < 2 || p.order_p > kMaxP)) return RPY_ERR_INVALID;
     if (p.direct_w < -1 || p.direct_x < -1) return RPY_ERR_INVALID;
-    if (p.quad != 0 && (p.quad < 3 || p.quad > 6)) return RPY_ERR_INVALID;
+    if (p.quad != 0 && (p.quad < 3 || p.quad > 6) && p.quad != 9) return RPY_ERR_INVALID;
     return RPY_OK;
 }
 
@@ -499,7 +500,7 @@ const char *rpy_strerror(int status) {
     switch (status) {
         case RPY_OK: return "success";
         case RPY_ERR_INVALID: return "invalid argument";
-        case RPY_ERR_DIGITS: return "digits must be 3 or 6";
+        case RPY_ERR_DIGITS: return "digits must be 3, 6 or 9";
         case RPY_ERR_OOM: return "device memory allocation failed";
         case RPY_ERR_CUDA: return "CUDA error";
         case RPY_ERR_TIMEOUT: return "device wait timed out";
@@ -807,7 +808,7 @@ int rpy_tree_stats(rpy_tree h, rpy_stats *o) {
 }
 
 int rpy_tree_footprint(int64_t n, int digits, int precision, int leaf_cap, int64_t *bytes) {
-    if (!bytes || n < 1 || (digits != 3 && digits != 6)) return RPY_ERR_INVALID;
+    if (!bytes || n < 1 || (digits != 3 && digits != 6 && digits != 9)) return RPY_ERR_INVALID;
     if (leaf_cap <= 0) leaf_cap = default_leaf_cap(digits);
     const ExpQuad &q = exp_quadrature(digits);
     int p = default_order(digits);
@@ -913,7 +914,7 @@ int rpy_alu_peak(int precision, double *flops_per_s, void *stream) {
 }
 
 int rpy_debug_table(int p, int digits, int which, double *dst, int64_t capacity, int64_t *count) {
-    if (p < 2 || p > kMaxP || digits < 3 || digits > 6) return RPY_ERR_INVALID;
+    if (p < 2 || p > kMaxP || ((digits < 3 || digits > 6) && digits != 9)) return RPY_ERR_INVALID;
     OpTables *h = nullptr;
     RPY_TRY(host_tables(p, digits, &h));
     std::vector<double> tmp;

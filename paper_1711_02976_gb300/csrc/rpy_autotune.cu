@@ -212,8 +212,9 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
     int s = check_forest_args(pos_dev, sys_offsets, nsys, a_host, f_dev, kT_over_eta_host);
     if (s != RPY_OK) return s;
     if (!out) return RPY_ERR_INVALID;
-    if (digits != 3 && digits != 6) return RPY_ERR_DIGITS;
+    if (digits != 3 && digits != 6 && digits != 9) return RPY_ERR_DIGITS;
     if (precision != RPY_FP64 && precision != RPY_FP32) return RPY_ERR_INVALID;
+    if (digits == 9 && precision != RPY_FP64) return RPY_ERR_DIGITS;
     rpy_autotune_params P{};
     if (params) P = *params;
     if (P.n_samples < 0 || P.timed_reps < 0 || !(P.margin >= 0.0) || P.margin > 1.0) return RPY_ERR_INVALID;
@@ -257,7 +258,7 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
         }
     } evg{e0, e1};
 
-    const double bound = digits == 3 ? 1e-3 : 1e-6;
+    const double bound = digits == 3 ? 1e-3 : (digits == 6 ? 1e-6 : 1e-9);
     const double goal = margin * bound;
     std::vector<Trial> trials;
 
@@ -327,7 +328,7 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
     base.precision = precision;
     const int pdef = default_order(digits);
     int capdef = default_leaf_cap(digits);   // doubled below while its tree does not fit on the device
-    const int plo = digits == 3 ? 4 : 8, phi = digits == 3 ? 12 : 24;
+    const int plo = digits == 3 ? 4 : (digits == 6 ? 8 : 16), phi = digits == 3 ? 12 : (digits == 6 ? 24 : 27);
     base.leaf_cap = capdef;
 
     auto err_at = [&](int q, int p) -> Trial {
@@ -384,7 +385,7 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
     // quadrature rule and order: for a 6-digit target the cheaper rules are
     // tried as well; among the (rule, order) pairs that meet the goal the
     // fastest timed matvec wins
-    std::vector<int> rules = digits == 3 ? std::vector<int>{3} : std::vector<int>{6, 5, 4};
+    std::vector<int> rules = digits == 3 ? std::vector<int>{3} : (digits == 6 ? std::vector<int>{6, 5, 4} : std::vector<int>{9});
     int best_q = rules[0], best_p = pdef;
     double best_ms = INFINITY, best_err = INFINITY;
     bool best_ok = false;

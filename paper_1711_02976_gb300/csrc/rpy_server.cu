@@ -272,7 +272,7 @@ int rpy_server_create(const rpy_server_params *params, rpy_server *out) {
 int rpy_server_add_system(rpy_server h, const double *pos_host, int64_t n, double a, const rpy_build_params *params,
                           int *system_id) {
     if (!h || !pos_host || n < 1 || !(a > 0) || !params || !system_id) return RPY_ERR_INVALID;
-    if (params->digits != 3 && params->digits != 6) return RPY_ERR_DIGITS;
+    if (params->digits != 3 && params->digits != 6 && params->digits != 9) return RPY_ERR_DIGITS;
     Server &S = h->S;
     SrvSystem sy;
     sy.n = n;

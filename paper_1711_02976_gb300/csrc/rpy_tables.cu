@@ -465,7 +465,7 @@ static void build_groups(OpTables &t) {
 
 // Plane-wave rule `qd` (3..6): the rule generated for that many digits.
 const ExpQuad &exp_quadrature(int qd) {
-    static ExpQuad q[4];
+    static ExpQuad q[5];
     static std::once_flag once;
     std::call_once(once, [] {
         auto set = [](ExpQuad &e, int s, const double *l, const double *w, const int *m) {
@@ -478,16 +478,17 @@ const ExpQuad &exp_quadrature(int qd) {
         set(q[1], RPY_EXPQ_D4_S, rpy_expq_d4_lambda, rpy_expq_d4_weight, rpy_expq_d4_m);
         set(q[2], RPY_EXPQ_D5_S, rpy_expq_d5_lambda, rpy_expq_d5_weight, rpy_expq_d5_m);
         set(q[3], RPY_EXPQ_D6_S, rpy_expq_d6_lambda, rpy_expq_d6_weight, rpy_expq_d6_m);
+        set(q[4], RPY_EXPQ_D9_S, rpy_expq_d9_lambda, rpy_expq_d9_weight, rpy_expq_d9_m);
     });
-    return q[qd <= 3 ? 0 : (qd >= 6 ? 3 : qd - 3)];
+    return q[qd <= 3 ? 0 : (qd >= 9 ? 4 : (qd >= 6 ? 3 : qd - 3))];
 }
 
 // Expansion order per setting, chosen from measured rel-L2 against the oracle
 // (1M-bead sphere and 4M-bead cube): p = 8 gives 5.5e-5 / 1.9e-5 at 3 digits,
 // p = 18 gives 4.0e-8 at 6 digits, each with a far-field-only error at least
 // 3x below the setting.
-int default_order(int digits) { return digits <= 3 ? 8 : 18; }
-int default_leaf_cap(int digits) { return digits <= 3 ? 40 : 100; }
+int default_order(int digits) { return digits <= 3 ? 8 : (digits <= 6 ? 18 : 26); }
+int default_leaf_cap(int digits) { return digits <= 3 ? 40 : (digits <= 6 ? 100 : 120); }
 
 int build_tables(int p, int qd, OpTables &t) {
     if (p < 2 || p > kMaxP) return RPY_ERR_INVALID;

@@ -60,6 +60,10 @@ def test_strerror_and_validation_without_device():
                             ctypes.byref(res), None) == -2
     assert lib.rpy_autotune(fake, off.ctypes.data, 1, av.ctypes.data, fake, sv.ctypes.data, 3, 0, None,
                             None, None) == -1
+    # 9 digits: FP64 only
+    assert lib.rpy_autotune(fake, off.ctypes.data, 1, av.ctypes.data, fake, sv.ctypes.data, 9, 1, None,
+                            ctypes.byref(res), None) == -2
+    assert rp.rpy_tree_footprint(10 ** 6, 9) > rp.rpy_tree_footprint(10 ** 6, 6)
     it, ch = ctypes.c_int(), ctypes.c_double()
     assert lib.rpy_lanczos_sqrt(None, fake, sv.ctypes.data, 10, 1e-8, fake, ctypes.byref(it), ctypes.byref(ch),
                                 None) == -1
@@ -156,7 +160,7 @@ def _quad(digits, p):
     return s, lam, w, M
 
 
-@pytest.mark.parametrize("digits,tol", [(3, 3.0e-4), (4, 4.0e-5), (5, 3.5e-6), (6, 4.5e-7)])
+@pytest.mark.parametrize("digits,tol", [(3, 3.0e-4), (4, 4.0e-5), (5, 3.5e-6), (6, 4.5e-7), (9, 2.5e-10)])
 def test_lambda_quadrature(digits, tol):
     from scipy.special import j0
     s, lam, w, M = _quad(digits, 10)
@@ -230,7 +234,7 @@ def _plane_wave_chain(M, d, off, p, digits):
     return Lf if f == 0 else _rot_apply(bwd, offs, p, f - 1, Lf)
 
 
-@pytest.mark.parametrize("digits,p,tol", [(3, 10, 2e-3), (5, 16, 2e-5), (6, 20, 3e-6)])
+@pytest.mark.parametrize("digits,p,tol", [(3, 10, 2e-3), (5, 16, 2e-5), (6, 20, 3e-6), (9, 24, 2e-10)])
 @pytest.mark.parametrize("d", range(6))
 def test_plane_wave_m2l_chain(d, digits, p, tol):
     off = np.array(OFFSETS[d], float)
