@@ -195,6 +195,8 @@ static void pack_tables(const OpTables &h, std::vector<char> &blob, std::vector<
     putT(h.forot_fwd);// 30
     putT(h.forot_bwd);// 31
     putI(h.frot_off); // 32
+    putI(h.u_k);      // 33
+    putI(h.u_start);  // 34
 }
 
 template <typename T>
@@ -239,6 +241,9 @@ static DevTables<T> bind_tables(const OpTables &h, char *base, const std::vector
     d.forot_bwd = reinterpret_cast<const T *>(base + o[31]);
     d.frot_off = reinterpret_cast<const int *>(base + o[32]);
     d.frot_len = h.frot_off.back();
+    d.u_k = reinterpret_cast<const int *>(base + o[33]);
+    d.u_start = reinterpret_cast<const int *>(base + o[34]);
+    d.NU = int(h.u_k.size());
     return d;
 }
 

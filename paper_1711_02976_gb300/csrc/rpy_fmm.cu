@@ -554,55 +554,144 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
             }
         }
         __syncthreads();
-        // W_j = (w_k/M_k) [A^0 + 2 sum_m i^m Re(A^m e^{i m a_j})], A = AE +- AO, all four
-        // sets per wave (one root lookup and index update serve four sets)
-        for (int j = threadIdx.x; j < S; j += blockDim.x) {
-            const int k = D.e_k[j];
-            const int j0 = D.k_start[k], jl = j - j0, Mk = 2 * (D.k_start[k + 1] - j0);
-            const cpx<T> *rt = D.roots + 2 * j0;
-            const cpx<T> *ae = AE + k * P1 * kSets;
-            const cpx<T> *ao = AO + k * P1 * kSets;
-            T er[kSets], orr[kSets], ei[kSets], oi[kSets];
-#pragma unroll
-            for (int st = 0; st < kSets; ++st) {
-                er[st] = ae[st].x;
-                orr[st] = ao[st].x;
-                ei[st] = 0;
-                oi[st] = 0;
-            }
-            int step2 = 2 * jl;
-            if (step2 >= Mk) step2 -= Mk;
-            int idx = 0;   // (m jl) mod Mk for even m
-            for (int m = 2; m <= p; m += 2) {
-                idx += step2;
-                if (idx >= Mk) idx -= Mk;
-                const cpx<T> z = rt[idx];
-#pragma unroll
+        if constexpr (sizeof(T) == 8) {
+            // W_j = (w_k/M_k) [A^0 + 2 sum_m i^m Re(A^m e^{i m a_j})], A = AE +- AO, all four
+            // sets per unit.  Waves t and M_k/2 - t of a node have angles a and pi - a:
+            // e^{i m (pi - a)} = (-1)^m conj(e^{i m a}), so with P = sum a.x z.x and
+            // Q = sum a.y z.y over even (or odd) m, Re(A z) = P - Q serves wave t and
+            // (-1)^m Re(A conj z) = +-(P + Q) its partner: two FMAs per (m, set) for
+            // both waves.  Real parts are stored after the even-m pass, imaginary parts
+            // after the odd-m pass.
+            const size_t dsz = size_t(kSets) * S;
+            for (int u = threadIdx.x; u < D.NU; u += blockDim.x) {
+                const int k = D.u_k[u];
+                const int j0 = D.k_start[k], H = D.k_start[k + 1] - j0, t = u - D.u_start[k], Mk = 2 * H;
+                const bool pair = t > 0 && 2 * t != H;
+                const int ja = j0 + t, jb = j0 + H - t;
+                const cpx<T> *rt = D.roots + 2 * j0;
+                const cpx<T> *ae = AE + k * P1 * kSets;
+                const cpx<T> *ao = AO + k * P1 * kSets;
+                const T wm = D.e_wm[ja];
+                T pe[kSets], qe[kSets], po[kSets], qo[kSets];
+    #pragma unroll
                 for (int st = 0; st < kSets; ++st) {
-                    const cpx<T> a = ae[m * kSets + st], o = ao[m * kSets + st];
-                    er[st] = fma(-a.y, z.y, fma(a.x, z.x, er[st]));
-                    orr[st] = fma(-o.y, z.y, fma(o.x, z.x, orr[st]));
+                    pe[st] = ae[st].x;
+                    qe[st] = 0;
+                    po[st] = ao[st].x;
+                    qo[st] = 0;
+                }
+                int step2 = 2 * t;
+                if (step2 >= Mk) step2 -= Mk;
+                int idx = 0;   // (m t) mod Mk for even m
+                for (int m = 2; m <= p; m += 2) {
+                    idx += step2;
+                    if (idx >= Mk) idx -= Mk;
+                    const cpx<T> z = rt[idx];
+    #pragma unroll
+                    for (int st = 0; st < kSets; ++st) {
+                        const cpx<T> a = ae[m * kSets + st], o = ao[m * kSets + st];
+                        pe[st] = fma(a.x, z.x, pe[st]);
+                        qe[st] = fma(a.y, z.y, qe[st]);
+                        po[st] = fma(o.x, z.x, po[st]);
+                        qo[st] = fma(o.y, z.y, qo[st]);
+                    }
+                }
+                // real parts: even m; + direction A = AE + AO, - direction AE - AO
+    #pragma unroll
+                for (int st = 0; st < kSets; ++st) {
+                    const T ea = pe[st] - qe[st], oa = po[st] - qo[st];
+                    Xo[base + size_t(2 * (f - f0)) * dsz + st * S + ja].x = wm * (ea + oa);
+                    Xo[base + size_t(2 * (f - f0) + 1) * dsz + st * S + ja].x = wm * (ea - oa);
+                    if (pair) {
+                        const T eb = pe[st] + qe[st], ob = po[st] + qo[st];
+                        Xo[base + size_t(2 * (f - f0)) * dsz + st * S + jb].x = wm * (eb + ob);
+                        Xo[base + size_t(2 * (f - f0) + 1) * dsz + st * S + jb].x = wm * (eb - ob);
+                    }
+                    pe[st] = 0;
+                    qe[st] = 0;
+                    po[st] = 0;
+                    qo[st] = 0;
+                }
+                idx = t;      // odd m, starting at m = 1
+                for (int m = 1; m <= p; m += 2) {
+                    const cpx<T> z = rt[idx];
+    #pragma unroll
+                    for (int st = 0; st < kSets; ++st) {
+                        const cpx<T> a = ae[m * kSets + st], o = ao[m * kSets + st];
+                        pe[st] = fma(a.x, z.x, pe[st]);
+                        qe[st] = fma(a.y, z.y, qe[st]);
+                        po[st] = fma(o.x, z.x, po[st]);
+                        qo[st] = fma(o.y, z.y, qo[st]);
+                    }
+                    idx += step2;
+                    if (idx >= Mk) idx -= Mk;
+                }
+                // imaginary parts: odd m, the partner with sign (-1)^m = -1
+    #pragma unroll
+                for (int st = 0; st < kSets; ++st) {
+                    const T ea = pe[st] - qe[st], oa = po[st] - qo[st];
+                    Xo[base + size_t(2 * (f - f0)) * dsz + st * S + ja].y = wm * (ea + oa);
+                    Xo[base + size_t(2 * (f - f0) + 1) * dsz + st * S + ja].y = wm * (ea - oa);
+                    if (pair) {
+                        const T eb = -(pe[st] + qe[st]), ob = -(po[st] + qo[st]);
+                        Xo[base + size_t(2 * (f - f0)) * dsz + st * S + jb].y = wm * (eb + ob);
+                        Xo[base + size_t(2 * (f - f0) + 1) * dsz + st * S + jb].y = wm * (eb - ob);
+                    }
                 }
             }
-            idx = jl;      // odd m, starting at m = 1
-            for (int m = 1; m <= p; m += 2) {
-                const cpx<T> z = rt[idx];
-#pragma unroll
+        } else {
+            // FP32: one wave per thread (the kernel is not bound by its FMAs, and
+            // twice the threads hide more latency)
+            // W_j = (w_k/M_k) [A^0 + 2 sum_m i^m Re(A^m e^{i m a_j})], A = AE +- AO, all four
+            // sets per wave (one root lookup and index update serve four sets)
+            for (int j = threadIdx.x; j < S; j += blockDim.x) {
+                const int k = D.e_k[j];
+                const int j0 = D.k_start[k], jl = j - j0, Mk = 2 * (D.k_start[k + 1] - j0);
+                const cpx<T> *rt = D.roots + 2 * j0;
+                const cpx<T> *ae = AE + k * P1 * kSets;
+                const cpx<T> *ao = AO + k * P1 * kSets;
+                T er[kSets], orr[kSets], ei[kSets], oi[kSets];
+    #pragma unroll
                 for (int st = 0; st < kSets; ++st) {
-                    const cpx<T> a = ae[m * kSets + st], o = ao[m * kSets + st];
-                    ei[st] = fma(-a.y, z.y, fma(a.x, z.x, ei[st]));
-                    oi[st] = fma(-o.y, z.y, fma(o.x, z.x, oi[st]));
+                    er[st] = ae[st].x;
+                    orr[st] = ao[st].x;
+                    ei[st] = 0;
+                    oi[st] = 0;
                 }
-                idx += step2;
-                if (idx >= Mk) idx -= Mk;
-            }
-            const T wm = D.e_wm[j];
-#pragma unroll
-            for (int st = 0; st < kSets; ++st) {
-                Xo[base + size_t(2 * (f - f0)) * kSets * S + st * S + j] =
-                    mk(wm * (er[st] + orr[st]), wm * (ei[st] + oi[st]));
-                Xo[base + size_t(2 * (f - f0) + 1) * kSets * S + st * S + j] =
-                    mk(wm * (er[st] - orr[st]), wm * (ei[st] - oi[st]));
+                int step2 = 2 * jl;
+                if (step2 >= Mk) step2 -= Mk;
+                int idx = 0;   // (m jl) mod Mk for even m
+                for (int m = 2; m <= p; m += 2) {
+                    idx += step2;
+                    if (idx >= Mk) idx -= Mk;
+                    const cpx<T> z = rt[idx];
+    #pragma unroll
+                    for (int st = 0; st < kSets; ++st) {
+                        const cpx<T> a = ae[m * kSets + st], o = ao[m * kSets + st];
+                        er[st] = fma(-a.y, z.y, fma(a.x, z.x, er[st]));
+                        orr[st] = fma(-o.y, z.y, fma(o.x, z.x, orr[st]));
+                    }
+                }
+                idx = jl;      // odd m, starting at m = 1
+                for (int m = 1; m <= p; m += 2) {
+                    const cpx<T> z = rt[idx];
+    #pragma unroll
+                    for (int st = 0; st < kSets; ++st) {
+                        const cpx<T> a = ae[m * kSets + st], o = ao[m * kSets + st];
+                        ei[st] = fma(-a.y, z.y, fma(a.x, z.x, ei[st]));
+                        oi[st] = fma(-o.y, z.y, fma(o.x, z.x, oi[st]));
+                    }
+                    idx += step2;
+                    if (idx >= Mk) idx -= Mk;
+                }
+                const T wm = D.e_wm[j];
+    #pragma unroll
+                for (int st = 0; st < kSets; ++st) {
+                    Xo[base + size_t(2 * (f - f0)) * kSets * S + st * S + j] =
+                        mk(wm * (er[st] + orr[st]), wm * (ei[st] + oi[st]));
+                    Xo[base + size_t(2 * (f - f0) + 1) * kSets * S + st * S + j] =
+                        mk(wm * (er[st] - orr[st]), wm * (ei[st] - oi[st]));
+                }
             }
         }
         __syncthreads();
@@ -703,9 +792,11 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = b0 + blockIdx.x;
     const int p = D.p, nc = ncoef(p), s = D.s, S = D.S, P1 = p + 1;
-    cpx<T> *Ip = reinterpret_cast<cpx<T> *>(smem_raw);   // [S]: + direction of the frame, one set
-    cpx<T> *Im = Ip + S;                                  // [S]: - direction
-    cpx<T> *Bp = Im + S;                                  // [s][P1]
+    const int NU = D.NU;
+    // per wave-pair unit u (waves t and M_k/2 - t of node k; see k_m2x), one set:
+    // Re and Im of I_t +- I_partner for the + direction (UQ[0..3]) and the - direction (UQ[4..7])
+    T *UQ = reinterpret_cast<T *>(smem_raw);
+    cpx<T> *Bp = reinterpret_cast<cpx<T> *>(UQ + 8 * NU);  // [s][P1]
     cpx<T> *Bm = Bp + s * P1;
     cpx<T> *Lf = Bm + s * P1;                             // [4][nc] frame accumulation
     cpx<T> *Lw = Lf + kSets * nc;                         // [4][nc] world accumulation
@@ -717,30 +808,43 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
             __syncthreads();
             const cpx<T> *sp = Xi + ((size_t(b) * (2 * nf) + 2 * (f - f0)) * kSets + st) * S;
             const cpx<T> *sm = Xi + ((size_t(b) * (2 * nf) + 2 * (f - f0) + 1) * kSets + st) * S;
-            for (int i = threadIdx.x; i < S; i += blockDim.x) {
-                Ip[i] = sp[i];
-                Im[i] = sm[i];
+            for (int u = threadIdx.x; u < NU; u += blockDim.x) {
+                const int k = D.u_k[u], j0 = D.k_start[k], H = D.k_start[k + 1] - j0, t = u - D.u_start[k];
+                const bool pair = t > 0 && 2 * t != H;
+                const cpx<T> pa = sp[j0 + t], ma = sm[j0 + t];
+                const cpx<T> pb = pair ? sp[j0 + H - t] : mk<T>(0, 0), mb = pair ? sm[j0 + H - t] : mk<T>(0, 0);
+                UQ[u] = pa.x + pb.x;
+                UQ[NU + u] = pa.x - pb.x;
+                UQ[2 * NU + u] = pa.y + pb.y;
+                UQ[3 * NU + u] = pa.y - pb.y;
+                UQ[4 * NU + u] = ma.x + mb.x;
+                UQ[5 * NU + u] = ma.x - mb.x;
+                UQ[6 * NU + u] = ma.y + mb.y;
+                UQ[7 * NU + u] = ma.y - mb.y;
             }
             __syncthreads();
             // b_k^m = sum_{j < M_k/2} (I_j + (-1)^m conj I_j) e^{-i m a_j}
             //       = 2 sum_j Re(I_j) e^{-i m a_j}      (m even)
             //       = 2i sum_j Im(I_j) e^{-i m a_j}     (m odd; the factor i is applied below)
+            // With e^{-i m (pi - a)} = (-1)^m conj(e^{-i m a}), a wave pair adds
+            // (v + (-1)^m v') cos(m a) - i (v - (-1)^m v') sin(m a): even m take the
+            // sum and difference of the real parts, odd m those of the imaginary parts.
             for (int e = threadIdx.x; e < s * P1; e += blockDim.x) {
-                int k = e / P1, m = e - k * P1;
-                int j0 = D.k_start[k], j1 = D.k_start[k + 1];
-                int Mk = 2 * (j1 - j0);
-                int mm = m % Mk;
+                const int k = e / P1, m = e - k * P1;
+                const int j0 = D.k_start[k], Mk = 2 * (D.k_start[k + 1] - j0);
+                const int u0 = D.u_start[k], u1 = D.u_start[k + 1];
+                const int mm = m % Mk;
                 const cpx<T> *rt = D.roots + 2 * j0;
+                const T *xp = UQ + ((m & 1) ? 3 : 0) * NU, *yp = UQ + ((m & 1) ? 2 : 1) * NU;
+                const T *xm = xp + 4 * NU, *ym = yp + 4 * NU;
                 T bpx = 0, bpy = 0, bmx = 0, bmy = 0;
                 int idx = 0;
-                for (int j = j0; j < j1; ++j) {
-                    cpx<T> r = rt[idx];
-                    T vp = (m & 1) ? Ip[j].y : Ip[j].x;
-                    T vm = (m & 1) ? Im[j].y : Im[j].x;
-                    bpx += vp * r.x;
-                    bpy -= vp * r.y;
-                    bmx += vm * r.x;
-                    bmy -= vm * r.y;
+                for (int u = u0; u < u1; ++u) {
+                    const cpx<T> r = rt[idx];
+                    bpx = fma(xp[u], r.x, bpx);
+                    bpy = fma(-yp[u], r.y, bpy);
+                    bmx = fma(xm[u], r.x, bmx);
+                    bmy = fma(-ym[u], r.y, bmy);
                     idx += mm;
                     if (idx >= Mk) idx -= Mk;
                 }
@@ -1188,9 +1292,9 @@ static size_t smem_m2x(int p, int s) {
     return sizeof(cpx<T>) * (3 * kSets * nc + 2 * kSets * s * (p + 1));
 }
 template <typename T>
-static size_t smem_x2l(int p, int s, int S) {
+static size_t smem_x2l(int p, int s, int NU) {
     int nc = ncoef(p);
-    return sizeof(cpx<T>) * (2 * S + 2 * s * (p + 1) + 4 * kSets * nc);
+    return sizeof(cpx<T>) * (4 * NU + 2 * s * (p + 1) + 4 * kSets * nc);
 }
 template <typename T>
 static size_t smem_far(int p) {
@@ -1282,12 +1386,12 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     const int nf = t.x_frames;
     size_t smx = smem_m2x<T>(p, D.s);
     RPY_TRY(set_smem(k_m2x<T>, smx));
-    size_t sxl = sizeof(T) == 4 ? smem_x2l4(p, D.s, D.S) : smem_x2l<T>(p, D.s, D.S);
+    size_t sxl = sizeof(T) == 4 ? smem_x2l4(p, D.s, D.S) : smem_x2l<T>(p, D.s, D.NU);
     if constexpr (sizeof(T) == 4) RPY_TRY(set_smem(k_x2l4, sxl));
     else RPY_TRY(set_smem(k_x2l<T>, sxl));
     for (int f0 = 0; f0 < 3; f0 += nf) {
         if (f0 == 0) prof_mark(t, RPY_STAGE_M2X, st);
-        k_m2x<T><<<n2, even_threads(D.S), smx, st>>>(b2, n2, D, M, Xo, f0, nf);
+        k_m2x<T><<<n2, even_threads(sizeof(T) == 8 ? D.NU : D.S), smx, st>>>(b2, n2, D, M, Xo, f0, nf);
         RPY_LAUNCHED(1);
         RPY_CHECK(cudaGetLastError());
         if (f0 == 0) prof_mark(t, RPY_STAGE_X2X, st);

@@ -115,6 +115,11 @@ struct OpTables {
     std::vector<int> e_k;         // [S] node of stored plane wave e
     std::vector<double> e_cos, e_sin, e_wm;   // [S] cos a, sin a, w_k / M_k
     std::vector<int> k_start;     // [s+1] first stored e of node k
+    // wave pairs: stored waves j and M_k/2 - j of a node have angles a and pi - a,
+    // so one set of products serves both; unit t of node k holds wave t and, for
+    // 0 < t < M_k/2 - t, its partner M_k/2 - t
+    std::vector<int> u_k;         // [NU] node of unit u
+    std::vector<int> u_start;     // [s+1] first unit of node k
     std::vector<double> shift;    // [216][S][2] e^{-lambda dz + i lambda (dx cos a + dy sin a)}
     // merge-and-shift groups per direction
     std::vector<int> grp_off;     // [6][G_MAX+1] start of group g in slot list (per direction)
@@ -156,6 +161,8 @@ struct DevTables {
     const cpx<T> *roots;
     const T *m2x_c, *x2l_c;
     const int *e_k, *k_start;
+    const int *u_k, *u_start;   // wave-pair units
+    int NU;
     const T *e_cos, *e_sin, *e_wm;
     const cpx<T> *shift;
     const int *grp_off, *grp_n, *grp_mask, *slot_list, *child_shift;

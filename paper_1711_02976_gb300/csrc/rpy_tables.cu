@@ -523,6 +523,14 @@ int build_tables(int p, int qd, OpTables &t) {
         }
     }
     t.k_start[q.s] = int(t.e_k.size());
+    t.u_k.clear();
+    t.u_start.assign(q.s + 1, 0);
+    for (int k = 0; k < q.s; ++k) {
+        t.u_start[k] = int(t.u_k.size());
+        const int H = q.m[k] / 2;
+        for (int u = 0; u < H / 2 + 1; ++u) t.u_k.push_back(k);
+    }
+    t.u_start[q.s] = int(t.u_k.size());
     t.shift.assign(size_t(216) * t.S * 2, 0.0);
     for (int off = 0; off < 216; ++off) {
         double dx = (off % 6) - 2.5, dy = ((off / 6) % 6) - 2.5, dz = (off / 36) - 2.5;
