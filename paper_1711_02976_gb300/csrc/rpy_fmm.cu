@@ -388,7 +388,7 @@ __global__ void k_l2l(int b0, int nb, DevTables<T> D, const int *par, const int 
 // The factorized rotation of the four sets: tmp <- za (src) (one 2x2 rotation per
 // coefficient), then dst <- zc (Y tmp), Y acting on real and imaginary parts
 // separately.  src and dst may not alias tmp; the caller synchronises after.
-template <typename T>
+template <typename T, bool QUARTER = false>
 __device__ void rotate_sets_f(const T *rf, const int *foff, int p, const cpx<T> *src, cpx<T> *tmp, cpx<T> *dst) {
     const int nc = ncoef(p);
     for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
@@ -405,9 +405,17 @@ __device__ void rotate_sets_f(const T *rf, const int *foff, int p, const cpx<T> 
         const T *yre = o + 4 * q + m * q, *yim = o + 4 * q + q * q + m * q;
         const cpx<T> *in = tmp + st * nc + tri(n, 0);
         T re = 0, im = 0;
-        for (int k = 0; k < q; ++k) {
-            re = fma(yre[k], in[k].x, re);
-            im = fma(yim[k], in[k].y, im);
+        if (QUARTER) {
+            // middle angle pi/2 (the frame rotations): the y blocks are checkerboards
+            // (checked when the tables are built); Im of m = 0 is zero for real fields
+            for (int k = (m + n) & 1; k < q; k += 2) re = fma(yre[k], in[k].x, re);
+            if (m > 0)
+                for (int k = 1 + ((m + n) & 1); k < q; k += 2) im = fma(yim[k], in[k].y, im);
+        } else {
+            for (int k = 0; k < q; ++k) {
+                re = fma(yre[k], in[k].x, re);
+                im = fma(yim[k], in[k].y, im);
+            }
         }
         const T c = o[2 * q + 2 * m], sn = o[2 * q + 2 * m + 1];
         dst[st * nc + i] = mk(fma(c, re, -sn * im), fma(sn, re, c * im));
@@ -522,7 +530,7 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
     for (int f = f0; f < f0 + nf; ++f) {
         const cpx<T> *Mu = Mw;
         if (f > 0) {
-            rotate_sets_f(D.frot_fwd + size_t(f - 1) * D.frot_len, D.frot_off, p, Mw, Tm, Mf);
+            rotate_sets_f<T, true>(D.frot_fwd + size_t(f - 1) * D.frot_len, D.frot_off, p, Mw, Tm, Mf);
             __syncthreads();
             Mu = Mf;
         }
@@ -872,7 +880,7 @@ __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *
         if (f == 0) {
             for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lf[i];
         } else {
-            rotate_sets_f(D.frot_bwd + size_t(f - 1) * D.frot_len, D.frot_off, p, Lf, Tm, Lr);
+            rotate_sets_f<T, true>(D.frot_bwd + size_t(f - 1) * D.frot_len, D.frot_off, p, Lf, Tm, Lr);
             __syncthreads();
             for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lr[i];
         }
@@ -972,7 +980,7 @@ __global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi,
         if (f == 0) {
             for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lf[i];
         } else {
-            rotate_sets_f(D.frot_bwd + size_t(f - 1) * D.frot_len, D.frot_off, p, Lf, Tm, Lr);
+            rotate_sets_f<float, false>(D.frot_bwd + size_t(f - 1) * D.frot_len, D.frot_off, p, Lf, Tm, Lr);
             __syncthreads();
             for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Lw[i] += Lr[i];
         }

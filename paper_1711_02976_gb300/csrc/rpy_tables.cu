@@ -332,8 +332,13 @@ static void rot_y(double b, double R[9]) {
 int factor_len(int n) { return 4 * (n + 1) + 2 * (n + 1) * (n + 1); }
 
 // Fills `out` (layout above) for the rotation X; false if a factor does not have the
-// expected structure (then the dense blocks must be used).
-static bool factor_rotation(const double X[9], int p, const std::vector<int> &foff, double *out) {
+// expected structure (then the dense blocks must be used).  With `quarter` (the
+// frame rotations, whose middle angle is pi/2) the y blocks must also have the
+// checkerboard structure the kernels rely on: Yre[mo][mi] = 0 unless mo + mi + n
+// is even, Yim[mo][mi] = 0 unless mo + mi + n is odd (rows and columns m >= 1;
+// the m = 0 imaginary parts of real fields vanish).
+static bool factor_rotation(const double X[9], int p, const std::vector<int> &foff, double *out,
+                            bool quarter = false) {
     // X = Rz(a) Ry(b) Rz(c): X22 = cos b, X02 = cos a sin b, X12 = sin a sin b,
     // X20 = -sin b cos c, X21 = sin b sin c
     const double b = std::acos(std::max(-1.0, std::min(1.0, X[8])));
@@ -386,6 +391,14 @@ static bool factor_rotation(const double X[9], int p, const std::vector<int> &fo
                 yre[mo * q + mi] = FY[(2 * mo) * B + 2 * mi];
                 yim[mo * q + mi] = FY[(2 * mo + 1) * B + 2 * mi + 1];
             }
+        if (quarter)
+            for (int mo = 0; mo <= n; ++mo)
+                for (int mi = 0; mi <= n; ++mi) {
+                    const bool even = ((mo + mi + n) & 1) == 0;
+                    if (!even && std::fabs(yre[mo * q + mi]) > 1e-13) return false;
+                    if (mo > 0 && mi > 0 && even && std::fabs(yim[mo * q + mi]) > 1e-13) return false;
+                    if (mo == 0 && mi > 0 && std::fabs(yim[mi]) > 1e-13) return false;
+                }
     }
     return true;
 }
@@ -557,8 +570,8 @@ int build_tables(int p, int qd, OpTables &t) {
             const double *Q = f == 0 ? kQx : kQy;
             double Qt[9];
             transpose3(Q, Qt);
-            if (!factor_rotation(Qt, p, t.frot_off, &t.frot_fwd[size_t(f) * FL]) ||
-                !factor_rotation(Q, p, t.frot_off, &t.frot_bwd[size_t(f) * FL]))
+            if (!factor_rotation(Qt, p, t.frot_off, &t.frot_fwd[size_t(f) * FL], true) ||
+                !factor_rotation(Q, p, t.frot_off, &t.frot_bwd[size_t(f) * FL], true))
                 return RPY_ERR_INTERNAL;
         }
         for (int o = 0; o < 8; ++o) {
