@@ -301,8 +301,10 @@ const char *rpy_last_cuda_error(void);
  * 5 M2X coefficients, 6 X2L coefficients, 7 stored plane waves (k, cos, sin,
  * w/M), 8 shift factors, 9 merge-and-shift groups, 10 rotation block offsets,
  * 11 quadrature (s, then lambda, w, M per node), 12 / 13 child-octant rotations
- * world->frame / frame->world, 14 / 15 z-axis M2M / L2L shift coefficients.  dst (host, may be NULL to
- * query) receives *count doubles.
+ * world->frame / frame->world, 14 / 15 z-axis M2M / L2L shift coefficients, 16 / 17 / 18
+ * per-axis shift factors e^{-lambda dz} [6][S], e^{i lambda dx cos a} and e^{i lambda dy sin a}
+ * [6][S][2] (offset index - 2.5 along the axis).  dst (host, may be NULL to query) receives
+ * *count doubles.
  */
 int rpy_debug_table(int p, int digits, int which, double *dst, int64_t capacity, int64_t *count);
 

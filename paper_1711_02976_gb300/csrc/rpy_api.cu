@@ -197,6 +197,9 @@ static void pack_tables(const OpTables &h, std::vector<char> &blob, std::vector<
     putI(h.frot_off); // 32
     putI(h.u_k);      // 33
     putI(h.u_start);  // 34
+    putT(h.shz);      // 35
+    putT(h.shx);      // 36
+    putT(h.shy);      // 37
 }
 
 template <typename T>
@@ -244,6 +247,9 @@ static DevTables<T> bind_tables(const OpTables &h, char *base, const std::vector
     d.u_k = reinterpret_cast<const int *>(base + o[33]);
     d.u_start = reinterpret_cast<const int *>(base + o[34]);
     d.NU = int(h.u_k.size());
+    d.shz = reinterpret_cast<const T *>(base + o[35]);
+    d.shx = reinterpret_cast<const cpx<T> *>(base + o[36]);
+    d.shy = reinterpret_cast<const cpx<T> *>(base + o[37]);
     return d;
 }
 
@@ -963,6 +969,9 @@ int rpy_debug_table(int p, int digits, int which, double *dst, int64_t capacity,
         case 13: v = &h->orot_bwd; break;
         case 14: v = &h->zm2m; break;
         case 15: v = &h->zl2l; break;
+        case 16: v = &h->shz; break;
+        case 17: v = &h->shx; break;
+        case 18: v = &h->shy; break;
         case 11:   // quadrature: s, then lambda, weight, M per node
         {
             const ExpQuad &q = exp_quadrature(digits);

@@ -707,12 +707,17 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
 }
 
 // ---------------------------------------------------------------- X2X merge-and-shift
-template <typename T>
+template <typename T, bool FAC>
 __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const int *child, const int *leaf,
                       const cpx<T> *Xo, cpx<T> *Xi, int f0, int nf) {
     __shared__ int src[216];
     __shared__ int vsrc[216], vsh[216], vpre[217];   // the present sources, compacted in slot order
     __shared__ int vend[216];   // child mask of its group at the last present source of a group, else 0
+    // FAC (FP32, few plane waves): the shift of a source as the product of its
+    // per-axis factors, from shared memory (z offsets x S, x offsets, y offsets);
+    // otherwise the shift table
+    __shared__ int voz[216], vox[216], voy[216];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     int P = parents[blockIdx.x];
     const int dl = blockIdx.y, d = 2 * f0 + dl;   // direction, and its slot in this pass's buffers
     const int S = D.S;
@@ -751,7 +756,23 @@ __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const
     }
     __syncthreads();
     const int nz = vpre[goff[ng]];
-    for (int z = threadIdx.x; z < nz; z += blockDim.x) vend[z] = 0;
+    for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+        vend[z] = 0;
+        const int o = vsh[z];
+        vox[z] = (o % 6) * S;
+        voy[z] = ((o / 6) % 6) * S;
+        voz[z] = (o / 36) * S;
+    }
+    T *sZ = reinterpret_cast<T *>(smem_raw);
+    cpx<T> *sX = reinterpret_cast<cpx<T> *>(sZ + ((6 * S + 3) & ~3));
+    cpx<T> *sY = sX + 6 * S;
+    if constexpr (FAC) {
+        for (int i = threadIdx.x; i < 6 * S; i += blockDim.x) {
+            sZ[i] = D.shz[i];
+            sX[i] = D.shx[i];
+            sY[i] = D.shy[i];
+        }
+    }
     __syncthreads();
     for (int g = threadIdx.x; g < ng; g += blockDim.x) {
         const int z1 = vpre[goff[g + 1]];
@@ -774,7 +795,14 @@ __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const
 #pragma unroll 4
         for (int z = 0; z < nz; ++z) {
             const cpx<T> x = Xd[size_t(vsrc[z]) * dstride + e];
-            const cpx<T> sh = D.shift[size_t(vsh[z]) * S + j];
+            cpx<T> sh;
+            if constexpr (FAC) {
+                const cpx<T> a = sX[vox[z] + j], b = sY[voy[z] + j];
+                const T c = sZ[voz[z] + j];
+                sh = mk(c * fmaf(a.x, b.x, -a.y * b.y), c * fmaf(a.x, b.y, a.y * b.x));
+            } else {
+                sh = D.shift[size_t(vsh[z]) * S + j];
+            }
             ga.x = fma(-x.y, sh.y, fma(x.x, sh.x, ga.x));
             ga.y = fma(x.y, sh.x, fma(x.x, sh.y, ga.y));
             const int mask = vend[z];   // block-uniform
@@ -1405,7 +1433,22 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
         if (f0 == 0) prof_mark(t, RPY_STAGE_X2X, st);
         if (t.n_x2x_par > 0) {
             dim3 g(t.n_x2x_par, 2 * nf);
-            k_x2x<T><<<g, x2x_threads(D.S), 0, st>>>(t.x2x_par, D, t.b_coll, t.b_child, t.b_leaf, Xo, Xi, f0, nf);
+            // FP32 with up to 256 stored waves: shifts from per-axis factors in shared
+            // memory (measured faster there; at more waves the shared memory costs
+            // occupancy and the table is faster)
+            bool fac = false;
+            if constexpr (sizeof(T) == 4) {
+                if (D.S <= 256) {
+                    const size_t sxx = sizeof(T) * ((6 * D.S + 3) & ~3) + 2 * sizeof(cpx<T>) * 6 * D.S;
+                    k_x2x<T, true><<<g, x2x_threads(D.S), sxx, st>>>(t.x2x_par, D, t.b_coll, t.b_child, t.b_leaf,
+                                                                     Xo, Xi, f0, nf);
+                    fac = true;
+                }
+            }
+            if (!fac) {
+                k_x2x<T, false><<<g, x2x_threads(D.S), 0, st>>>(t.x2x_par, D, t.b_coll, t.b_child, t.b_leaf, Xo, Xi,
+                                                                f0, nf);
+            }
             RPY_LAUNCHED(1);
             RPY_CHECK(cudaGetLastError());
         }

@@ -121,6 +121,10 @@ struct OpTables {
     std::vector<int> u_k;         // [NU] node of unit u
     std::vector<int> u_start;     // [s+1] first unit of node k
     std::vector<double> shift;    // [216][S][2] e^{-lambda dz + i lambda (dx cos a + dy sin a)}
+    // the same shifts per axis: shift(off) = shz[iz] * shx[ix] * shy[iy] with
+    // off = ix + 6 iy + 36 iz (offset d = index - 2.5 along each axis)
+    std::vector<double> shz;      // [6][S] e^{-lambda dz}
+    std::vector<double> shx, shy; // [6][S][2] e^{i lambda dx cos a}, e^{i lambda dy sin a}
     // merge-and-shift groups per direction
     std::vector<int> grp_off;     // [6][G_MAX+1] start of group g in slot list (per direction)
     std::vector<int> grp_n;       // [6] number of groups
@@ -165,6 +169,8 @@ struct DevTables {
     int NU;
     const T *e_cos, *e_sin, *e_wm;
     const cpx<T> *shift;
+    const T *shz;
+    const cpx<T> *shx, *shy;
     const int *grp_off, *grp_n, *grp_mask, *slot_list, *child_shift;
 };
 

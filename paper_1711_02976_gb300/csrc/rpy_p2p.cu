@@ -370,7 +370,9 @@ __global__ void __launch_bounds__(kP32Threads, 4) k_p2p32(const int2 *items, con
             const int Ns = lpre[L];
             for (int c0 = 0; c0 < Ns; c0 += kP32Chunk) {
                 const int nS = min(kP32Chunk, Ns - c0);
-                __syncthreads();
+                // no barrier here: the one after the prefix (first chunk) or after the
+                // previous chunk's compute (and its FP64 queue pass) already orders
+                // every read of sP, sQ2 and sJ before this chunk's writes
                 for (int e = threadIdx.x; e < nS; e += kP32Threads) {
                     int q = c0 + e, lo = 0, hi = L;   // box: lpre[lo] <= q < lpre[lo + 1]
                     while (hi - lo > 1) {

@@ -555,6 +555,18 @@ int build_tables(int p, int qd, OpTables &t) {
             t.shift[(size_t(off) * t.S + e) * 2 + 1] = mag * std::sin(ph);
         }
     }
+    t.shz.assign(size_t(6) * t.S, 0.0);
+    t.shx.assign(size_t(6) * t.S * 2, 0.0);
+    t.shy.assign(size_t(6) * t.S * 2, 0.0);
+    for (int i = 0; i < 6; ++i)
+        for (int e = 0; e < t.S; ++e) {
+            const double lam = q.lambda[t.e_k[e]], d = i - 2.5;
+            t.shz[size_t(i) * t.S + e] = std::exp(-lam * d);
+            t.shx[(size_t(i) * t.S + e) * 2] = std::cos(lam * d * t.e_cos[e]);
+            t.shx[(size_t(i) * t.S + e) * 2 + 1] = std::sin(lam * d * t.e_cos[e]);
+            t.shy[(size_t(i) * t.S + e) * 2] = std::cos(lam * d * t.e_sin[e]);
+            t.shy[(size_t(i) * t.S + e) * 2 + 1] = std::sin(lam * d * t.e_sin[e]);
+        }
     build_groups(t);
     // factorized rotations: frames (x, y) and the eight child octants, forward and back
     {

@@ -264,6 +264,24 @@ def test_shift_table_formula():
         np.testing.assert_allclose(sh[off, :, 0] + 1j * sh[off, :, 1], ref, rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("digits", [3, 6])
+def test_per_axis_shift_factors_multiply_to_the_shift_table(digits):
+    """The FP32 X2X forms each plane-wave shift from per-axis factors: their
+    product must be the full shift e^{-lambda dz + i lambda (dx cos a + dy sin a)}."""
+    p = 8
+    pw = rp.rpy_debug_table(p, digits, 7).reshape(-1, 4)
+    S = pw.shape[0]
+    sh = rp.rpy_debug_table(p, digits, 8).reshape(216, S, 2)
+    sz = rp.rpy_debug_table(p, digits, 16).reshape(6, S)
+    sx = rp.rpy_debug_table(p, digits, 17).reshape(6, S, 2)
+    sy = rp.rpy_debug_table(p, digits, 18).reshape(6, S, 2)
+    cx, cy = sx[..., 0] + 1j * sx[..., 1], sy[..., 0] + 1j * sy[..., 1]
+    for off in range(216):
+        ix, iy, iz = off % 6, (off // 6) % 6, off // 36
+        prod = sz[iz] * cx[ix] * cy[iy]
+        np.testing.assert_allclose(prod, sh[off, :, 0] + 1j * sh[off, :, 1], rtol=1e-13, atol=1e-13)
+
+
 def test_merge_and_shift_groups_cover_v_lists():
     """Every (child of a parent, child of a colleague) pair that is not adjacent
     is served by exactly one direction and one group; adjacent pairs by none."""
