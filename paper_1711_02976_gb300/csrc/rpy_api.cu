@@ -387,16 +387,29 @@ static int upload_s(Tree &t, const double *s_host, cudaStream_t st) {
 }
 
 // Body of the matvec on stream st: near field, direct substitutes, far field.
-static int matvec_body(Tree &t, const SysConst &sc, int parts, cudaStream_t st) {
+// With `side` (the captured graph) the two pair passes run on side_stream
+// beside the far-field chain and are joined back into st at the end; the
+// stage-timing path keeps them in sequence.
+static int matvec_body(Tree &t, const SysConst &sc, int parts, cudaStream_t st, bool side = false) {
+    cudaStream_t sp = st;
+    if (side) {
+        RPY_CHECK(cudaEventRecord(t.fork_ev, st));
+        RPY_CHECK(cudaStreamWaitEvent(t.side_stream, t.fork_ev, 0));
+        sp = t.side_stream;
+    }
     prof_mark(t, RPY_STAGE_P2P, st);
-    if (parts & RPY_PART_NEAR) RPY_TRY(run_p2p(t, t.fs, t.u_near, sc, st, false));
-    if (parts & RPY_PART_FAR) RPY_TRY(run_p2p(t, t.fs, t.u_dir, sc, st, true));
+    if (parts & RPY_PART_NEAR) RPY_TRY(run_p2p(t, t.fs, t.u_near, sc, sp, false));
+    if (parts & RPY_PART_FAR) RPY_TRY(run_p2p(t, t.fs, t.u_dir, sc, sp, true));
     prof_mark(t, RPY_STAGE_P2M, st);
     if (parts & RPY_PART_FAR) {
         if (t.params.precision == RPY_FP32)
             RPY_TRY(run_far_t<float>(t, t.dt32, t.fs, nullptr, t.u_far, nullptr, sc, st));
         else
             RPY_TRY(run_far_t<double>(t, t.dt64, t.fs, nullptr, t.u_far, nullptr, sc, st));
+    }
+    if (side) {
+        RPY_CHECK(cudaEventRecord(t.join_ev, t.side_stream));
+        RPY_CHECK(cudaStreamWaitEvent(st, t.join_ev, 0));
     }
     return RPY_OK;
 }
@@ -410,8 +423,11 @@ static void drop_graph(Tree &t) {
 // stream is not allowed) and keep the instantiated graph.
 static int capture_graph(Tree &t, const SysConst &sc) {
     if (!t.cap_stream) RPY_CHECK(cudaStreamCreateWithFlags(&t.cap_stream, cudaStreamNonBlocking));
+    if (!t.side_stream) RPY_CHECK(cudaStreamCreateWithFlags(&t.side_stream, cudaStreamNonBlocking));
+    if (!t.fork_ev) RPY_CHECK(cudaEventCreateWithFlags(&t.fork_ev, cudaEventDisableTiming));
+    if (!t.join_ev) RPY_CHECK(cudaEventCreateWithFlags(&t.join_ev, cudaEventDisableTiming));
     RPY_CHECK(cudaStreamBeginCapture(t.cap_stream, cudaStreamCaptureModeThreadLocal));
-    int s = matvec_body(t, sc, RPY_PART_ALL, t.cap_stream);
+    int s = matvec_body(t, sc, RPY_PART_ALL, t.cap_stream, true);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(t.cap_stream, &g);
     if (s != RPY_OK) {
@@ -596,6 +612,9 @@ int rpy_tree_update_positions(rpy_tree h, const double *pos_dev, void *stream) {
     for (int k = 0; k < 16; ++k) fresh.ev[k] = t.ev[k];
     fresh.done = t.done;
     fresh.cap_stream = t.cap_stream;
+    fresh.side_stream = t.side_stream;
+    fresh.fork_ev = t.fork_ev;
+    fresh.join_ev = t.join_ev;
     fresh.sys_off_h = t.sys_off_h;
     fresh.a_h = t.a_h;
     fresh.cache = std::move(t.cache);
@@ -847,6 +866,9 @@ void rpy_tree_free(rpy_tree h) {
         if (t.done) cudaEventDestroy(t.done);
         drop_graph(t);
         if (t.cap_stream) cudaStreamDestroy(t.cap_stream);
+        if (t.side_stream) cudaStreamDestroy(t.side_stream);
+        if (t.fork_ev) cudaEventDestroy(t.fork_ev);
+        if (t.join_ev) cudaEventDestroy(t.join_ev);
     }
     h->magic = 0;
     delete h;

@@ -270,6 +270,10 @@ struct Tree {
     cudaEvent_t done = nullptr;       // recorded after every asynchronous call (survives the caller's stream)
     // CUDA graph of the matvec body (P2P .. L2P), captured on the second matvec of a build
     cudaStream_t cap_stream = nullptr;
+    // captured matvec: the near field runs on side_stream beside the far field
+    // (fork_ev / join_ev order the two branches inside the graph)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int matvecs = 0;                  // matvecs since the last build
     cudaEvent_t ev[16] = {};
