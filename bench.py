@@ -24,6 +24,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -159,6 +160,21 @@ def make_workload(name):
         return Forest(synth.config4(nsys=24))
     w = getattr(synth, gen)()
     return Forest(w) if isinstance(w, list) else w
+
+
+def host_cpu():
+    """The host the CPU baseline ran on: model name, online cores, cores in this
+    process's affinity mask."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model, "nproc": os.cpu_count(), "affinity": len(os.sched_getaffinity(0))}
 
 
 def flops_model(stats, stage):
@@ -560,6 +576,7 @@ def main():
                           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                           "config": {"workload": args.config, "description": CONFIGS[args.config]["desc"]},
                           "cpu_baseline": {"value": round(v, 6), "unit": "Mbeads/s", "cores": th, "kind": "oracle",
+                                           "host": host_cpu(),
                                            "sample": f"{k} targets x all {sysm.n} sources per step; extrapolated "
                                                      f"O(N^2) direct rate"},
                           "e2e": {"value": round(v, 6), "unit": "Mbeads/s", "h2d_bytes_per_step": 0,
@@ -601,7 +618,7 @@ def main():
                 "params": pf["config"]["params"],
                 "note": "same workload and digit setting, P2P and translations in FP32 with compensated sums"}
         result["cpu_baseline"] = {"value": round(len(tg) / dt / 1e6, 6), "unit": "Mbeads/s", "cores": th,
-                                  "kind": "oracle",
+                                  "kind": "oracle", "host": host_cpu(),
                                   "sample": (f"all {sysm.n} beads (full direct sum)" if len(tg) == sysm.n else
                                              f"{len(tg)} targets (seed 12345) x all {sysm.n} sources; extrapolated "
                                              f"O(N^2) direct rate = targets/s")}
