@@ -475,7 +475,7 @@ def serve(args, local):
            "total_beads": int(sum(sy.n for sy in systems)), "capacity_req_s": round(cap_rps, 3),
            "closed_loop": {"Mbeads_s": round(beads / wall / 1e6, 3), "p50_ms": round(float(np.percentile(lat, 50)), 2),
                            "p99_ms": round(float(np.percentile(lat, 99)), 2)}, "rates": []}
-    for frac in (0.5, 0.9):
+    for frac in (0.3, 0.5, 0.7, 0.9):
         t0 = time.perf_counter()
         lat, beads = run(args.serve_requests, frac * cap_rps)
         wall = time.perf_counter() - t0
@@ -548,7 +548,7 @@ def main():
                          "e.g. to profile the autotuned configuration")
     ap.add_argument("--mode", default="bench", choices=["bench", "serve", "bd"])
     ap.add_argument("--serve-systems", type=int, default=64)
-    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=64, help="requests per arrival rate")
     ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     ws, rank, local = _dist()
