@@ -1397,8 +1397,10 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     prof_mark(t, RPY_STAGE_M2M, st);
-    // FP64: rotation-based (fewer FP64 operations); FP32: dense operator
-    const bool rot = sizeof(T) == 8;
+    // FP64: rotation-based M2M and L2L (fewer FP64 operations).  FP32: the dense
+    // operators, except L2L from p = 12 (measured: one child per block makes the
+    // rotation form faster there; M2M's eight children per block do not)
+    const bool rot = sizeof(T) == 8, rot_l = rot || p >= 12;
     size_t smr3 = sizeof(cpx<T>) * 4 * kSets * nc, smr2 = sizeof(cpx<T>) * 3 * kSets * nc;
     int Dd = 2 * nc, thr = ((Dd + 31) / 32) * 32;
     size_t smd = sizeof(T) * kSets * Dd;
@@ -1473,7 +1475,7 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     for (int l = 3; l < t.nlevels; ++l) {
         int lb = t.level_off[l], ln = t.level_off[l + 1] - lb;
         if (ln > 0) {
-            if (rot) k_l2l_rot<T><<<ln, 256, smr2, st>>>(lb, ln, D, t.b_parent, t.b_cell, L);
+            if (rot_l) k_l2l_rot<T><<<ln, 256, smr2, st>>>(lb, ln, D, t.b_parent, t.b_cell, L);
             else k_l2l<T><<<ln, thr, smd, st>>>(lb, ln, D, t.b_parent, t.b_cell, L);
             RPY_LAUNCHED(1);
         }
