@@ -339,6 +339,12 @@ int tree_alloc_workspace(Tree &t, cudaStream_t) {
     RPY_TRY(dev_alloc(t, &t.Xo, es * nb * 2 * t.x_frames * kSets * h.S));
     RPY_TRY(dev_alloc(t, &t.Xi, es * nb * 2 * t.x_frames * kSets * h.S));
     RPY_TRY(dev_alloc(t, &t.EVg, es * size_t(t.nleaf) * 18 * h.nc));
+    if (t.params.precision != RPY_FP32) {
+        size_t wide = 0;
+        for (int l = 2; l + 1 < int(t.level_off.size()); ++l)
+            wide = std::max(wide, size_t(t.level_off[l + 1] - t.level_off[l]));
+        if (wide > 0) RPY_TRY(dev_alloc(t, &t.m2m_scratch, es * wide * 8 * kSets * h.nc));
+    }
     RPY_TRY(dev_alloc(t, (void **)&t.fs, sizeof(double) * 3 * t.n));
     if (t.params.precision == RPY_FP32) {
         RPY_TRY(dev_alloc(t, (void **)&t.p32, sizeof(float) * 6 * t.n));

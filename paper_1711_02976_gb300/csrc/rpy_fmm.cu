@@ -481,6 +481,57 @@ __global__ void k_m2m_rot(int b0, int nb, DevTables<T> D, const int *leaf, const
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) dst[i] = acc[i];
 }
 
+// One child per block (the children of one level): rotate, z-shift and rotate
+// back as k_m2m_rot, then write the child's share to its slot Sc[parent][octant];
+// k_m2m_sum adds the slots of each parent in octant order, so that the result
+// is the same, bit for bit, as k_m2m_rot's eight children in sequence.
+template <typename T>
+__global__ void k_m2m_child(int c0, int pb0, DevTables<T> D, const int *par, const int *cell, const cpx<T> *M,
+                            cpx<T> *Sc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = c0 + blockIdx.x;
+    const int p = D.p, nc = ncoef(p), P1 = p + 1;
+    cpx<T> *X = reinterpret_cast<cpx<T> *>(smem_raw);
+    cpx<T> *Y = X + kSets * nc;
+    cpx<T> *Tm = Y + kSets * nc;   // rotation scratch
+    const int o = (cell[3 * c] & 1) | ((cell[3 * c + 1] & 1) << 1) | ((cell[3 * c + 2] & 1) << 2);
+    const cpx<T> *src = M + size_t(c) * kSets * nc;
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) X[i] = src[i];
+    __syncthreads();
+    rotate_sets_f(D.forot_fwd + size_t(o) * D.frot_len, D.frot_off, p, X, Tm, Y);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
+        int st = e / nc, i = e - st * nc;
+        int n = deg_of(i), m = i - tri(n, 0);
+        const T *z = D.zm2m + size_t(i) * P1;
+        cpx<T> a = mk<T>(0, 0);
+        for (int k = m; k <= n; ++k) a += z[k] * Y[st * nc + tri(k, m)];
+        X[e] = a;
+    }
+    __syncthreads();
+    rotate_sets_f(D.forot_bwd + size_t(o) * D.frot_len, D.frot_off, p, X, Tm, Y);
+    __syncthreads();
+    cpx<T> *dst = Sc + (size_t(par[c] - pb0) * 8 + o) * kSets * nc;
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) dst[i] = Y[i];
+}
+
+template <typename T>
+__global__ void k_m2m_sum(int b0, int nc4, const int *leaf, const int *child, const cpx<T> *Sc, cpx<T> *M) {
+    const int b = b0 + blockIdx.x;
+    if (leaf[b]) return;
+    int ch[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) ch[o] = child[8 * b + o];
+    const cpx<T> *src = Sc + size_t(blockIdx.x) * 8 * nc4;
+    for (int i = threadIdx.x; i < nc4; i += blockDim.x) {
+        cpx<T> acc = mk<T>(0, 0);
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+            if (ch[o] >= 0) acc += src[size_t(o) * nc4 + i];
+        M[size_t(b) * nc4 + i] = acc;
+    }
+}
+
 template <typename T>
 __global__ void k_l2l_rot(int b0, int nb, DevTables<T> D, const int *par, const int *cell, cpx<T> *L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1406,14 +1457,23 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     size_t smd = sizeof(T) * kSets * Dd;
     RPY_TRY(set_smem(k_m2m_rot<T>, smr3));
     RPY_TRY(set_smem(k_l2l_rot<T>, smr2));
+    RPY_TRY(set_smem(k_m2m_child<T>, smr2));
     RPY_TRY(set_smem(k_m2m<T>, smd));
     RPY_TRY(set_smem(k_l2l<T>, smd));
     for (int l = t.nlevels - 2; l >= 2; --l) {
         int lb = t.level_off[l], ln = t.level_off[l + 1] - lb;
         if (ln > 0) {
-            if (rot) k_m2m_rot<T><<<ln, 256, smr3, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
-            else k_m2m<T><<<ln, thr, smd, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
-            RPY_LAUNCHED(1);
+            const int cb = t.level_off[l + 1], cn = t.level_off[l + 2] - cb;   // their children
+            if (rot && t.m2m_scratch && cn > 0) {
+                cpx<T> *Sc = static_cast<cpx<T> *>(t.m2m_scratch);
+                k_m2m_child<T><<<cn, 256, smr2, st>>>(cb, lb, D, t.b_parent, t.b_cell, M, Sc);
+                k_m2m_sum<T><<<ln, 256, 0, st>>>(lb, kSets * nc, t.b_leaf, t.b_child, Sc, M);
+                RPY_LAUNCHED(2);
+            } else {
+                if (rot) k_m2m_rot<T><<<ln, 256, smr3, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
+                else k_m2m<T><<<ln, thr, smd, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
+                RPY_LAUNCHED(1);
+            }
         }
     }
     RPY_CHECK(cudaGetLastError());

@@ -237,6 +237,7 @@ struct Tree {
     // expansions and matvec workspace
     void *M = nullptr, *L = nullptr, *Xo = nullptr, *Xi = nullptr;
     int x_frames = 3;                 // plane-wave frames per pass (3 or 1)
+    void *m2m_scratch = nullptr;      // FP64 M2M: [boxes of the widest level][8 octants][4][nc] child shares
     void *EVg = nullptr;              // [nleaf][18][ncoef(p)] derived local expansions of Eq. (2.8)
     double *fs = nullptr;             // sorted forces SoA [3][n]
     float *p32 = nullptr;             // FP32 form: sorted positions as hi + lo floats, [6][n] (x,y,z hi; x,y,z lo)
