@@ -1449,8 +1449,7 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     RPY_CHECK(cudaGetLastError());
     prof_mark(t, RPY_STAGE_M2M, st);
     // FP64: rotation-based M2M and L2L (fewer FP64 operations).  FP32: the dense
-    // operators, except L2L from p = 12 (measured: one child per block makes the
-    // rotation form faster there; M2M's eight children per block do not)
+    // operators below p = 12, the rotation forms (one child per block) from there
     const bool rot = sizeof(T) == 8, rot_l = rot || p >= 12;
     size_t smr3 = sizeof(cpx<T>) * 4 * kSets * nc, smr2 = sizeof(cpx<T>) * 3 * kSets * nc;
     int Dd = 2 * nc, thr = ((Dd + 31) / 32) * 32;
@@ -1464,7 +1463,7 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
         int lb = t.level_off[l], ln = t.level_off[l + 1] - lb;
         if (ln > 0) {
             const int cb = t.level_off[l + 1], cn = t.level_off[l + 2] - cb;   // their children
-            if (rot && t.m2m_scratch && cn > 0) {
+            if (rot_l && t.m2m_scratch && cn > 0) {
                 cpx<T> *Sc = static_cast<cpx<T> *>(t.m2m_scratch);
                 k_m2m_child<T><<<cn, 256, smr2, st>>>(cb, lb, D, t.b_parent, t.b_cell, M, Sc);
                 k_m2m_sum<T><<<ln, 256, 0, st>>>(lb, kSets * nc, t.b_leaf, t.b_child, Sc, M);
