@@ -476,3 +476,38 @@ def test_9digit_sphere_sampled_parity():
     assert st["digits"] == 9 and st["order_p"] == 26 and st["quad"] in (0, 9)
     with pytest.raises(Exception):
         rp.rpy_forest_build(cuda_tensor(sysm.pos), [0, sysm.n], [sysm.a], 9, precision=rp.RPY_FP32)
+
+
+def test_laplace_far_field_error_decays_with_order_and_hessian_is_traceless():
+    """The Laplace far field of the FMM (9-digit plane-wave rule, so that the
+    truncation at order p dominates; pure FMM) against direct sums at p = 4, 8, 12,
+    16: the error falls by a factor of at least 3 per step of 4 in p (geometric
+    decay), and the Hessian of every expansion has zero trace (the expansions are
+    harmonic)."""
+    import torch
+    pos = _clustered(2000, 5)
+    rng = np.random.default_rng(6)
+    q = rng.standard_normal((len(pos), 4))
+    errs = []
+    for p in (4, 8, 12, 16):
+        t = rp.rpy_forest_build(cuda_tensor(pos), [0, len(pos)], [1e-5], 9, leaf_cap=12, order_p=p, direct_w=-1,
+                                direct_x=-1)
+        out = torch.empty((len(pos), 4, 13), dtype=torch.float64, device="cuda")
+        rp.rpy_laplace_far(t, cuda_tensor(q), out)
+        got = out.cpu().numpy()
+        lm = leaf_members(t)
+        leaves = rp.rpy_tree_export(t, "leaves")
+        ul = csr(t, "u_off", "u_idx")
+        ref = np.zeros(got.shape[:2])
+        for li, b in enumerate(leaves):
+            tg = lm[int(b)]
+            near = np.concatenate([lm[int(c)] for c in ul[li]])
+            far = np.setdiff1d(np.arange(len(pos)), near)
+            if len(far):
+                ref[tg] = oracle.laplace_direct(pos[far], q[far], pos[tg])[0]
+        errs.append(oracle.rel_l2(got[:, :, 0], ref))
+        H = got[:, :, 4:13].reshape(len(pos), 4, 3, 3)
+        assert np.abs(np.trace(H, axis1=2, axis2=3)).max() <= 1e-9 * np.abs(H).max(), p
+        t.close()
+    for e0, e1 in zip(errs, errs[1:]):
+        assert e1 <= e0 / 3, errs
