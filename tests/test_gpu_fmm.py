@@ -511,3 +511,40 @@ def test_laplace_far_field_error_decays_with_order_and_hessian_is_traceless():
         t.close()
     for e0, e1 in zip(errs, errs[1:]):
         assert e1 <= e0 / 3, errs
+
+
+def test_fmm_operator_is_reciprocal():
+    """D is symmetric (Sec. 1, D_ij = D_ji^T): for the FMM matvec at 6 digits,
+    |v.(D w) - w.(D v)| <= 1e-6 |v| |D w|."""
+    import torch
+    sysm = synth.sphere_plus_cube(30000, 91, 2e-4)
+    rng = np.random.default_rng(92)
+    v, w = rng.standard_normal((sysm.n, 3)), rng.standard_normal((sysm.n, 3))
+    t = rp.rpy_tree_build(cuda_tensor(sysm.pos), sysm.n, sysm.a, 6)
+    Dv, Dw = torch.empty((sysm.n, 3), dtype=torch.float64, device="cuda"), torch.empty(
+        (sysm.n, 3), dtype=torch.float64, device="cuda")
+    rp.rpy_matvec(t, cuda_tensor(v), sysm.s, Dv)
+    rp.rpy_matvec(t, cuda_tensor(w), sysm.s, Dw)
+    torch.cuda.synchronize()
+    dv, dw = Dv.cpu().numpy(), Dw.cpu().numpy()
+    lhs = abs(float(np.sum(v * dw)) - float(np.sum(w * dv)))
+    assert lhs <= 1e-6 * np.linalg.norm(v) * np.linalg.norm(dw), lhs
+
+
+@pytest.mark.parametrize("digits,tol", [(3, 2e-3), (6, 2e-6)])
+def test_rotation_equivariance(digits, tol):
+    """u(Q r, Q F) = Q u(r, F) for a rotation Q about the system's centre: the tree,
+    the lists and the plane-wave directions all change, the velocity may not
+    (beyond the digit setting)."""
+    sysm = synth.sphere_plus_cube(20000, 93, 2e-4)
+    rng = np.random.default_rng(94)
+    A = rng.standard_normal((3, 3))
+    Q, _ = np.linalg.qr(A)
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] = -Q[:, 0]
+    c = np.full(3, 0.5)
+    pos2 = (sysm.pos - c) @ Q.T + c
+    f2 = sysm.f @ Q.T
+    u1, _ = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, digits)
+    u2, _ = matvec(pos2, f2, sysm.a, sysm.s, digits)
+    assert oracle.rel_l2(u2, u1 @ Q.T) <= tol
