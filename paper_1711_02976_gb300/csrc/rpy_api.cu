@@ -852,7 +852,10 @@ int rpy_tree_footprint(int64_t n, int digits, int precision, int leaf_cap, int64
     // boxes: leaves ~ 2n/cap on clustered data, plus internal boxes (< leaves/7 * 8)
     double nbox = 4.0 * double(n) / double(leaf_cap) + 64.0;
     const int xf = plane_wave_frames(nbox, es, q.half());
-    double per_box = es * (2.0 * kSets * ncoef(p) + 2.0 * 2 * xf * kSets * q.half() + 18.0 * ncoef(p)) +
+    // M, L, plane waves, L2P scratch, and (rotation-based M2M) a per-octant share
+    // slot for the boxes of one level, counted here for every box
+    const double m2m = (precision != RPY_FP32 || p >= 12) ? 8.0 * kSets * ncoef(p) : 0.0;
+    double per_box = es * (2.0 * kSets * ncoef(p) + 2.0 * 2 * xf * kSets * q.half() + 18.0 * ncoef(p) + m2m) +
                      4.0 * (8 + 27 + 3 + 12) + 32.0;
     double per_bead = 3 * 8 /*pos*/ + 8 /*key*/ + 4 + 4 + 9 * 8 /*fs, unear, ufar*/ + 27 * 4 /*U list share*/ +
                       (precision == RPY_FP32 ? 9 * 4 /*p32, f32*/ : 0);
