@@ -548,3 +548,26 @@ def test_rotation_equivariance(digits, tol):
     u1, _ = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, digits)
     u2, _ = matvec(pos2, f2, sysm.a, sysm.s, digits)
     assert oracle.rel_l2(u2, u1 @ Q.T) <= tol
+
+
+def test_fp32_precision_form_6digit():
+    """The FP32 form at the 6-digit setting (default p = 18: rotation-based M2M and
+    L2L, FP32 plane waves) meets rel-L2 <= 1e-6 against the oracle, also as a forest."""
+    sysm = synth.sphere_plus_cube(20000, 95, 2e-4)
+    tg = synth.sample_targets(sysm.n, 800)
+    _check(sysm.pos, sysm.f, sysm.a, sysm.s, 6, 1e-6, targets=tg, precision=rp.RPY_FP32)
+    import torch
+    b = synth.uniform_cube(8000, seed=96, a=0.002)
+    pos = np.concatenate([sysm.pos, b.pos])
+    f = np.concatenate([sysm.f, b.f])
+    t = rp.rpy_forest_build(cuda_tensor(pos), [0, sysm.n, sysm.n + b.n], [sysm.a, b.a], 6,
+                            precision=rp.RPY_FP32)
+    U = torch.empty((len(pos), 3), dtype=torch.float64, device="cuda")
+    rp.rpy_forest_matvec(t, cuda_tensor(f), [sysm.s, b.s], U)
+    rp.rpy_tree_sync(t)
+    u = U.cpu().numpy()
+    ra = oracle.rpy_direct(sysm.pos, sysm.f, sysm.a, sysm.s, targets=tg)
+    tb = synth.sample_targets(b.n, 400)
+    rb = oracle.rpy_direct(b.pos, b.f, b.a, b.s, targets=tb)
+    assert oracle.rel_l2(u[tg], ra) <= 1e-6
+    assert oracle.rel_l2(u[sysm.n + tb], rb) <= 1e-6
