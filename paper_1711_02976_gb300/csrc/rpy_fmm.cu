@@ -7,7 +7,8 @@
 //
 // Kernels, in launch order:
 //   k_p2m      S->M   leaves: M_n^m = sum_j q_j conj(y_n^m(eta_j))
-//   k_m2m_rot  M->M   rotate to the child's shift axis, z-shift, rotate back
+//   k_m2m_child, k_m2m_sum  M->M   per child: rotate to the shift axis, z-shift, rotate back;
+//                      per parent: add the children's shares in octant order
 //   k_m2x      M->I   rotate into the frame of each axis, outgoing plane waves
 //                     W_kj = (w_k/M_k) sum_{n,m} M_n^m i^|m| lambda_k^n e^{i m a_kj} / sqrt((n-|m|)!(n+|m|)!)
 //   k_x2x      I->I   merge-and-shift: per parent and direction, sources are
@@ -422,69 +423,15 @@ __device__ void rotate_sets_f(const T *rf, const int *foff, int p, const cpx<T> 
     }
 }
 
-template <typename T>
-__device__ void rotate_sets(const T *rot, const int *roff, int p, const cpx<T> *src, cpx<T> *dst) {
-    const int nc = ncoef(p);
-    int tot = kSets * 2 * nc;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        int s = e / (2 * nc), r = e - s * 2 * nc;
-        int n = deg_of(r >> 1);
-        int B = 2 * (n + 1);
-        int lo = r - 2 * tri(n, 0);
-        const T *row = rot + roff[n] + lo * B;
-        const T *in = reinterpret_cast<const T *>(src + s * nc) + 2 * tri(n, 0);
-        T a = 0;
-        for (int c = 0; c < B; ++c) a += row[c] * in[c];
-        reinterpret_cast<T *>(dst + s * nc)[r] = a;
-    }
-}
-
 // ---------------------------------------------------------------- rotation-based M2M / L2L
 // Child octant o: rotate into the frame whose z axis is the shift direction,
 // apply the m-diagonal z-shift, rotate back (O(p^3) per child instead of the
 // O(p^4) dense operator).
-template <typename T>
-__global__ void k_m2m_rot(int b0, int nb, DevTables<T> D, const int *leaf, const int *child, cpx<T> *M) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    int b = b0 + blockIdx.x;
-    if (leaf[b]) return;
-    const int p = D.p, nc = ncoef(p), P1 = p + 1;
-    cpx<T> *X = reinterpret_cast<cpx<T> *>(smem_raw);
-    cpx<T> *Y = X + kSets * nc;
-    cpx<T> *acc = Y + kSets * nc;
-    cpx<T> *Tm = acc + kSets * nc;   // rotation scratch
-    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) acc[i] = mk<T>(0, 0);
-    for (int o = 0; o < 8; ++o) {
-        int c = child[8 * b + o];
-        if (c < 0) continue;
-        __syncthreads();
-        const cpx<T> *src = M + size_t(c) * kSets * nc;
-        for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) X[i] = src[i];
-        __syncthreads();
-        rotate_sets_f(D.forot_fwd + size_t(o) * D.frot_len, D.frot_off, p, X, Tm, Y);
-        __syncthreads();
-        for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
-            int st = e / nc, i = e - st * nc;
-            int n = deg_of(i), m = i - tri(n, 0);
-            const T *z = D.zm2m + size_t(i) * P1;
-            cpx<T> a = mk<T>(0, 0);
-            for (int k = m; k <= n; ++k) a += z[k] * Y[st * nc + tri(k, m)];
-            X[e] = a;
-        }
-        __syncthreads();
-        rotate_sets_f(D.forot_bwd + size_t(o) * D.frot_len, D.frot_off, p, X, Tm, Y);
-        __syncthreads();
-        for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) acc[i] += Y[i];
-    }
-    __syncthreads();
-    cpx<T> *dst = M + size_t(b) * kSets * nc;
-    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) dst[i] = acc[i];
-}
-
-// One child per block (the children of one level): rotate, z-shift and rotate
-// back as k_m2m_rot, then write the child's share to its slot Sc[parent][octant];
-// k_m2m_sum adds the slots of each parent in octant order, so that the result
-// is the same, bit for bit, as k_m2m_rot's eight children in sequence.
+// One child per block (the children of one level): rotate into the frame
+// whose z axis is the shift direction, apply the m-diagonal z-shift, rotate back
+// (O(p^3) per child instead of the O(p^4) dense operator), and write the
+// child's share to its slot Sc[parent][octant]; k_m2m_sum adds the slots of each
+// parent in octant order (a fixed order: the result does not depend on timing).
 template <typename T>
 __global__ void k_m2m_child(int c0, int pb0, DevTables<T> D, const int *par, const int *cell, const cpx<T> *M,
                             cpx<T> *Sc) {
@@ -1450,11 +1397,10 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     prof_mark(t, RPY_STAGE_M2M, st);
     // FP64: rotation-based M2M and L2L (fewer FP64 operations).  FP32: the dense
     // operators below p = 12, the rotation forms (one child per block) from there
-    const bool rot = sizeof(T) == 8, rot_l = rot || p >= 12;
-    size_t smr3 = sizeof(cpx<T>) * 4 * kSets * nc, smr2 = sizeof(cpx<T>) * 3 * kSets * nc;
+    const bool rot_l = sizeof(T) == 8 || p >= 12;
+    size_t smr2 = sizeof(cpx<T>) * 3 * kSets * nc;
     int Dd = 2 * nc, thr = ((Dd + 31) / 32) * 32;
     size_t smd = sizeof(T) * kSets * Dd;
-    RPY_TRY(set_smem(k_m2m_rot<T>, smr3));
     RPY_TRY(set_smem(k_l2l_rot<T>, smr2));
     RPY_TRY(set_smem(k_m2m_child<T>, smr2));
     RPY_TRY(set_smem(k_m2m<T>, smd));
@@ -1463,14 +1409,17 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
         int lb = t.level_off[l], ln = t.level_off[l + 1] - lb;
         if (ln > 0) {
             const int cb = t.level_off[l + 1], cn = t.level_off[l + 2] - cb;   // their children
-            if (rot_l && t.m2m_scratch && cn > 0) {
-                cpx<T> *Sc = static_cast<cpx<T> *>(t.m2m_scratch);
-                k_m2m_child<T><<<cn, 256, smr2, st>>>(cb, lb, D, t.b_parent, t.b_cell, M, Sc);
-                k_m2m_sum<T><<<ln, 256, 0, st>>>(lb, kSets * nc, t.b_leaf, t.b_child, Sc, M);
-                RPY_LAUNCHED(2);
+            if (rot_l) {
+                // the share slots exist whenever a level >= 2 does (tree_alloc_workspace)
+                if (cn > 0) {
+                    if (!t.m2m_scratch) return RPY_ERR_INTERNAL;
+                    cpx<T> *Sc = static_cast<cpx<T> *>(t.m2m_scratch);
+                    k_m2m_child<T><<<cn, 256, smr2, st>>>(cb, lb, D, t.b_parent, t.b_cell, M, Sc);
+                    k_m2m_sum<T><<<ln, 256, 0, st>>>(lb, kSets * nc, t.b_leaf, t.b_child, Sc, M);
+                    RPY_LAUNCHED(2);
+                }
             } else {
-                if (rot) k_m2m_rot<T><<<ln, 256, smr3, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
-                else k_m2m<T><<<ln, thr, smd, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
+                k_m2m<T><<<ln, thr, smd, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
                 RPY_LAUNCHED(1);
             }
         }
