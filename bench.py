@@ -44,6 +44,18 @@ CONFIGS = {
     "sphere1m_9digit_fp64": dict(gen="config2", digits=9, precision=0, leaf_cap=0,
                                  desc="1,000,000 beads: sphere surface r=0.5 + 10% uniform cube, a=1e-4, "
                                       "9-digit, FP64 (the paper's third accuracy setting)"),
+    # the paper's other timed workloads (Sec. 4.3, 512 Cray XC30 nodes): 15M cube at 6 and 9
+    # digits, 8M sphere surface at 3, 6 and 9 digits (Mbeads/s = N / time)
+    "cube15m_6digit_fp64": dict(gen="config3", digits=6, precision=0, leaf_cap=0, paper_mbeads_s=15.787,
+                                desc="15,000,000 beads uniform cube, a=2e-5, 6-digit, FP64"),
+    "cube15m_9digit_fp64": dict(gen="config3", digits=9, precision=0, leaf_cap=0, paper_mbeads_s=12.185,
+                                desc="15,000,000 beads uniform cube, a=2e-5, 9-digit, FP64"),
+    "sphere8m_3digit_fp64": dict(gen="sphere8m", digits=3, precision=0, leaf_cap=0, paper_mbeads_s=18.448,
+                                 desc="8,000,000 beads uniform on a sphere surface, a=1e-4, 3-digit, FP64"),
+    "sphere8m_6digit_fp64": dict(gen="sphere8m", digits=6, precision=0, leaf_cap=0, paper_mbeads_s=5.310,
+                                 desc="8,000,000 beads uniform on a sphere surface, a=1e-4, 6-digit, FP64"),
+    "sphere8m_9digit_fp64": dict(gen="sphere8m", digits=9, precision=0, leaf_cap=0, paper_mbeads_s=1.912,
+                                 desc="8,000,000 beads uniform on a sphere surface, a=1e-4, 9-digit, FP64"),
     "cube4096_3digit_fp64": dict(gen="config1", digits=3, precision=0, leaf_cap=40,
                                  desc="4,096 beads uniform cube, a=0.004, 3-digit, FP64, leaf cap 40"),
     "cube15m_3digit_fp32": dict(gen="config3", digits=3, precision=1, leaf_cap=0,
@@ -611,7 +623,7 @@ def main():
         err_far = oracle.rel_l2(u_dev[tg] - selft, ref - selft)
         result["rel_l2"] = err
         result["rel_l2_far"] = err_far
-        if not args.no_forms and CONFIGS[args.config]["precision"] == 0:
+        if not args.no_forms and CONFIGS[args.config]["precision"] == 0 and CONFIGS[args.config]["digits"] != 9:
             pf, psys, pu = precision_form(args, local, args.config)
             result["precision_form"] = {
                 "value": pf["value"], "unit": "Mbeads/s", "ms_per_step": pf["ms_per_step"],

@@ -340,8 +340,8 @@ int tree_alloc_workspace(Tree &t, cudaStream_t) {
     RPY_TRY(dev_alloc(t, &t.Xi, es * nb * 2 * t.x_frames * kSets * h.S));
     RPY_TRY(dev_alloc(t, &t.EVg, es * size_t(t.nleaf) * 18 * h.nc));
     if (t.params.precision != RPY_FP32 || h.p >= 12) {   // rotation-based M2M (see run_far_t)
-        size_t wide = 0;
-        for (int l = 2; l + 1 < int(t.level_off.size()); ++l)
+        size_t wide = 0;   // the widest parent level of the M2M pass (levels 2 .. nlevels - 2)
+        for (int l = 2; l <= t.nlevels - 2; ++l)
             wide = std::max(wide, size_t(t.level_off[l + 1] - t.level_off[l]));
         if (wide > 0) RPY_TRY(dev_alloc(t, &t.m2m_scratch, es * wide * 8 * kSets * h.nc));
     }

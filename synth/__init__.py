@@ -92,6 +92,12 @@ def config3(n: int = 15_000_000) -> BeadSystem:
     return uniform_cube(n, 3, 2e-5)
 
 
+def sphere8m(n: int = 8_000_000) -> BeadSystem:
+    """N=8,000,000 uniform on the sphere of radius 0.5 centred in the unit cube
+    (the paper's sphere workload), seed 6, a=1e-4."""
+    return sphere_plus_cube(n, 6, 1e-4, frac_cube=0.0)
+
+
 def config4(nsys: int = 256, seed: int = 4, lo: float = 1e3, hi: float = 2e5):
     """Many independent systems of log-uniform size, each a uniform cube or a
     Plummer-like cluster (coin flip), a_s = 0.5 / N_s^(1/3)."""
