@@ -71,6 +71,9 @@ CONFIGS = {
     "sphere200k_6digit_fp32": dict(gen="sphere200k", digits=6, precision=1, leaf_cap=0,
                                    desc="200,000 beads: sphere surface + 10% cube (seed 2), a=1e-4, 6-digit, FP32 "
                                         "precision form (small case for ncu captures)"),
+    "cube2m_3digit_fp32": dict(gen="cube2m", digits=3, precision=1, leaf_cap=0,
+                               desc="2,000,000 beads uniform cube (seed 3), a=2e-5, 3-digit, FP32 precision form "
+                                    "(small case of the 15M cube's near field for ncu captures: ~60 beads per leaf)"),
     "batch24_3digit_fp32": dict(gen="config4_24", digits=3, precision=1, leaf_cap=0,
                                 desc="24 systems in one forest drawn like the 256-system batch (seed 4), 3-digit, "
                                      "FP32 precision form (small case for ncu captures)"),
@@ -172,6 +175,8 @@ def make_workload(name):
         return synth.sphere_plus_cube(200000, 2, 1e-4)
     if gen == "config4_24":
         return Forest(synth.config4(nsys=24))
+    if gen == "cube2m":
+        return synth.uniform_cube(2000000, 3, 2e-5)
     w = getattr(synth, gen)()
     return Forest(w) if isinstance(w, list) else w
 
