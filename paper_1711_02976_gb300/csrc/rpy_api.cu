@@ -78,7 +78,7 @@ __global__ void k_combine(const int *perm, int64_t n, const double *un, const do
     for (int a = 0; a < 3; ++a) {
         double v = 0.0;
         if (parts & RPY_PART_NEAR) v += un[3 * i + a];
-        if (parts & RPY_PART_FAR) v += uf[3 * i + a] + ud[3 * i + a];
+        if (parts & RPY_PART_FAR) v += uf[3 * i + a] + (ud ? ud[3 * i + a] : 0.0);
         u[3 * j + a] = v;
     }
 }
@@ -404,8 +404,13 @@ static int matvec_body(Tree &t, const SysConst &sc, int parts, cudaStream_t st, 
         sp = t.side_stream;
     }
     prof_mark(t, RPY_STAGE_P2P, st);
-    if (parts & RPY_PART_NEAR) RPY_TRY(run_p2p(t, t.fs, t.u_near, sc, sp, false));
-    if (parts & RPY_PART_FAR) RPY_TRY(run_p2p(t, t.fs, t.u_dir, sc, sp, true));
+    if (parts == RPY_PART_ALL) {
+        // one pass over each leaf's U list and direct substitutes (u_dir stays zero)
+        RPY_TRY(run_p2p(t, t.fs, t.u_near, sc, sp, kListM));
+    } else {
+        if (parts & RPY_PART_NEAR) RPY_TRY(run_p2p(t, t.fs, t.u_near, sc, sp, kListU));
+        if (parts & RPY_PART_FAR) RPY_TRY(run_p2p(t, t.fs, t.u_dir, sc, sp, kListD));
+    }
     prof_mark(t, RPY_STAGE_P2M, st);
     if (parts & RPY_PART_FAR) {
         if (t.params.precision == RPY_FP32)
@@ -468,7 +473,9 @@ int run_matvec(Tree &t, const double *f_dev, const double *s_host, double *u_dev
         RPY_TRY(matvec_body(t, sc, parts, st));
     }
     prof_mark(t, RPY_STAGE_COMBINE, st);
-    k_combine<<<nb256(t.n), 256, 0, st>>>(t.perm, t.n, t.u_near, t.u_far, t.u_dir, parts, u_dev);
+    // the full matvec summed the direct substitutes into u_near
+    k_combine<<<nb256(t.n), 256, 0, st>>>(t.perm, t.n, t.u_near, t.u_far, parts == RPY_PART_ALL ? nullptr : t.u_dir,
+                                          parts, u_dev);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     prof_mark(t, RPY_NUM_STAGES, st);

@@ -232,6 +232,10 @@ struct Tree {
     // decreasing cost order for the U-list pass and for the direct-substitute pass
     int n_items = 0;
     int2 *u_items = nullptr, *d_items = nullptr;
+    // the near list of the full matvec: per leaf the U list, then the direct substitutes;
+    // its work items in decreasing cost order (one pass for both)
+    int *m_off = nullptr, *m_idx = nullptr;
+    int2 *m_items = nullptr;
     int64_t n_d = 0, d_pairs = 0;
     int direct_w = 0, direct_x = 0;    // bead-count thresholds in use (0 = none)
     // expansions and matvec workspace
@@ -310,7 +314,8 @@ __device__ __forceinline__ double pow2i(int l) { return __hiloint2double((1023 +
 template <typename T>
 int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *lapq, double *ufar, double *lapout,
               const SysConst &sc, cudaStream_t st);
-int run_p2p(Tree &t, const double *fs, double *out, const SysConst &sc, cudaStream_t st, bool direct_list);
+constexpr int kListU = 0, kListD = 1, kListM = 2;   // near list: U, direct substitutes, both
+int run_p2p(Tree &t, const double *fs, double *out, const SysConst &sc, cudaStream_t st, int list);
 int split_positions_f32(Tree &t, cudaStream_t st);
 // the tree of a valid handle, else nullptr
 Tree *tree_of(rpy_tree h);

@@ -498,13 +498,14 @@ static cudaError_t set_p2p32_smem() {
     return e;
 }
 
-// U lists (near field, self term added) or the direct substitutes of small
-// W / X interactions (no self term).
-int run_p2p(Tree &t, const double *fs, double *out, const SysConst &sc, cudaStream_t st, bool direct_list) {
-    const int *off = direct_list ? t.d_off : t.u_off;
-    const int *idx = direct_list ? t.d_idx : t.u_idx;
+// U lists (near field, self term added), the direct substitutes of small
+// W / X interactions (no self term), or both in one pass (the full matvec).
+int run_p2p(Tree &t, const double *fs, double *out, const SysConst &sc, cudaStream_t st, int list) {
+    const bool direct_list = list == kListD, merged = list == kListM;
+    const int *off = merged ? t.m_off : (direct_list ? t.d_off : t.u_off);
+    const int *idx = merged ? t.m_idx : (direct_list ? t.d_idx : t.u_idx);
     int add_self = direct_list ? 0 : 1;
-    const int2 *items = direct_list ? t.d_items : t.u_items;
+    const int2 *items = merged ? t.m_items : (direct_list ? t.d_items : t.u_items);
     if (t.n_items == 0) return RPY_OK;
     if (t.params.precision == RPY_FP32) {
         RPY_CHECK(set_p2p32_smem());

@@ -747,7 +747,7 @@ __device__ __forceinline__ uint64_t cost_key(unsigned long long c) {
 
 __global__ void k_item_fill(int nleaf, const int *leaves, const int *beg, const int *end, const int *uoff,
                             const int *uidx, const int *doff, const int *didx, const int *ioff, int2 *items,
-                            uint64_t *ku, uint32_t *vu, uint64_t *kd, uint32_t *vd) {
+                            uint64_t *ku, uint32_t *vu, uint64_t *kd, uint32_t *vd, uint64_t *km, uint32_t *vm) {
     int li = blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= nleaf) return;
     int b = leaves[li];
@@ -762,15 +762,32 @@ __global__ void k_item_fill(int nleaf, const int *leaves, const int *beg, const 
         vu[it] = uint32_t(it);
         kd[it] = cost_key(sd * tc);
         vd[it] = uint32_t(it);
+        km[it] = cost_key((su + sd) * tc);
+        vm[it] = uint32_t(it);
     }
 }
 
-__global__ void k_item_order(int n, const int2 *items, const uint32_t *ou, const uint32_t *od, int2 *u_items,
-                             int2 *d_items) {
+__global__ void k_item_order(int n, const int2 *items, const uint32_t *ou, const uint32_t *od, const uint32_t *om,
+                             int2 *u_items, int2 *d_items, int2 *m_items) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     u_items[i] = items[ou[i]];
     d_items[i] = items[od[i]];
+    m_items[i] = items[om[i]];
+}
+
+// The near list of the full matvec: per leaf its U list followed by its direct
+// substitutes (m_off = u_off + d_off, both exclusive prefix sums over leaves).
+__global__ void k_merge_lists(int nleaf, const int *uoff, const int *uidx, const int *doff, const int *didx,
+                              int *moff, int *midx) {
+    int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li > nleaf) return;
+    const int m0 = uoff[li] + doff[li];
+    moff[li] = m0;
+    if (li == nleaf) return;
+    int q = m0;
+    for (int k = uoff[li]; k < uoff[li + 1]; ++k) midx[q++] = uidx[k];
+    for (int k = doff[li]; k < doff[li + 1]; ++k) midx[q++] = didx[k];
 }
 
 // ---------------------------------------------------------------- build driver
@@ -1014,6 +1031,12 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
                                                      wdoff, wdidx, xdoff, xdidx, nullptr, t.d_off, t.d_idx);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
+    RPY_TRY(dev_alloc(t, (void **)&t.m_off, sizeof(int) * (nleaf + 1)));
+    RPY_TRY(dev_alloc(t, (void **)&t.m_idx, sizeof(int) * std::max(int(t.n_u) + nd, 1)));
+    k_merge_lists<<<nblk(nleaf + 1, 128), 128, 0, st>>>(nleaf, t.u_off, t.u_idx, t.d_off, t.d_idx, t.m_off,
+                                                         t.m_idx);
+    RPY_LAUNCHED(1);
+    RPY_CHECK(cudaGetLastError());
     // -- statistics
     unsigned long long *d_pairs;
     int *d_max;
@@ -1046,28 +1069,32 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
         RPY_TRY(exclusive_scan_i32(icnt, ioff, nleaf + 1, &ni, stmp, sbytes, st));
         t.n_items = ni;
         int2 *items;
-        uint64_t *ku, *kd, *kt;
-        uint32_t *vu, *vd, *vt;
+        uint64_t *ku, *kd, *km, *kt;
+        uint32_t *vu, *vd, *vm, *vt;
         int *icounts;
         const int itiles = nblk(std::max(ni, 1), kSortTile);
         RPY_TRY(dev_alloc(scratch, (void **)&items, sizeof(int2) * std::max(ni, 1)));
         RPY_TRY(dev_alloc(scratch, (void **)&ku, sizeof(uint64_t) * std::max(ni, 1)));
         RPY_TRY(dev_alloc(scratch, (void **)&kd, sizeof(uint64_t) * std::max(ni, 1)));
+        RPY_TRY(dev_alloc(scratch, (void **)&km, sizeof(uint64_t) * std::max(ni, 1)));
         RPY_TRY(dev_alloc(scratch, (void **)&kt, sizeof(uint64_t) * std::max(ni, 1)));
         RPY_TRY(dev_alloc(scratch, (void **)&vu, sizeof(uint32_t) * std::max(ni, 1)));
         RPY_TRY(dev_alloc(scratch, (void **)&vd, sizeof(uint32_t) * std::max(ni, 1)));
+        RPY_TRY(dev_alloc(scratch, (void **)&vm, sizeof(uint32_t) * std::max(ni, 1)));
         RPY_TRY(dev_alloc(scratch, (void **)&vt, sizeof(uint32_t) * std::max(ni, 1)));
         RPY_TRY(dev_alloc(scratch, (void **)&icounts, sizeof(int) * 256 * size_t(itiles)));
         if (scan_tmp_bytes(256 * itiles) > sbytes) return RPY_ERR_INTERNAL;
         RPY_TRY(dev_alloc(t, (void **)&t.u_items, sizeof(int2) * std::max(ni, 1)));
         RPY_TRY(dev_alloc(t, (void **)&t.d_items, sizeof(int2) * std::max(ni, 1)));
+        RPY_TRY(dev_alloc(t, (void **)&t.m_items, sizeof(int2) * std::max(ni, 1)));
         if (ni > 0) {
             k_item_fill<<<nblk(nleaf, 256), 256, 0, st>>>(nleaf, t.leaves, t.b_begin, t.b_end, t.u_off, t.u_idx,
-                                                          t.d_off, t.d_idx, ioff, items, ku, vu, kd, vd);
+                                                          t.d_off, t.d_idx, ioff, items, ku, vu, kd, vd, km, vm);
             RPY_LAUNCHED(1);
             RPY_TRY(radix_sort(ku, vu, kt, vt, ni, 8, icounts, stmp, sbytes, st));
             RPY_TRY(radix_sort(kd, vd, kt, vt, ni, 8, icounts, stmp, sbytes, st));
-            k_item_order<<<nblk(ni, 256), 256, 0, st>>>(ni, items, vu, vd, t.u_items, t.d_items);
+            RPY_TRY(radix_sort(km, vm, kt, vt, ni, 8, icounts, stmp, sbytes, st));
+            k_item_order<<<nblk(ni, 256), 256, 0, st>>>(ni, items, vu, vd, vm, t.u_items, t.d_items, t.m_items);
             RPY_LAUNCHED(1);
             RPY_CHECK(cudaGetLastError());
         }
