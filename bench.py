@@ -332,7 +332,7 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
 # DRAM bytes per bead of one FP64 U-list P2P launch, from the ncu capture of the
 # 200k-bead sphere case (profiles/k_p2p_fp64_sphere200k.md: 10,256,896 B); the
 # traffic is the sources' positions and forces, so it grows with the bead count.
-P2P64_DRAM_BYTES_PER_BEAD = 10256896.0 / 200000.0
+P2P64_DRAM_BYTES_PER_BEAD = 10747648.0 / 200000.0   # merged U + direct pass, 200k-bead ncu capture
 
 
 def roofline(result, stats, stage_ms, peaks):
@@ -347,7 +347,7 @@ def roofline(result, stats, stage_ms, peaks):
             traffic = round(P2P64_DRAM_BYTES_PER_BEAD * stats["n_beads"])
         return {"kernel": top, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak / 1e12, 4),
                 "unit": "TFLOP/s", "frac": round(ach / (peak / 1e12), 4), "traffic": traffic,
-                "traffic_note": "DRAM bytes of the U-list launch, scaled by bead count from a 200k-bead ncu capture"
+                "traffic_note": "DRAM bytes of the near-field launch (U lists and direct substitutes), scaled by bead count from a 200k-bead ncu capture"
                 if traffic else None,
                 "fp64_pipe_utilisation_ncu": 0.910 if (top == "p2p" and prec == "fp64") else None,
                 "peak_source": "measured FMA-chain probe on this GPU (rpy_alu_peak)"}
