@@ -82,7 +82,17 @@ typedef struct {
                          bit 2 (RPY_FLAG_EVAL_PER_POTENTIAL): evaluate Eq. (2.8) at the beads
                          per Laplace potential (approach 1 of Sec. 2: 12 expansions per
                          bead) instead of one expansion per velocity component (approach 2,
-                         the default: 6 expansions per bead); other bits must be 0 */
+                         the default: 6 expansions per bead);
+                         bit 3 (RPY_FLAG_BOX_ORIGIN) / bit 4 (RPY_FLAG_CUBE_ORIGIN): where the
+                         fourth charge set q4 = F . (r - o) of Sec. 2 takes its origin o.  Box
+                         origin: every expansion carries q4 about its own box centre, moved
+                         along with each translation (M2M, X2X, L2L), so its values stay of
+                         the size of the box's own moments; cube origin: one origin per system
+                         (the bounding-cube centre), which leaves the far-field combination
+                         grad L4 - sum_k x_k grad L_k of Eq. (2.8) to cancel terms of size
+                         |x - o| |grad L|.  Default: box origin for RPY_FP32, cube origin for
+                         RPY_FP64 (whose rounding does not need it); at most one of the two
+                         bits; other bits must be 0 */
     int direct_w;     /* W-list boxes with at most this many beads are summed directly
                          instead of by multipole evaluation: 0 = automatic
                          (about 1.8 (p+3)(p+4)/2), -1 = never */
@@ -96,7 +106,8 @@ typedef struct {
                          464, 1168 stored plane waves per direction) */
 } rpy_build_params;
 
-enum { RPY_FLAG_NO_GRAPH = 1, RPY_FLAG_FRAME_PASSES = 2, RPY_FLAG_EVAL_PER_POTENTIAL = 4 };
+enum { RPY_FLAG_NO_GRAPH = 1, RPY_FLAG_FRAME_PASSES = 2, RPY_FLAG_EVAL_PER_POTENTIAL = 4, RPY_FLAG_BOX_ORIGIN = 8,
+       RPY_FLAG_CUBE_ORIGIN = 16 };
 
 /* Statistics of a built tree (host struct filled by rpy_tree_stats). */
 typedef struct {
@@ -399,6 +410,9 @@ typedef struct {
     double tune_ms;          /* host wall time of the search */
     int n_trials;            /* entries of trials[] filled (the search stops recording at 48) */
     rpy_autotune_trial trials[48];
+    double verify_rel_l2;    /* error of the choice on the verification sample */
+    int n_verify;            /* targets of the verification sample */
+    int verify_ok;           /* 1 when verify_rel_l2 <= 0.5 x bound */
 } rpy_autotune_result;
 
 /*
@@ -414,7 +428,16 @@ typedef struct {
  *      meets the goal, the one of least error;
  *   3. leaf capacity in {0.5, 0.7, 1, 1.4, 2} x default, then the thresholds
  *      {never, half, automatic, double}: the fastest median matvec (CUDA events
- *      on `stream`) among candidates that keep the error within the goal.
+ *      on `stream`) among candidates that keep the error within the goal;
+ *   4. verification: the choice against an independent FP64 direct sum on four
+ *      times n_samples fresh targets, half uniform over all beads and half over
+ *      the beads of the tree's two deepest leaf levels (where the translation
+ *      chains are longest).  It must reach 0.5 x bound.  Otherwise, for RPY_FP32,
+ *      the FP64 path at the same parameters is verified and taken when it passes
+ *      (the excess was FP32 rounding, which a higher order cannot remove), and
+ *      the order is raised by one while neither passes (at most four times).
+ *      out->best.precision is then RPY_FP64 although RPY_FP32 was asked for; the
+ *      caller sees the change there and in verify_rel_l2 / verify_ok.
  * Builds and frees one tree per candidate; allocates device scratch of
  * N x 3 doubles.  Synchronises `stream`.  Arguments as for rpy_forest_build and
  * rpy_forest_matvec; params may be NULL (all defaults).

@@ -26,12 +26,13 @@ __all__ = [
     "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt",
     "rpy_bd_step", "rpy_evaluate", "rpy_matvec_batched", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
     "RPY_PART_ALL", "RPY_FLAG_NO_GRAPH", "RPY_FLAG_FRAME_PASSES",
-    "RPY_FLAG_EVAL_PER_POTENTIAL", "EXPORTED_SYMBOLS",
+    "RPY_FLAG_EVAL_PER_POTENTIAL", "RPY_FLAG_BOX_ORIGIN", "RPY_FLAG_CUBE_ORIGIN", "EXPORTED_SYMBOLS",
 ]
 
 RPY_FP64, RPY_FP32 = 0, 1
 RPY_PART_NEAR, RPY_PART_FAR, RPY_PART_ALL = 1, 2, 3
 RPY_FLAG_NO_GRAPH, RPY_FLAG_FRAME_PASSES, RPY_FLAG_EVAL_PER_POTENTIAL = 1, 2, 4
+RPY_FLAG_BOX_ORIGIN, RPY_FLAG_CUBE_ORIGIN = 8, 16
 FIELDS = {
     "perm": (1, np.int32), "keys": (2, np.uint64), "box_level": (3, np.int32), "box_range": (4, np.int32),
     "box_parent": (5, np.int32), "box_center": (6, np.float64), "box_leaf": (7, np.int32),
@@ -97,7 +98,8 @@ class AutotuneTrial(ctypes.Structure):
 class AutotuneResult(ctypes.Structure):
     _fields_ = [("best", BuildParams), ("est_rel_l2", ctypes.c_double), ("matvec_ms", ctypes.c_double),
                 ("goal", ctypes.c_double), ("tune_ms", ctypes.c_double), ("n_trials", ctypes.c_int),
-                ("trials", AutotuneTrial * 48)]
+                ("trials", AutotuneTrial * 48), ("verify_rel_l2", ctypes.c_double), ("n_verify", ctypes.c_int),
+                ("verify_ok", ctypes.c_int)]
 
 
 class ServerParams(ctypes.Structure):
@@ -310,6 +312,7 @@ def rpy_autotune(pos, sys_offsets, a, f, kT_over_eta, digits, precision=RPY_FP64
     return {
         "best": {k: getattr(b, k) for k, _ in BuildParams._fields_},
         "est_rel_l2": res.est_rel_l2, "matvec_ms": res.matvec_ms, "goal": res.goal, "tune_ms": res.tune_ms,
+        "verify_rel_l2": res.verify_rel_l2, "n_verify": res.n_verify, "verify_ok": bool(res.verify_ok),
         "trials": [{k: getattr(res.trials[i], k) for k, _ in AutotuneTrial._fields_} for i in range(res.n_trials)],
     }
 

@@ -520,7 +520,9 @@ static int check_params(const rpy_build_params &p) {
     if (p.precision != RPY_FP64 && p.precision != RPY_FP32) return RPY_ERR_INVALID;
     if (p.digits == 9 && p.precision != RPY_FP64) return RPY_ERR_DIGITS;   // beyond FP32 arithmetic
     if (p.leaf_cap < 0 || p.order_p < 0 || p.max_level < 0 || p.max_level > kMaxLevel ||
-        (p.flags & ~(RPY_FLAG_NO_GRAPH | RPY_FLAG_FRAME_PASSES | RPY_FLAG_EVAL_PER_POTENTIAL)) != 0)
+        (p.flags & ~(RPY_FLAG_NO_GRAPH | RPY_FLAG_FRAME_PASSES | RPY_FLAG_EVAL_PER_POTENTIAL |
+                     RPY_FLAG_BOX_ORIGIN | RPY_FLAG_CUBE_ORIGIN)) != 0 ||
+        ((p.flags & RPY_FLAG_BOX_ORIGIN) && (p.flags & RPY_FLAG_CUBE_ORIGIN)))
         return RPY_ERR_INVALID;
     if (p.order_p != 0 && (p.order_p < 2 || p.order_p > kMaxP)) return RPY_ERR_INVALID;
     if (p.direct_w < -1 || p.direct_x < -1) return RPY_ERR_INVALID;

@@ -227,26 +227,42 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     *out = rpy_autotune_result{};
 
-    // sampled targets (distinct, uniform over all beads)
     const int64_t N = sys_offsets[nsys];
+    Scratch sc;
+    double *u = nullptr;
+    RPY_CHECK(sc.alloc(&u, size_t(N) * 3));
+    // a sample of targets with its FP64 direct sum and the device buffers that gather
+    // the matvec's velocities there
+    struct Probe {
+        std::vector<int64_t> tg;
+        std::vector<double> ref, got;
+        double rn = 0.0;
+        int64_t *dt = nullptr;
+        double *ug = nullptr;
+    };
+    auto make_probe = [&](std::vector<int64_t> tgv, Probe &pr) -> int {
+        pr.tg = std::move(tgv);
+        const int64_t k = int64_t(pr.tg.size());
+        pr.ref.assign(3 * k, 0.0);
+        pr.got.assign(3 * k, 0.0);
+        Sampled S = describe(sys_offsets, nsys, a_host, kT_over_eta_host, pr.tg);
+        RPY_TRY(direct_sampled(pos_dev, f_dev, S, pr.ref.data(), st));
+        pr.rn = 0.0;
+        for (double v : pr.ref) pr.rn += v * v;
+        RPY_CHECK(sc.alloc(&pr.ug, size_t(k) * 3));
+        RPY_CHECK(sc.alloc(&pr.dt, size_t(k)));
+        RPY_CHECK(cudaMemcpyAsync(pr.dt, pr.tg.data(), sizeof(int64_t) * k, cudaMemcpyHostToDevice, st));
+        return RPY_OK;
+    };
+    // sampled targets of the search (distinct, uniform over all beads)
     const int64_t K = std::min<int64_t>(K0, N);
     uint64_t seed = P.seed ? P.seed : 0x5EEDF00Dull;
-    std::set<int64_t> pick;
-    while (int64_t(pick.size()) < K) pick.insert(int64_t(splitmix64(seed) % uint64_t(N)));
-    std::vector<int64_t> tg(pick.begin(), pick.end());
-    Sampled S = describe(sys_offsets, nsys, a_host, kT_over_eta_host, tg);
-    std::vector<double> ref(3 * K), got(3 * K);
-    RPY_TRY(direct_sampled(pos_dev, f_dev, S, ref.data(), st));
-    double rn = 0.0;
-    for (double v : ref) rn += v * v;
-
-    Scratch sc;
-    double *u = nullptr, *ug = nullptr;
-    int64_t *dt = nullptr;
-    RPY_CHECK(sc.alloc(&u, size_t(N) * 3));
-    RPY_CHECK(sc.alloc(&ug, size_t(K) * 3));
-    RPY_CHECK(sc.alloc(&dt, size_t(K)));
-    RPY_CHECK(cudaMemcpyAsync(dt, tg.data(), sizeof(int64_t) * K, cudaMemcpyHostToDevice, st));
+    Probe probe;
+    {
+        std::set<int64_t> pick;
+        while (int64_t(pick.size()) < K) pick.insert(int64_t(splitmix64(seed) % uint64_t(N)));
+        RPY_TRY(make_probe(std::vector<int64_t>(pick.begin(), pick.end()), probe));
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     RPY_CHECK(cudaEventCreate(&e0));
     RPY_CHECK(cudaEventCreate(&e1));
@@ -262,8 +278,9 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
     const double goal = margin * bound;
     std::vector<Trial> trials;
 
-    // one trial: build, one untimed matvec, the sampled error, optionally `reps` timed matvecs
-    auto run = [&](rpy_build_params prm, bool timed, Trial &T) -> int {
+    // one trial: build, one untimed matvec, the sampled error on `pr`, optionally `reps`
+    // timed matvecs
+    auto run = [&](rpy_build_params prm, bool timed, Trial &T, Probe &pr) -> int {
         T.prm = prm;
         rpy_tree tree = nullptr;
         int r = rpy_forest_build(pos_dev, sys_offsets, nsys, a_host, &prm, stream, &tree);
@@ -280,14 +297,15 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
             T.status = r;
             return r;
         }
-        k_gather_rows<<<unsigned((K + 127) / 128), 128, 0, st>>>(u, dt, K, ug);
+        const int64_t k = int64_t(pr.tg.size());
+        k_gather_rows<<<unsigned((k + 127) / 128), 128, 0, st>>>(u, pr.dt, k, pr.ug);
         RPY_LAUNCHED(1);
         RPY_CHECK(cudaGetLastError());
-        RPY_CHECK(cudaMemcpyAsync(got.data(), ug, sizeof(double) * 3 * K, cudaMemcpyDeviceToHost, st));
+        RPY_CHECK(cudaMemcpyAsync(pr.got.data(), pr.ug, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, st));
         RPY_CHECK(cudaStreamSynchronize(st));
         double dn = 0.0;
-        for (int64_t i = 0; i < 3 * K; ++i) dn += (got[i] - ref[i]) * (got[i] - ref[i]);
-        T.err = rn > 0.0 ? std::sqrt(dn / rn) : std::sqrt(dn);
+        for (int64_t i = 0; i < 3 * k; ++i) dn += (pr.got[i] - pr.ref[i]) * (pr.got[i] - pr.ref[i]);
+        T.err = pr.rn > 0.0 ? std::sqrt(dn / pr.rn) : std::sqrt(dn);
         if (timed) {
             std::vector<float> ms;
             for (int q = 0; q < reps; ++q) {
@@ -336,7 +354,7 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
         b.quad = q;
         b.order_p = p;
         Trial T;
-        run(b, false, T);
+        run(b, false, T, probe);
         record(T);
         return T;
     };
@@ -412,7 +430,7 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
         b.quad = q;
         b.order_p = pk.p;
         Trial T;
-        int r = run(b, true, T);
+        int r = run(b, true, T, probe);
         record(T);
         RPY_TRY(r);
         if (T.err <= goal && (!best_ok || T.ms < best_ms)) {
@@ -433,7 +451,7 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
     bool have = false;
     auto consider = [&](const rpy_build_params &q) -> int {
         Trial T;
-        int r = run(q, true, T);
+        int r = run(q, true, T, probe);
         record(T);
         if (r == RPY_ERR_OOM) return RPY_OK;   // a setting too large for the device is skipped
         RPY_TRY(r);
@@ -461,6 +479,81 @@ extern "C" int rpy_autotune(const double *pos_dev, const int64_t *sys_offsets, i
         q.direct_x = w[1];
         RPY_TRY(consider(q));
     }
+
+    // verification on a fresh sample, four times the search's: half uniform over all
+    // beads, half over the beads in the leaves of the chosen tree's two deepest levels
+    // (the longest translation chains, and in the FP32 form the most rounding)
+    const int64_t KV = std::min<int64_t>(4 * K, N);
+    Probe vprobe;
+    {
+        std::vector<int64_t> deep;
+        {
+            rpy_tree tree = nullptr;
+            RPY_TRY(rpy_forest_build(pos_dev, sys_offsets, nsys, a_host, &best.prm, stream, &tree));
+            struct TreeGuard {
+                rpy_tree t;
+                ~TreeGuard() { rpy_tree_free(t); }
+            } tgd{tree};
+            auto fetch = [&](int field, std::vector<int> &v) -> int {
+                int64_t bytes = 0;
+                RPY_TRY(rpy_tree_export(tree, field, nullptr, 0, &bytes));
+                v.resize(size_t(bytes) / sizeof(int));
+                return rpy_tree_export(tree, field, v.data(), bytes, &bytes);
+            };
+            std::vector<int> perm, rng, lv, lvl;
+            RPY_TRY(fetch(RPY_FIELD_PERM, perm));
+            RPY_TRY(fetch(RPY_FIELD_BOX_RANGE, rng));
+            RPY_TRY(fetch(RPY_FIELD_LEAVES, lv));
+            RPY_TRY(fetch(RPY_FIELD_BOX_LEVEL, lvl));
+            int top = 0;
+            for (int b : lv) top = std::max(top, lvl[b]);
+            for (int b : lv)
+                if (lvl[b] >= top - 1)
+                    for (int j = rng[2 * b]; j < rng[2 * b + 1]; ++j) deep.push_back(perm[j]);
+        }
+        uint64_t vseed = seed ^ 0xA5A5A5A5DEADBEEFull;
+        std::set<int64_t> pick;
+        const int64_t kd = std::min<int64_t>(KV / 2, int64_t(deep.size()));
+        while (int64_t(pick.size()) < kd) pick.insert(deep[splitmix64(vseed) % uint64_t(deep.size())]);
+        while (int64_t(pick.size()) < KV) pick.insert(int64_t(splitmix64(vseed) % uint64_t(N)));
+        RPY_TRY(make_probe(std::vector<int64_t>(pick.begin(), pick.end()), vprobe));
+    }
+    const double vgoal = 0.5 * bound;
+    Trial V;
+    RPY_TRY(run(best.prm, false, V, vprobe));
+    const int pmax = phi;
+    for (int tries = 0; V.err > vgoal && tries < 4; ++tries) {
+        rpy_build_params q = V.prm;
+        if (q.precision == RPY_FP32) {
+            // FP32 rounding or truncation?  The FP64 path at the same parameters decides
+            rpy_build_params q64 = q;
+            q64.precision = RPY_FP64;
+            Trial V64;
+            int r = run(q64, false, V64, vprobe);
+            if (r == RPY_OK && V64.err <= vgoal) {
+                V = V64;
+                break;
+            }
+            if (r != RPY_OK && r != RPY_ERR_OOM) return r;
+        }
+        if (q.order_p + 1 > pmax) break;
+        ++q.order_p;
+        Trial Vn;
+        int r = run(q, false, Vn, vprobe);
+        if (r == RPY_ERR_OOM) break;
+        RPY_TRY(r);
+        V = Vn;
+    }
+    if (V.prm.order_p != best.prm.order_p || V.prm.precision != best.prm.precision) {
+        // the verified choice differs from the search's: its own sampled error and time
+        Trial T;
+        RPY_TRY(run(V.prm, true, T, probe));
+        record(T);
+        best = T;
+    }
+    out->verify_rel_l2 = V.err;
+    out->n_verify = int(KV);
+    out->verify_ok = V.err <= vgoal ? 1 : 0;
     out->best = best.prm;
     out->est_rel_l2 = best.err;
     out->matvec_ms = best.ms;

@@ -245,11 +245,13 @@ __host__ __device__ inline int p2x_chunk(int p, int threads) { return (threads /
 
 // MODE 0: P2M over the leaf's own beads (multipole about its centre)
 // MODE 1: P2L over the beads of every box in X(b) (local about b's centre)
+// The fourth charge q4 = F . (r - o) takes its origin o at the expansion's own
+// centre when rb is set (box origin), else at the system's cube centre.
 template <typename T, int MODE>
 __global__ void k_p2x(int b0, int nb, DevTables<T> D, const int *beg, const int *end, const double *ctr,
                       const double *side, const int *lvl, const int *leaf, const int *bsys, const int *xoff,
                       const int *xidx, const double *pos, const double *fs, const double *lapq, int64_t n,
-                      SysConst sc, cpx<T> *out) {
+                      SysConst sc, cpx<T> *out, int rb) {
     const int kChunkB = p2x_chunk(D.p, blockDim.x);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = b0 + blockIdx.x;
@@ -266,8 +268,9 @@ __global__ void k_p2x(int b0, int nb, DevTables<T> D, const int *beg, const int 
     T *q = reinterpret_cast<T *>(acc + kSets * nc);
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) acc[i] = mk<T>(0, 0);
     int sy = bsys[b];
-    double c0x = sc.cube[4 * sy], c0y = sc.cube[4 * sy + 1], c0z = sc.cube[4 * sy + 2];
     double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
+    const double c0x = rb ? cx : sc.cube[4 * sy], c0y = rb ? cy : sc.cube[4 * sy + 1],
+                 c0z = rb ? cz : sc.cube[4 * sy + 2];   // origin of q4
     const double ih = sc.pc[sy].icube * pow2i(lvl[b]);   // 1 / side[b], exactly
     int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     // harmonics: hG points per warp, lane -> (point hg, column pair hc)
@@ -325,8 +328,11 @@ __global__ void k_p2x(int b0, int nb, DevTables<T> D, const int *beg, const int 
 // Dense per-octant operators (used by the FP32 form, where one streaming pass
 // over the operator beats the rotation's extra synchronisation).
 // M2M: parent M = sum over children of T_o [child M]; output degree n uses inputs of degree <= n.
+// rb (box origin of q4): the child's set 4 moves its origin from the child's
+// centre to the parent's first, M4 += (c_child - c_parent) . M_F (sets 1..3).
 template <typename T>
-__global__ void k_m2m(int b0, int nb, DevTables<T> D, const int *leaf, const int *child, cpx<T> *M) {
+__global__ void k_m2m(int b0, int nb, DevTables<T> D, const int *leaf, const int *child, const double *side,
+                      int rb, cpx<T> *M) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = b0 + blockIdx.x;
     if (leaf[b]) return;
@@ -342,6 +348,13 @@ __global__ void k_m2m(int b0, int nb, DevTables<T> D, const int *leaf, const int
         __syncthreads();
         for (int i = threadIdx.x; i < kSets * Dd; i += blockDim.x) X[i] = src[i];
         __syncthreads();
+        if (rb) {
+            const double h = 0.5 * side[c];   // child centre - parent centre = h (2 bit - 1) per axis
+            const T dx = T((o & 1) ? h : -h), dy = T((o & 2) ? h : -h), dz = T((o & 4) ? h : -h);
+            for (int i = threadIdx.x; i < Dd; i += blockDim.x)
+                X[3 * Dd + i] = fma(dz, X[2 * Dd + i], fma(dy, X[Dd + i], fma(dx, X[i], X[3 * Dd + i])));
+            __syncthreads();
+        }
         if (r < Dd) {
             const T *Tt = D.m2m_t + size_t(o) * Dd * Dd;
             for (int k = 0; k < kmax; ++k) {
@@ -358,8 +371,11 @@ __global__ void k_m2m(int b0, int nb, DevTables<T> D, const int *leaf, const int
 }
 
 // L2L: child L += S_o [parent L]; output degree k uses inputs of degree >= k.
+// rb (box origin of q4): the shifted set 4 moves its origin from the parent's
+// centre to the child's, L4 += (c_parent - c_child) . L_F.
 template <typename T>
-__global__ void k_l2l(int b0, int nb, DevTables<T> D, const int *par, const int *cell, cpx<T> *L) {
+__global__ void k_l2l(int b0, int nb, DevTables<T> D, const int *par, const int *cell, const double *side, int rb,
+                      cpx<T> *L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = b0 + blockIdx.x;
     int P = par[b];
@@ -379,6 +395,11 @@ __global__ void k_l2l(int b0, int nb, DevTables<T> D, const int *par, const int 
         T t = St[size_t(k) * Dd + r];
 #pragma unroll
         for (int s = 0; s < kSets; ++s) acc[s] += t * X[s * Dd + k];
+    }
+    if (rb) {
+        const double h = 0.5 * side[b];   // parent centre - child centre = -h (2 bit - 1) per axis
+        const T dx = T((o & 1) ? -h : h), dy = T((o & 2) ? -h : h), dz = T((o & 4) ? -h : h);
+        acc[3] = fma(dz, acc[2], fma(dy, acc[1], fma(dx, acc[0], acc[3])));
     }
     T *dst = reinterpret_cast<T *>(L + size_t(b) * kSets * nc);
     for (int s = 0; s < kSets; ++s) dst[s * Dd + r] += acc[s];
@@ -432,9 +453,11 @@ __device__ void rotate_sets_f(const T *rf, const int *foff, int p, const cpx<T> 
 // (O(p^3) per child instead of the O(p^4) dense operator), and write the
 // child's share to its slot Sc[parent][octant]; k_m2m_sum adds the slots of each
 // parent in octant order (a fixed order: the result does not depend on timing).
+// rb (box origin of q4): the share's set 4 moves its origin from the child's
+// centre to the parent's, M4 += (c_child - c_parent) . M_F.
 template <typename T>
-__global__ void k_m2m_child(int c0, int pb0, DevTables<T> D, const int *par, const int *cell, const cpx<T> *M,
-                            cpx<T> *Sc) {
+__global__ void k_m2m_child(int c0, int pb0, DevTables<T> D, const int *par, const int *cell, const double *side,
+                            int rb, const cpx<T> *M, cpx<T> *Sc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int c = c0 + blockIdx.x;
     const int p = D.p, nc = ncoef(p), P1 = p + 1;
@@ -459,7 +482,17 @@ __global__ void k_m2m_child(int c0, int pb0, DevTables<T> D, const int *par, con
     rotate_sets_f(D.forot_bwd + size_t(o) * D.frot_len, D.frot_off, p, X, Tm, Y);
     __syncthreads();
     cpx<T> *dst = Sc + (size_t(par[c] - pb0) * 8 + o) * kSets * nc;
-    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) dst[i] = Y[i];
+    const double h = 0.5 * side[c];
+    const T dx = T((o & 1) ? h : -h), dy = T((o & 2) ? h : -h), dz = T((o & 4) ? h : -h);
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) {
+        cpx<T> v = Y[i];
+        if (rb && i >= 3 * nc) {
+            const int k = i - 3 * nc;
+            const cpx<T> fx = Y[k], fy = Y[nc + k], fz = Y[2 * nc + k];
+            v = mk(fma(dz, fz.x, fma(dy, fy.x, fma(dx, fx.x, v.x))), fma(dz, fz.y, fma(dy, fy.y, fma(dx, fx.y, v.y))));
+        }
+        dst[i] = v;
+    }
 }
 
 template <typename T>
@@ -479,8 +512,11 @@ __global__ void k_m2m_sum(int b0, int nc4, const int *leaf, const int *child, co
     }
 }
 
+// rb (box origin of q4): the shifted set 4 moves its origin from the parent's
+// centre to the child's, L4 += (c_parent - c_child) . L_F.
 template <typename T>
-__global__ void k_l2l_rot(int b0, int nb, DevTables<T> D, const int *par, const int *cell, cpx<T> *L) {
+__global__ void k_l2l_rot(int b0, int nb, DevTables<T> D, const int *par, const int *cell, const double *side,
+                          int rb, cpx<T> *L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = b0 + blockIdx.x;
     int P = par[b];
@@ -506,7 +542,17 @@ __global__ void k_l2l_rot(int b0, int nb, DevTables<T> D, const int *par, const 
     rotate_sets_f(D.forot_bwd + size_t(o) * D.frot_len, D.frot_off, p, X, Tm, Y);
     __syncthreads();
     cpx<T> *dst = L + size_t(b) * kSets * nc;
-    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) dst[i] += Y[i];
+    const double h = 0.5 * side[b];
+    const T dx = T((o & 1) ? -h : h), dy = T((o & 2) ? -h : h), dz = T((o & 4) ? -h : h);
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) {
+        cpx<T> v = Y[i];
+        if (rb && i >= 3 * nc) {
+            const int k = i - 3 * nc;
+            const cpx<T> fx = Y[k], fy = Y[nc + k], fz = Y[2 * nc + k];
+            v = mk(fma(dz, fz.x, fma(dy, fy.x, fma(dx, fx.x, v.x))), fma(dz, fz.y, fma(dy, fy.y, fma(dx, fx.y, v.y))));
+        }
+        dst[i] += v;
+    }
 }
 
 // ---------------------------------------------------------------- M2X
@@ -822,6 +868,154 @@ __global__ void k_x2x(const int *parents, DevTables<T> D, const int *coll, const
     }
 }
 
+// Merge-and-shift with the four charge sets of a plane wave in one thread (the
+// FP32 form, and the box-origin form in either precision).  With rb (box origin
+// of q4 = F . (r - o)), set 4 travels with its origin at the centre of the box
+// whose expansion it is: each source's set 4 moves to the parent centre as it is
+// merged, X4 += (c_source - c_parent) . X_F, and each merged sum moves to the
+// child as it is shifted there, X4 += (c_parent - c_child) . X_F, with X_F the
+// force sets 1..3 of the same wave (rotations of the frames act on the plane-wave
+// variables only, so the world offsets apply as they are).
+template <typename T, bool FAC>
+__global__ void k_x2x4(const int *parents, DevTables<T> D, const int *coll, const int *child, const int *leaf,
+                       const double *side, const cpx<T> *Xo, cpx<T> *Xi, int f0, int nf, int rb) {
+    __shared__ int src[216];
+    __shared__ int vsrc[216], vsh[216], vpre[217], vend[216];
+    __shared__ int voz[216], vox[216], voy[216];
+    __shared__ T vd[3][216];   // source centre - parent centre (world axes), set-4 origin move
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = parents[blockIdx.x];
+    const int dl = blockIdx.y, d = 2 * f0 + dl;
+    const int S = D.S;
+    const double hc = 0.5 * side[P];   // side of P's children (and of the sources)
+    for (int sl = threadIdx.x; sl < 216; sl += blockDim.x) {
+        int q = sl >> 3, o = sl & 7;
+        int Q = coll[27 * P + q];
+        src[sl] = (Q >= 0 && !leaf[Q]) ? child[8 * Q + o] : -1;
+    }
+    __syncthreads();
+    const int ng = D.grp_n[d];
+    const int *goff = D.grp_off + d * (kGroupMax + 1);
+    const int *gmask = D.grp_mask + d * kGroupMax;
+    const int *slots = D.slot_list + d * 216;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, nsl = goff[ng];
+        int carry = 0;
+        for (int z0 = 0; z0 < nsl; z0 += 32) {
+            const int z = z0 + lane;
+            int ent = 0, sb = -1;
+            if (z < nsl) {
+                ent = slots[z];
+                sb = src[ent & 255];
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, sb >= 0);
+            const int pos = carry + __popc(bal & ((1u << lane) - 1u));
+            if (z < nsl) vpre[z] = pos;
+            if (sb >= 0) {
+                vsrc[pos] = sb;
+                vsh[pos] = ent >> 8;
+                // slot = colleague (dx, dy, dz in -1..1, index 9 dz + 3 dy + dx + 13) x 8 + child octant:
+                // source centre - P's centre = hc (2 d + bit - 1/2) per axis, in world axes
+                const int sl = ent & 255, q = sl >> 3, o = sl & 7;
+                vd[0][pos] = T(hc * (2 * (q % 3 - 1) + (o & 1) - 0.5));
+                vd[1][pos] = T(hc * (2 * ((q / 3) % 3 - 1) + ((o >> 1) & 1) - 0.5));
+                vd[2][pos] = T(hc * (2 * (q / 9 - 1) + ((o >> 2) & 1) - 0.5));
+            }
+            carry += __popc(bal);
+        }
+        if (lane == 0) vpre[nsl] = carry;
+    }
+    __syncthreads();
+    const int nz = vpre[goff[ng]];
+    for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+        vend[z] = 0;
+        const int o = vsh[z];
+        vox[z] = (o % 6) * S;
+        voy[z] = ((o / 6) % 6) * S;
+        voz[z] = (o / 36) * S;
+    }
+    T *sZ = reinterpret_cast<T *>(smem_raw);
+    cpx<T> *sX = reinterpret_cast<cpx<T> *>(sZ + ((6 * S + 3) & ~3));
+    cpx<T> *sY = sX + 6 * S;
+    if constexpr (FAC) {
+        for (int i = threadIdx.x; i < 6 * S; i += blockDim.x) {
+            sZ[i] = D.shz[i];
+            sX[i] = D.shx[i];
+            sY[i] = D.shy[i];
+        }
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        const int z1 = vpre[goff[g + 1]];
+        if (z1 > vpre[goff[g]]) vend[z1 - 1] = gmask[g];
+    }
+    __syncthreads();
+    int ch[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) ch[t] = child[8 * P + t];
+    const size_t dstride = size_t(2 * nf) * kSets * S;
+    const cpx<T> *Xd = Xo + size_t(dl) * kSets * S;
+    for (int j = threadIdx.x; j < S; j += blockDim.x) {
+        cpx<T> acc[8][kSets];
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+#pragma unroll
+            for (int k = 0; k < kSets; ++k) acc[t][k] = mk<T>(0, 0);
+        cpx<T> ga[kSets];
+#pragma unroll
+        for (int k = 0; k < kSets; ++k) ga[k] = mk<T>(0, 0);
+#pragma unroll 2
+        for (int z = 0; z < nz; ++z) {
+            const cpx<T> *xs = Xd + size_t(vsrc[z]) * dstride + j;
+            cpx<T> x[kSets];
+#pragma unroll
+            for (int k = 0; k < kSets; ++k) x[k] = xs[size_t(k) * S];
+            if (rb) {
+                const T ex = vd[0][z], ey = vd[1][z], ez = vd[2][z];
+                x[3].x = fma(ez, x[2].x, fma(ey, x[1].x, fma(ex, x[0].x, x[3].x)));
+                x[3].y = fma(ez, x[2].y, fma(ey, x[1].y, fma(ex, x[0].y, x[3].y)));
+            }
+            cpx<T> sh;
+            if constexpr (FAC) {
+                const cpx<T> a = sX[vox[z] + j], b = sY[voy[z] + j];
+                const T c = sZ[voz[z] + j];
+                sh = mk(c * fma(a.x, b.x, -a.y * b.y), c * fma(a.x, b.y, a.y * b.x));
+            } else {
+                sh = D.shift[size_t(vsh[z]) * S + j];
+            }
+#pragma unroll
+            for (int k = 0; k < kSets; ++k) {
+                ga[k].x = fma(-x[k].y, sh.y, fma(x[k].x, sh.x, ga[k].x));
+                ga[k].y = fma(x[k].y, sh.x, fma(x[k].x, sh.y, ga[k].y));
+            }
+            const int mask = vend[z];   // block-uniform
+            if (mask) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if ((mask >> t) & 1)
+#pragma unroll
+                        for (int k = 0; k < kSets; ++k) acc[t][k] += ga[k];
+#pragma unroll
+                for (int k = 0; k < kSets; ++k) ga[k] = mk<T>(0, 0);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (ch[t] < 0) continue;
+            if (rb) {   // P's centre - child t's centre = -(hc / 2) (2 bit - 1) per axis
+                const double h = 0.5 * hc;
+                const T ex = T((t & 1) ? -h : h), ey = T((t & 2) ? -h : h), ez = T((t & 4) ? -h : h);
+                acc[t][3].x = fma(ez, acc[t][2].x, fma(ey, acc[t][1].x, fma(ex, acc[t][0].x, acc[t][3].x)));
+                acc[t][3].y = fma(ez, acc[t][2].y, fma(ey, acc[t][1].y, fma(ex, acc[t][0].y, acc[t][3].y)));
+            }
+            const cpx<T> sh = D.shift[size_t(D.child_shift[d * 8 + t]) * S + j];
+            cpx<T> *dst = Xi + (size_t(ch[t]) * (2 * nf) + dl) * kSets * S + j;
+#pragma unroll
+            for (int k = 0; k < kSets; ++k) dst[size_t(k) * S] = acc[t][k] * sh;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- X2L
 template <typename T>
 __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *L, int f0, int nf) {
@@ -1068,11 +1262,13 @@ __device__ void build_eval_set(const cpx<T> *src, int p, int P, cpx<T> *EV, cpx<
     __syncthreads();
 }
 
+// rb: the multipoles carry q4 about their own box centres (box origin), so the
+// set-4 gradient is re-based from the source box's centre to the leaf's.
 template <typename T>
 __global__ void k_far_eval(const int *leaves, DevTables<T> D, const int *beg, const int *end, const double *ctr,
                            const double *side, const int *lvl, const int *bsys, const int *woff, const int *widx,
                            const double *pos, int64_t n, SysConst sc, const cpx<T> *L, const cpx<T> *M,
-                           double *ufar) {
+                           double *ufar, int rb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int li = blockIdx.x;
     int b = leaves[li];
@@ -1101,8 +1297,10 @@ __global__ void k_far_eval(const int *leaves, DevTables<T> D, const int *beg, co
             __syncthreads();
             for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) srcs[i] = E[i];
             __syncthreads();
-            if (w < 0) build_eval_set<T, false>(srcs, p, P, EV, tmp, cbx - c0x, cby - c0y, cbz - c0z, G);
-            else build_eval_set<T, true>(srcs, p, P, EV, tmp, cbx - c0x, cby - c0y, cbz - c0z, G);
+            // origin of the source expansion's q4: its own centre (box origin) or the cube centre
+            const double ox = rb ? ctr[3 * C] : c0x, oy = rb ? ctr[3 * C + 1] : c0y, oz = rb ? ctr[3 * C + 2] : c0z;
+            if (w < 0) build_eval_set<T, false>(srcs, p, P, EV, tmp, cbx - ox, cby - oy, cbz - oz, G);
+            else build_eval_set<T, true>(srcs, p, P, EV, tmp, cbx - ox, cby - oy, cbz - oz, G);
             double ih = icube * pow2i(lvl[C]);   // 1 / side[C], exactly
             T acc[kNE];
 #pragma unroll
@@ -1124,9 +1322,11 @@ __global__ void k_far_eval(const int *leaves, DevTables<T> D, const int *beg, co
 
 // Per leaf at level >= 2: the 18 derived local expansions of Eq. (2.8),
 // written to global memory for the bead-parallel evaluation.
+// rb: the local expansions carry q4 about their own box centres (box origin),
+// so set 4 needs no re-basing to the leaf centre.
 template <typename T>
 __global__ void k_eval_prep(const int *leaves, DevTables<T> D, const double *ctr, const int *lvl, const int *bsys,
-                            SysConst sc, const cpx<T> *L, cpx<T> *EVg, int per_component) {
+                            SysConst sc, const cpx<T> *L, cpx<T> *EVg, int per_component, int rb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int li = blockIdx.x;
     int b = leaves[li];
@@ -1141,8 +1341,10 @@ __global__ void k_eval_prep(const int *leaves, DevTables<T> D, const double *ctr
     __syncthreads();
     int sy = bsys[b];
     cpx<T> *EV = EVg + size_t(li) * kNE * nc;
-    build_eval_set<T, false>(srcs, p, p, EV, tmp, ctr[3 * b] - sc.cube[4 * sy], ctr[3 * b + 1] - sc.cube[4 * sy + 1],
-                             ctr[3 * b + 2] - sc.cube[4 * sy + 2], G);
+    if (rb) build_eval_set<T, false>(srcs, p, p, EV, tmp, 0.0, 0.0, 0.0, G);
+    else
+        build_eval_set<T, false>(srcs, p, p, EV, tmp, ctr[3 * b] - sc.cube[4 * sy],
+                                 ctr[3 * b + 1] - sc.cube[4 * sy + 1], ctr[3 * b + 2] - sc.cube[4 * sy + 2], G);
     // Fold the terms of Eq. (2.8) that are not multiplied by a coordinate into
     // fields 0..2 (in units of C1/h):  L_d + h^-1 dL4'_d - (C2/C1) h^-2 dL_C,d.
     // The bead evaluation then needs fields 0..11 only.
@@ -1388,12 +1590,17 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     }
     int b2 = t.level_off[2];
     int n2 = nbx - b2;
+    // origin of q4 (RPY charges only; the Laplace diagnostic takes its charges as given):
+    // each expansion's own box centre by default in FP32, the cube centre in FP64
+    const int fl = t.params.flags;
+    const int rb = lapq ? 0
+                        : (sizeof(T) == 4 ? !(fl & RPY_FLAG_CUBE_ORIGIN) : (fl & RPY_FLAG_BOX_ORIGIN) != 0);
     // upward pass
     size_t sp = smem_p2x<T>(p, 128);
     RPY_TRY(set_smem(k_p2x<T, 0>, sp));
     RPY_TRY(set_smem(k_p2x<T, 1>, sp));
     k_p2x<T, 0><<<n2, 128, sp, st>>>(b2, n2, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level, t.b_leaf,
-                                     t.b_sys, t.x_off, t.x_idx, t.pos, fs, lapq, t.n, sc, M);
+                                     t.b_sys, t.x_off, t.x_idx, t.pos, fs, lapq, t.n, sc, M, rb);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     prof_mark(t, RPY_STAGE_M2M, st);
@@ -1416,12 +1623,12 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
                 if (cn > 0) {
                     if (!t.m2m_scratch) return RPY_ERR_INTERNAL;
                     cpx<T> *Sc = static_cast<cpx<T> *>(t.m2m_scratch);
-                    k_m2m_child<T><<<cn, 256, smr2, st>>>(cb, lb, D, t.b_parent, t.b_cell, M, Sc);
+                    k_m2m_child<T><<<cn, 256, smr2, st>>>(cb, lb, D, t.b_parent, t.b_cell, t.b_side, rb, M, Sc);
                     k_m2m_sum<T><<<ln, 256, 0, st>>>(lb, kSets * nc, t.b_leaf, t.b_child, Sc, M);
                     RPY_LAUNCHED(2);
                 }
             } else {
-                k_m2m<T><<<ln, thr, smd, st>>>(lb, ln, D, t.b_leaf, t.b_child, M);
+                k_m2m<T><<<ln, thr, smd, st>>>(lb, ln, D, t.b_leaf, t.b_child, t.b_side, rb, M);
                 RPY_LAUNCHED(1);
             }
         }
@@ -1445,19 +1652,25 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
         if (f0 == 0) prof_mark(t, RPY_STAGE_X2X, st);
         if (t.n_x2x_par > 0) {
             dim3 g(t.n_x2x_par, 2 * nf);
-            // FP32 with up to 256 stored waves: shifts from per-axis factors in shared
-            // memory (measured faster there; at more waves the shared memory costs
-            // occupancy and the table is faster)
-            bool fac = false;
-            if constexpr (sizeof(T) == 4) {
-                if (D.S <= 256) {
-                    const size_t sxx = sizeof(T) * ((6 * D.S + 3) & ~3) + 2 * sizeof(cpx<T>) * 6 * D.S;
-                    k_x2x<T, true><<<g, x2x_threads(D.S), sxx, st>>>(t.x2x_par, D, t.b_coll, t.b_child, t.b_leaf,
-                                                                     Xo, Xi, f0, nf);
-                    fac = true;
+            // FP32 (and the box-origin form): the four sets of a wave in one thread.  FP32 with
+            // up to 256 stored waves: shifts from per-axis factors in shared memory (measured
+            // faster there; at more waves the shared memory costs occupancy and the table is
+            // faster)
+            if (sizeof(T) == 4 || rb) {
+                bool fac = false;
+                if constexpr (sizeof(T) == 4) {
+                    if (D.S <= 256) {
+                        const size_t sxx = sizeof(T) * ((6 * D.S + 3) & ~3) + 2 * sizeof(cpx<T>) * 6 * D.S;
+                        k_x2x4<T, true><<<g, even_threads(D.S), sxx, st>>>(t.x2x_par, D, t.b_coll, t.b_child,
+                                                                           t.b_leaf, t.b_side, Xo, Xi, f0, nf, rb);
+                        fac = true;
+                    }
                 }
-            }
-            if (!fac) {
+                if (!fac) {
+                    k_x2x4<T, false><<<g, even_threads(D.S), 0, st>>>(t.x2x_par, D, t.b_coll, t.b_child, t.b_leaf,
+                                                                      t.b_side, Xo, Xi, f0, nf, rb);
+                }
+            } else {
                 k_x2x<T, false><<<g, x2x_threads(D.S), 0, st>>>(t.x2x_par, D, t.b_coll, t.b_child, t.b_leaf, Xo, Xi,
                                                                 f0, nf);
             }
@@ -1477,7 +1690,7 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     // X list
     prof_mark(t, RPY_STAGE_P2L, st);
     k_p2x<T, 1><<<n2, 128, sp, st>>>(b2, n2, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level, t.b_leaf,
-                                     t.b_sys, t.x_off, t.x_idx, t.pos, fs, lapq, t.n, sc, L);
+                                     t.b_sys, t.x_off, t.x_idx, t.pos, fs, lapq, t.n, sc, L, rb);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     // downward pass
@@ -1485,8 +1698,8 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     for (int l = 3; l < t.nlevels; ++l) {
         int lb = t.level_off[l], ln = t.level_off[l + 1] - lb;
         if (ln > 0) {
-            if (rot_l) k_l2l_rot<T><<<ln, 256, smr2, st>>>(lb, ln, D, t.b_parent, t.b_cell, L);
-            else k_l2l<T><<<ln, thr, smd, st>>>(lb, ln, D, t.b_parent, t.b_cell, L);
+            if (rot_l) k_l2l_rot<T><<<ln, 256, smr2, st>>>(lb, ln, D, t.b_parent, t.b_cell, t.b_side, rb, L);
+            else k_l2l<T><<<ln, thr, smd, st>>>(lb, ln, D, t.b_parent, t.b_cell, t.b_side, rb, L);
             RPY_LAUNCHED(1);
         }
     }
@@ -1498,7 +1711,8 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
         RPY_TRY(set_smem(k_eval_prep<T>, sp2));
         // one expansion per velocity component unless the per-potential form is asked for
         const int per_comp = (t.params.flags & RPY_FLAG_EVAL_PER_POTENTIAL) ? 0 : 1;
-        k_eval_prep<T><<<t.nleaf, 128, sp2, st>>>(t.leaves, D, t.b_center, t.b_level, t.b_sys, sc, L, EVg, per_comp);
+        k_eval_prep<T><<<t.nleaf, 128, sp2, st>>>(t.leaves, D, t.b_center, t.b_level, t.b_sys, sc, L, EVg, per_comp,
+                                                  rb);
         RPY_LAUNCHED(1);
         const int ga = int((t.n + 127) / 128);
         if (per_comp)
@@ -1511,7 +1725,7 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
         size_t sf = smem_far<T>(p);
         RPY_TRY(set_smem(k_far_eval<T>, sf));
         k_far_eval<T><<<t.nleaf, 64, sf, st>>>(t.leaves, D, t.b_begin, t.b_end, t.b_center, t.b_side, t.b_level,
-                                                t.b_sys, t.w_off, t.w_idx, t.pos, t.n, sc, L, M, ufar);
+                                                t.b_sys, t.w_off, t.w_idx, t.pos, t.n, sc, L, M, ufar, rb);
         RPY_LAUNCHED(1);
         RPY_CHECK(cudaGetLastError());
     }

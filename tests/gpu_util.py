@@ -9,14 +9,15 @@ def cuda_tensor(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to("cuda")
 
 
-def matvec(pos, f, a, s, digits, leaf_cap=0, precision=0, parts=3, order_p=0, direct_w=0, direct_x=0):
+def matvec(pos, f, a, s, digits, leaf_cap=0, precision=0, parts=3, order_p=0, direct_w=0, direct_x=0, flags=0,
+           quad=0):
     """Build a tree on the GPU and apply it once; returns (u (N,3) numpy, tree)."""
     import torch
     P, F = cuda_tensor(pos), cuda_tensor(f)
     U = torch.empty_like(F)
-    if order_p or direct_w or direct_x:
+    if order_p or direct_w or direct_x or flags or quad:
         t = rp.rpy_forest_build(P, [0, len(pos)], [a], digits, leaf_cap=leaf_cap, precision=precision,
-                                order_p=order_p, direct_w=direct_w, direct_x=direct_x)
+                                order_p=order_p, direct_w=direct_w, direct_x=direct_x, flags=flags, quad=quad)
     else:
         t = rp.rpy_tree_build(P, len(pos), a, digits, leaf_cap=leaf_cap, precision=precision)
     rp.rpy_matvec_parts(t, F, s, U, parts)

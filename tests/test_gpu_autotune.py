@@ -93,3 +93,29 @@ def test_evaluate_sources_at_targets():
     u = U.cpu().numpy()
     assert oracle.rel_l2(u, ref) <= 1e-6
     assert np.max(np.abs(u[:10] - ref[:10])) <= 1e-6 * np.max(np.abs(ref))
+
+
+def test_autotune_verifies_its_choice_on_a_fresh_deep_sample():
+    """With the loosest search margin (accept a sampled error up to the bound itself on
+    64 targets), the tuner's choice must still pass its verification: an independent
+    FP64 direct sum on 256 fresh targets, half in the two deepest leaf levels, at half
+    the bound.  The verified choice meets the setting against the oracle."""
+    sysm = synth.sphere_plus_cube(200000, seed=33, a=1e-4)
+    P, F = cuda_tensor(sysm.pos), cuda_tensor(sysm.f)
+    res = rp.rpy_autotune(P, [0, sysm.n], [sysm.a], F, sysm.s, 6, rp.RPY_FP32, n_samples=64, timed_reps=1,
+                          margin=1.0)
+    best = res["best"]
+    assert res["n_verify"] == 256
+    assert res["verify_ok"] and res["verify_rel_l2"] <= 0.5e-6
+    assert best["precision"] in (rp.RPY_FP32, rp.RPY_FP64)
+    import torch
+    t = rp.rpy_forest_build(P, [0, sysm.n], [sysm.a], 6, leaf_cap=best["leaf_cap"], precision=best["precision"],
+                            order_p=best["order_p"], direct_w=best["direct_w"], direct_x=best["direct_x"],
+                            quad=best["quad"])
+    U = torch.empty_like(F)
+    rp.rpy_forest_matvec(t, F, [sysm.s], U)
+    rp.rpy_tree_sync(t)
+    tg = synth.sample_targets(sysm.n, k=400, seed=78)
+    ref = oracle.rpy_direct(sysm.pos, sysm.f, sysm.a, sysm.s, targets=tg)
+    assert oracle.rel_l2(U.cpu().numpy()[tg], ref) <= 1e-6
+    t.close()

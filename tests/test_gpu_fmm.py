@@ -571,3 +571,105 @@ def test_fp32_precision_form_6digit():
     rb = oracle.rpy_direct(b.pos, b.f, b.a, b.s, targets=tb)
     assert oracle.rel_l2(u[tg], ra) <= 1e-6
     assert oracle.rel_l2(u[sysm.n + tb], rb) <= 1e-6
+
+
+# ---------------------------------------------------------------- origin of the fourth charge set
+
+@pytest.mark.parametrize("extra", [0, rp.RPY_FLAG_FRAME_PASSES, rp.RPY_FLAG_EVAL_PER_POTENTIAL])
+@pytest.mark.parametrize("direct", [(-1, -1), (0, 0)])
+def test_box_origin_equals_cube_origin_fp64(extra, direct):
+    """q4 = F . (r - o) about each box's own centre, moved along with every translation
+    (P2M, M2M, X2X merge and child shift, P2L, L2L, M2P and L2P re-based to the leaf), gives
+    the velocity of one origin per system up to FP64 rounding: Eq. (2.8) holds for any
+    common origin, and each move is the exact identity M4(o') = M4(o) + (o - o') . M_F."""
+    sysm = synth.sphere_plus_cube(30000, 31, 1e-4)
+    kw = dict(leaf_cap=40, direct_w=direct[0], direct_x=direct[1])
+    u0, t0 = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, 6, flags=rp.RPY_FLAG_CUBE_ORIGIN | extra, **kw)
+    u1, t1 = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, 6, flags=rp.RPY_FLAG_BOX_ORIGIN | extra, **kw)
+    st = rp.rpy_tree_stats(t1)
+    assert st["depth"] >= 5 and st["n_xlist"] > 0
+    if direct == (-1, -1):
+        assert st["n_wlist"] > 0
+    assert oracle.rel_l2(u1, u0) < 1e-12
+
+
+@pytest.mark.parametrize("digits,order", [(3, 8), (6, 16)])   # dense M2M / L2L below p = 12, rotations above
+def test_fp32_box_origin_rounding_against_fp64(digits, order):
+    """The FP32 form's rounding (its difference from the FP64 path at the same tree and
+    order) with the box origin of q4 stays below the cube-origin form's on a deep adaptive
+    tree, and below 0.3 x the digit setting's bound (FP32 unit roundoff is 6e-8)."""
+    sysm = synth.sphere_plus_cube(400000, 41, 2e-5)
+    kw = dict(order_p=order, leaf_cap=20)
+    u64, t64 = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, digits, **kw)
+    ub, tb = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, digits, precision=rp.RPY_FP32, **kw)
+    uc, tc = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, digits, precision=rp.RPY_FP32, flags=rp.RPY_FLAG_CUBE_ORIGIN,
+                    **kw)
+    assert rp.rpy_tree_stats(tb)["depth"] >= 7
+    rb, rc = oracle.rel_l2(ub, u64), oracle.rel_l2(uc, u64)
+    assert rb < rc, (rb, rc)
+    assert rb < 0.3 * (1e-3 if digits == 3 else 1e-6), rb
+
+
+@pytest.mark.parametrize("leaf_cap,depth", [(0, 7), (40, 8)])
+def test_fp32_6digit_deep_sphere_2m(leaf_cap, depth):
+    """The FP32 form at the 6-digit setting on a 2M-bead sphere (90% on the surface, 10%
+    in the cube), at the default leaf capacity (tree depth 7) and at 40 (depth 8), against
+    the oracle on 500 targets."""
+    sysm = synth.sphere_plus_cube(2_000_000, 42, 1e-4)
+    tg = synth.sample_targets(sysm.n, 500)
+    e, e_far, t = _check(sysm.pos, sysm.f, sysm.a, sysm.s, 6, 1e-6, targets=tg, precision=rp.RPY_FP32,
+                         leaf_cap=leaf_cap)
+    assert rp.rpy_tree_stats(t)["depth"] >= depth
+
+
+def test_batch_shaped_forest_fp32_3digit():
+    """24 systems drawn like the 256-system batch (log-uniform sizes 1e3..2e5, half
+    Plummer clusters, a = 0.5 / N^(1/3), so 2a is the mean spacing and the 2a rule leaves
+    oversize leaves in the cluster cores), one forest, FP32 at 3 digits with default
+    parameters: every system meets rel-L2 <= 1e-3 against the oracle on its own sampled
+    targets, and the far part alone stays within 5x of that."""
+    import torch
+    systems = synth.config4(nsys=24)
+    off = np.concatenate([[0], np.cumsum([sy.n for sy in systems])]).astype(np.int64)
+    pos = np.concatenate([sy.pos for sy in systems])
+    f = np.concatenate([sy.f for sy in systems])
+    t = rp.rpy_forest_build(cuda_tensor(pos), off, [sy.a for sy in systems], 3, precision=rp.RPY_FP32)
+    U = torch.empty((len(pos), 3), dtype=torch.float64, device="cuda")
+    rp.rpy_forest_matvec(t, cuda_tensor(f), [sy.s for sy in systems], U)
+    rp.rpy_tree_sync(t)
+    u = U.cpu().numpy()
+    st = rp.rpy_tree_stats(t)
+    assert st["leaves_over_cap"] > 0   # the 2a rule binds in the cluster cores
+    kinds = set()
+    for k, sy in enumerate(systems):
+        tg = synth.sample_targets(sy.n, 150, seed=100 + k)
+        ref = oracle.rpy_direct(sy.pos, sy.f, sy.a, sy.s, targets=tg)
+        got = u[off[k] + tg]
+        self_t = sy.s / (6 * math.pi * sy.a) * sy.f[tg]
+        assert oracle.rel_l2(got, ref) <= 1e-3, (k, sy.name)
+        assert oracle.rel_l2(got - self_t, ref - self_t) <= 5e-3, (k, sy.name)
+        kinds.add(sy.name.rstrip("0123456789"))
+    assert kinds == {"cube", "plummer"}
+
+
+@pytest.mark.parametrize("precision,tol", [(rp.RPY_FP64, 1e-12), (rp.RPY_FP32, 1e-6)])
+def test_full_matvec_equals_near_plus_far_parts(precision, tol):
+    """The full matvec sums each leaf's U list and its direct substitutes of small W / X
+    interactions in one near-field pass; the part calls keep them apart (NEAR: U lists and
+    self term; FAR: everything else, direct substitutes included).  Both splits add up to the
+    same velocity, up to the rounding that regrouping the sums allows."""
+    import torch
+    sysm = synth.sphere_plus_cube(30000, 51, 1e-4)
+    t = rp.rpy_forest_build(cuda_tensor(sysm.pos), [0, sysm.n], [sysm.a], 6, precision=precision, leaf_cap=40,
+                            direct_w=200, direct_x=60)
+    st = rp.rpy_tree_stats(t)
+    assert st["n_dlist"] > 0 and st["d_pairs"] > 0
+    F = cuda_tensor(sysm.f)
+    out = {}
+    for name, part in (("all", rp.RPY_PART_ALL), ("near", rp.RPY_PART_NEAR), ("far", rp.RPY_PART_FAR)):
+        U = torch.empty_like(F)
+        rp.rpy_matvec_parts(t, F, sysm.s, U, part)
+        rp.rpy_tree_sync(t)
+        out[name] = U.cpu().numpy()
+    assert oracle.rel_l2(out["near"] + out["far"], out["all"]) < tol
+    assert oracle.rel_l2(out["far"], out["all"]) > 1e-3   # the far part is not negligible
