@@ -196,20 +196,6 @@ def host_cpu():
     return {"model": model, "nproc": os.cpu_count(), "affinity": len(os.sched_getaffinity(0))}
 
 
-def flops_model(stats, stage):
-    """Algorithmic floating-point operations of one stage (FMA = 2), counted
-    from the far branch of the pair kernels: FP64 38 per pair (3 sub, r^2 5,
-    Newton step of the reciprocal square root 5, 1/r^2 1, 1/r^3 1, t1 2,
-    1 - 2a^2/r^2 2, c 1, R.F 5, t2 1, accumulate 12); FP32 33 per pair (the
-    same without the Newton step: the reciprocal square root runs on the
-    special-function unit and is not counted; the Kahan merges, one per 32
-    pairs, are not counted either)."""
-    if stage == "p2p":
-        per = 38.0 if stats["precision"] == 0 else 33.0
-        return (stats["u_pairs"] + stats["d_pairs"]) * per
-    return None
-
-
 def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profile=True):
     import torch
     import paper_1711_02976_gb300 as rp
@@ -232,6 +218,7 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
     a_list = sysm.a_list if forest else [sysm.a]
     s_list = sysm.s_list if forest else [sysm.s]
     tune = None
+    prec = cfg["precision"]
     bp = {"leaf_cap": cfg["leaf_cap"], "order_p": 0, "direct_w": 0, "direct_x": 0, "quad": 0}
     if getattr(args, "params", None):
         vals = [int(v) for v in args.params.split(",")]
@@ -241,7 +228,8 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
         # thresholds, by sampled-target error against the GPU direct sum and timed matvecs
         tune = rp.rpy_autotune(P, off, a_list, F, s_list, cfg["digits"], cfg["precision"])
         bp = {k: tune["best"][k] for k in ("leaf_cap", "order_p", "direct_w", "direct_x", "quad")}
-    tree = rp.rpy_forest_build(P, off, a_list, cfg["digits"], precision=cfg["precision"], **bp)
+        prec = tune["best"]["precision"]   # an FP32 choice that fails verification falls back to FP64
+    tree = rp.rpy_forest_build(P, off, a_list, cfg["digits"], precision=prec, **bp)
     matvec = lambda: rp.rpy_forest_matvec(tree, F, s_list, U)
 
     for _ in range(warmup):
@@ -302,10 +290,10 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
         "metric": METRIC, "value": round(value, 4), "unit": "Mbeads/s", "n_gpus": ws, "steps": steps,
         "warmup": warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": (round(value / cfg["paper_mbeads_s"], 4) if cfg.get("paper_mbeads_s") else None),
-        "dtype": "f64" if cfg["precision"] == 0 else "f32+f64",
+        "dtype": "f64" if prec == 0 else "f32+f64",
         "data": "synthetic (seeded numpy; shapes of the paper's sphere/cube workloads)",
         "config": {"workload": config, "description": cfg["desc"], "n_beads": n, "digits": cfg["digits"],
-                   "precision": "fp64" if cfg["precision"] == 0 else "fp32", "parallelism": f"replicas x{ws}",
+                   "precision": "fp64" if prec == 0 else "fp32", "parallelism": f"replicas x{ws}",
                    "l2": "flushed between timed steps (256 MB write)", "step": "tree build + matvec",
                    "leaf_cap": stats["leaf_cap"], "order_p": stats["order_p"], "exp_terms": stats["exp_terms"],
                    "direct_w": bp["direct_w"], "direct_x": bp["direct_x"], "quad_rule": stats["quad"],
@@ -320,74 +308,99 @@ def run_ours(args, ws, rank, local, config=None, steps=None, warmup=None, profil
                                        "n_xlist", "n_dlist", "max_leaf_count", "leaves_over_cap", "device_bytes")},
         "gpu_launches": int(launches), "clocks": clocks,
         "autotune": None if tune is None else {
-            "chosen": bp, "est_rel_l2": tune["est_rel_l2"], "goal": tune["goal"], "tune_ms": round(tune["tune_ms"], 1),
-            "n_trials": len(tune["trials"]), "samples": 256,
+            "chosen": dict(bp, precision="fp64" if prec == 0 else "fp32"), "est_rel_l2": tune["est_rel_l2"],
+            "goal": tune["goal"], "tune_ms": round(tune["tune_ms"], 1), "n_trials": len(tune["trials"]),
+            "samples": 256, "verify_rel_l2": tune["verify_rel_l2"], "n_verify": tune["n_verify"],
+            "verify_ok": tune["verify_ok"],
             "method": "per plane-wave rule, smallest p with sampled error <= goal; fastest (rule, p); then leaf cap "
-                      "and direct thresholds by timed matvecs"},
+                      "and direct thresholds by timed matvecs; verified on 1,024 fresh targets (half in the two "
+                      "deepest leaf levels) at 0.5 x bound"},
     }
+    work = rp.rpy_tree_work(tree)
     tree.close()
-    return result, sysm, u_dev, stats, stage_ms, None
+    return result, sysm, u_dev, stats, stage_ms, work
 
 
-# DRAM bytes per bead of one FP64 U-list P2P launch, from the ncu capture of the
-# 200k-bead sphere case (profiles/k_p2p_fp64_sphere200k.md: 10,256,896 B); the
-# traffic is the sources' positions and forces, so it grows with the bead count.
-P2P64_DRAM_BYTES_PER_BEAD = 10747648.0 / 200000.0   # merged U + direct pass, 200k-bead ncu capture
+# DRAM bytes per bead of the FP64 near-field launch (the merged pass over U lists and
+# direct substitutes, k_p2p), from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the 200,000-bead sphere + cube workload at 6 digits, FP64
+# (bench.py --config sphere200k_6digit_fp64): 10,747,648 B per launch.  The traffic is
+# the sources' positions and forces, so it grows with the bead count; it is reported
+# only for that kernel.
+P2P64_DRAM_BYTES_PER_BEAD = 10747648.0 / 200000.0
 
 
-def roofline(result, stats, stage_ms, peaks):
+def hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, written by the
+    driver next to this file), else the profiling recipe's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json: STREAM-style copy)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s, one earlier GB300 measurement)"
+
+
+def roofline(precision, stage_ms, work, peaks, n_beads=None):
+    """Roofline of the dominant stage (largest time) and the fractions of every stage.
+    work[stage] = (algorithmic FLOPs, algorithmic DRAM bytes) of one matvec on the tree
+    (rpy_tree_work); the achieved rates divide them by the stage's CUDA-event time.  A
+    stage's bound is the roof it is closer to: the FP64 or FP32 FMA peak measured on
+    this GPU (rpy_alu_peak) or the measured HBM copy bandwidth."""
+    hbm, hbm_src = hbm_peak_gbs()
+    alu = peaks["fp64"] if precision == "fp64" else peaks["fp32"]
+    per = {}
+    for k, ms in stage_ms.items():
+        fl, by = work.get(k, (0.0, 0.0))
+        if ms <= 0:
+            continue
+        fa = fl / (ms * 1e-3) / alu if fl else 0.0
+        fh = by / (ms * 1e-3) / 1e9 / hbm if by else 0.0
+        per[k] = {"ms": round(ms, 4), "frac_alu": round(fa, 4), "frac_hbm": round(fh, 4)}
     top = max(stage_ms, key=lambda k: stage_ms[k])
-    fl = flops_model(stats, top)
-    prec = result["config"]["precision"]
-    if fl is not None and stage_ms[top] > 0:
-        peak = peaks["fp64"] if prec == "fp64" else peaks["fp32"]
-        ach = fl / (stage_ms[top] * 1e-3) / 1e12
-        traffic = None
-        if top == "p2p" and prec == "fp64":
-            traffic = round(P2P64_DRAM_BYTES_PER_BEAD * stats["n_beads"])
-        return {"kernel": top, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak / 1e12, 4),
-                "unit": "TFLOP/s", "frac": round(ach / (peak / 1e12), 4), "traffic": traffic,
-                "traffic_note": "DRAM bytes of the near-field launch (U lists and direct substitutes), scaled by bead count from a 200k-bead ncu capture"
-                if traffic else None,
-                "fp64_pipe_utilisation_ncu": 0.910 if (top == "p2p" and prec == "fp64") else None,
-                "peak_source": "measured FMA-chain probe on this GPU (rpy_alu_peak)"}
-    return {"kernel": top, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-            "traffic": None}
+    fl, by = work[top]
+    t = stage_ms[top] * 1e-3
+    fa, fh = fl / t / alu, by / t / 1e9 / hbm
+    if fa >= fh:
+        out = {"kernel": top, "bound": "alu", "achieved": round(fl / t / 1e12, 4), "peak": round(alu / 1e12, 4),
+               "unit": "TFLOP/s", "frac": round(fa, 4),
+               "peak_source": f"measured {precision.upper()} FMA-chain probe on this GPU (rpy_alu_peak)"}
+    else:
+        out = {"kernel": top, "bound": "hbm", "achieved": round(by / t / 1e9, 1), "peak": hbm, "unit": "GB/s",
+               "frac": round(fh, 4), "peak_source": hbm_src}
+    out["algorithmic"] = {"flops": fl, "bytes": by, "stage_ms": round(stage_ms[top], 4)}
+    out["traffic"] = None
+    if top == "p2p" and precision == "fp64" and n_beads:
+        out["traffic"] = round(P2P64_DRAM_BYTES_PER_BEAD * n_beads)
+        out["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of k_p2p per bead from an ncu capture "
+                               "of the 200k-bead sphere (6 digits, FP64), scaled by bead count")
+    out["stages"] = per
+    return out
 
 
-def e2e_host(args, sysm, cfg, bp=None):
-    """The same work through the public API with host data, every step: H2D of the
-    positions from pinned memory, rpy_tree_update_positions (the tree built on the first
-    call stays resident, as in a Brownian-dynamics loop), H2D of the forces, the matvec,
-    D2H of the velocities.  One system at the default parameters without a resident tree
-    would use rpy_matvec_host (one call: copies, build, matvec, copy back)."""
+def e2e_host(args, sysm, cfg, bp=None, precision=None):
+    """The same work through the C ABI with host buffers, every step: one call of
+    rpy_tree_matvec_host on the resident tree with page-locked host arrays, which copies
+    the positions to the device, rebuilds the tree for them, copies the forces, applies
+    the matvec and copies the velocities back (the Brownian-dynamics / serving step).
+    The tree is built once before the timed steps."""
     import torch
     import paper_1711_02976_gb300 as rp
     n = sysm.n
-    pos_h = torch.from_numpy(sysm.pos).pin_memory()
-    f_h = torch.from_numpy(sysm.f).pin_memory()
-    u_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    pos_h = torch.from_numpy(sysm.pos).pin_memory().numpy()
+    f_h = torch.from_numpy(sysm.f).pin_memory().numpy()
+    u_h = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
     forest = isinstance(sysm, Forest)
-    P = torch.empty((n, 3), dtype=torch.float64, device="cuda")
-    F = torch.empty_like(P)
-    U = torch.empty_like(P)
     off = sysm.off if forest else [0, n]
     a_list = sysm.a_list if forest else [sysm.a]
     s_list = sysm.s_list if forest else [sysm.s]
     kw = bp if bp is not None else {"leaf_cap": cfg["leaf_cap"]}
-    P.copy_(pos_h)
-    tree = rp.rpy_forest_build(P, off, a_list, cfg["digits"], precision=cfg["precision"], **kw)
-
-    def call():
-        P.copy_(pos_h, non_blocking=True)
-        rp.rpy_tree_update_positions(tree, P)
-        F.copy_(f_h, non_blocking=True)
-        rp.rpy_forest_matvec(tree, F, s_list, U)
-        u_h.copy_(U, non_blocking=True)
-        torch.cuda.synchronize()
+    P = torch.from_numpy(sysm.pos).cuda()
+    tree = rp.rpy_forest_build(P, off, a_list, cfg["digits"],
+                               precision=cfg["precision"] if precision is None else precision, **kw)
+    del P
+    call = lambda: rp.rpy_tree_matvec_host(tree, pos_h, f_h, s_list, u_h)
     for _ in range(2):
         call()
-    torch.cuda.synchronize()
     ts = []
     for _ in range(max(2, min(args.steps, 5))):
         t0 = time.perf_counter()
@@ -397,8 +410,8 @@ def e2e_host(args, sysm, cfg, bp=None):
     t = statistics.median(ts)
     return {"value": round(n / t / 1e6, 4), "unit": "Mbeads/s", "h2d_bytes_per_step": 2 * n * 3 * 8,
             "d2h_bytes_per_step": n * 3 * 8, "ms_per_step": round(t * 1e3, 3),
-            "api": "per step: H2D positions, rpy_tree_update_positions, H2D forces, rpy_forest_matvec, D2H "
-                   "velocities (pinned host arrays, resident tree)"}
+            "api": "per step one rpy_tree_matvec_host call (C ABI, page-locked host arrays): H2D positions, "
+                   "tree rebuild, H2D forces, matvec, D2H velocities, on the resident tree"}
 
 
 def cpu_oracle_sample(sysm, k):
@@ -441,8 +454,8 @@ def precision_form(args, local, sysm_cfg):
     cfg = dict(CONFIGS[sysm_cfg])
     name = sysm_cfg + "__fp32"
     CONFIGS[name] = dict(cfg, precision=1, desc=cfg["desc"].replace("FP64", "FP32 precision form"))
-    res, sysm, u, stats, stage_ms, _ = run_ours(args, 1, 0, local, config=name, steps=3, warmup=2, profile=False)
-    return res, sysm, u
+    res, sysm, u, stats, stage_ms, work = run_ours(args, 1, 0, local, config=name, steps=3, warmup=2, profile=True)
+    return res, sysm, u, stage_ms, work
 
 
 def serve(args, local):
@@ -526,7 +539,7 @@ def bd(args, local):
     F = torch.from_numpy(sysm.f).cuda()
     tune = rp.rpy_autotune(P, off, a_list, F, s_list, cfg["digits"], cfg["precision"])
     bp = {k: tune["best"][k] for k in ("leaf_cap", "order_p", "direct_w", "direct_x", "quad")}
-    tree = rp.rpy_forest_build(P, off, a_list, cfg["digits"], precision=cfg["precision"], **bp)
+    tree = rp.rpy_forest_build(P, off, a_list, cfg["digits"], precision=tune["best"]["precision"], **bp)
     rng = torch.Generator(device="cuda").manual_seed(77)
     a0 = float(np.min(a_list))
     kT, eta = 1.0, 1.0 / (6 * math.pi * a0)   # kT/eta = 6 pi a: D_ii = 1 for the smallest bead
@@ -610,16 +623,16 @@ def main():
         if rank == 0:
             print(json.dumps(bd(args, local)), flush=True)
         return
-    result, sysm, u_dev, stats, stage_ms, _ = run_ours(args, ws, rank, local)
+    result, sysm, u_dev, stats, stage_ms, work = run_ours(args, ws, rank, local)
     import paper_1711_02976_gb300 as rp
     peaks = {"fp64": rp.rpy_alu_peak(rp.RPY_FP64), "fp32": rp.rpy_alu_peak(rp.RPY_FP32)}
     result["alu_peaks_tflops"] = {k: round(v / 1e12, 3) for k, v in peaks.items()}
-    result["roofline"] = roofline(result, stats, stage_ms, peaks)
+    result["roofline"] = roofline(result["config"]["precision"], stage_ms, work, peaks, stats["n_beads"])
     if not args.no_e2e:
         c = result["config"]
         bp = ({k: c[k] for k in ("leaf_cap", "order_p", "direct_w", "direct_x")} | {"quad": c["quad_rule"]}
               if c["params"] in ("autotuned", "fixed") else None)
-        result["e2e"] = e2e_host(args, sysm, CONFIGS[args.config], bp)
+        result["e2e"] = e2e_host(args, sysm, CONFIGS[args.config], bp, 0 if c["precision"] == "fp64" else 1)
     if rank == 0:
         import oracle
         tg, ref, dt, th = cpu_oracle_sample(sysm, args.targets)
@@ -629,14 +642,17 @@ def main():
         result["rel_l2"] = err
         result["rel_l2_far"] = err_far
         if not args.no_forms and CONFIGS[args.config]["precision"] == 0 and CONFIGS[args.config]["digits"] != 9:
-            pf, psys, pu = precision_form(args, local, args.config)
+            pf, psys, pu, pstage, pwork = precision_form(args, local, args.config)
             result["precision_form"] = {
                 "value": pf["value"], "unit": "Mbeads/s", "ms_per_step": pf["ms_per_step"],
                 "resident_tree_matvec_ms": pf["resident_tree_matvec_ms"], "dtype": "f32+f64",
                 "rel_l2": oracle.rel_l2(pu[tg], ref), "rel_l2_far": oracle.rel_l2(pu[tg] - selft, ref - selft),
                 "leaf_cap": pf["config"]["leaf_cap"], "order_p": pf["config"]["order_p"],
-                "params": pf["config"]["params"],
-                "note": "same workload and digit setting, P2P and translations in FP32 with compensated sums"}
+                "params": pf["config"]["params"], "stages_ms": pf["stages_ms"],
+                "roofline": roofline("fp32", pstage, pwork, peaks),
+                "note": "same workload and digit setting: P2P in FP32 with compensated (Kahan) sums, translations "
+                        "in FP32 with every expansion's fourth charge set about its own box centre; bounding "
+                        "cube, Morton keys, r ~ 0 pairs and per-bead sums in FP64"}
         result["cpu_baseline"] = {"value": round(len(tg) / dt / 1e6, 6), "unit": "Mbeads/s", "cores": th,
                                   "kind": "oracle", "host": host_cpu(),
                                   "sample": (f"all {sysm.n} beads (full direct sum)" if len(tg) == sysm.n else

@@ -207,6 +207,24 @@ int rpy_matvec_parts(rpy_tree t, const double *f_dev, double kT_over_eta, double
                      void *stream);
 
 /*
+ * The matvec of a resident tree with HOST buffers: the step of a Brownian-
+ * dynamics loop or a serving request (Sec. 1: D F at the current positions).
+ * When pos_host is non-NULL it is copied to the device and the tree is rebuilt
+ * for it (as rpy_tree_update_positions); then f_host is copied, u = D F is
+ * applied (as rpy_forest_matvec) and u is copied back to u_host.  All on
+ * `stream`, synchronised before return.  Page-locked host buffers
+ * (cudaHostAlloc, cudaHostRegister) copy at full bus speed; pageable ones work
+ * and copy slower.  The tree allocates 9 N doubles of device buffers for the
+ * copies on the first call and keeps them until rpy_tree_free.
+ *   pos_host           host, N x 3 FP64 (caller order), or NULL: positions unchanged
+ *   f_host             host, N x 3 FP64
+ *   kT_over_eta_host   host, one value per system (finite)
+ *   u_host             host, N x 3 FP64 (written)
+ */
+int rpy_tree_matvec_host(rpy_tree t, const double *pos_host, const double *f_host,
+                         const double *kT_over_eta_host, double *u_host, void *stream);
+
+/*
  * One-shot form with the paper's argument list (positions, radius, forces,
  * kT/eta, accuracy digits): builds a tree, applies it once, frees it.
  * All arrays are device arrays.  Synchronises `stream`.
@@ -471,6 +489,20 @@ int rpy_alu_peak(int precision, double *flops_per_s, void *stream);
  * give wrong cubes.  Asynchronous on `stream`; allocates nothing.
  */
 int rpy_bounding_cube_noalloc(const double *pos_dev, int64_t n, double *cube_dev, void *stream);
+
+/*
+ * Algorithmic work of one matvec on t, per stage (RPY_STAGE_*): flops_host[k]
+ * floating-point operations (an FMA counts 2) and bytes_host[k] DRAM bytes that
+ * stage k needs at this tree, order and plane-wave rule, counted from the tree
+ * (near-list bead pairs, boxes per level, present merge-and-shift sources per
+ * parent and direction, X- and W-list sizes): the numerators of the roofline
+ * fractions reported beside measured stage times.  The paper has no
+ * counterpart (it is instrumentation); the operation counts follow the
+ * kernels' algorithms as listed in rpy_work.cu.  n = slots in each array
+ * (entries beyond RPY_NUM_STAGES are zeroed).  Copies tree arrays to the host;
+ * synchronises t's last stream.
+ */
+int rpy_tree_work(rpy_tree t, double *flops_host, double *bytes_host, int n);
 
 /* Number of kernels this library has launched in this process (all devices). */
 int64_t rpy_launch_count(void);

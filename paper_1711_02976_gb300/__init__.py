@@ -21,10 +21,10 @@ __all__ = [
     "RpyError", "RpyStats", "BuildParams", "load", "rpy_tree_build", "rpy_forest_build",
     "rpy_tree_update_positions", "rpy_matvec", "rpy_forest_matvec", "rpy_matvec_parts",
     "rpy_matvec_oneshot", "rpy_matvec_host", "rpy_laplace_far", "rpy_tree_export", "rpy_tree_stats",
-    "rpy_tree_sync", "rpy_tree_footprint", "rpy_tree_free", "rpy_strerror", "rpy_last_cuda_error",
+    "rpy_tree_sync", "rpy_tree_footprint", "rpy_tree_free", "rpy_strerror", "rpy_last_cuda_error", "rpy_tree_work",
     "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times", "rpy_launch_count",
     "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt",
-    "rpy_bd_step", "rpy_evaluate", "rpy_matvec_batched", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
+    "rpy_bd_step", "rpy_evaluate", "rpy_matvec_batched", "rpy_tree_matvec_host", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
     "RPY_PART_ALL", "RPY_FLAG_NO_GRAPH", "RPY_FLAG_FRAME_PASSES",
     "RPY_FLAG_EVAL_PER_POTENTIAL", "RPY_FLAG_BOX_ORIGIN", "RPY_FLAG_CUBE_ORIGIN", "EXPORTED_SYMBOLS",
 ]
@@ -49,7 +49,7 @@ EXPORTED_SYMBOLS = [
     "rpy_launch_count", "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_server_create", "rpy_server_add_system",
     "rpy_server_submit", "rpy_server_wait", "rpy_server_cancel", "rpy_server_drain", "rpy_server_stats_get",
     "rpy_server_destroy", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt", "rpy_bd_step", "rpy_evaluate",
-    "rpy_matvec_batched",
+    "rpy_matvec_batched", "rpy_tree_work", "rpy_tree_matvec_host",
 ]
 STAGES = ["gather", "p2p", "p2m", "m2m", "m2x", "x2x", "x2l", "p2l", "l2l", "eval", "combine"]
 
@@ -156,6 +156,8 @@ def load(build_if_missing: bool = True):
             "rpy_debug_table": [i, i, i, vp, i64, ctypes.POINTER(i64)],
             "rpy_tree_set_profiling": [vp, i],
             "rpy_tree_stage_times": [vp, vp, i],
+            "rpy_tree_work": [vp, vp, vp, i],
+            "rpy_tree_matvec_host": [vp, vp, vp, vp, vp, vp],
             "rpy_launch_count": [],
             "rpy_alu_peak": [i, ctypes.POINTER(d), vp],
             "rpy_bounding_cube_noalloc": [vp, i64, vp, vp],
@@ -397,6 +399,20 @@ def rpy_matvec_host(pos, a, f, kT_over_eta, digits, u, precision=RPY_FP64, strea
                                   int(precision), _ptr(u), _stream(stream)), "rpy_matvec_host")
 
 
+def rpy_tree_matvec_host(tree, pos, f, kT_over_eta, u, stream=None):
+    """Resident-tree matvec with host numpy arrays (N x 3 float64, C-contiguous; pos may be
+    None to keep the positions): rebuild for pos, copy f, u = D f, copy u back (synchronous)."""
+    nsys = tree.nsys if isinstance(tree, Tree) else 1
+    for name, arr in (("pos", pos), ("f", f), ("u", u)):
+        if arr is None and name == "pos":
+            continue
+        if not isinstance(arr, np.ndarray) or arr.dtype != np.float64 or not arr.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name} must be a C-contiguous float64 numpy array")
+    sv = np.ascontiguousarray(np.broadcast_to(np.asarray(kT_over_eta, dtype=np.float64), (nsys,)))
+    _check(load().rpy_tree_matvec_host(_h(tree), _ptr(pos) if pos is not None else None, _ptr(f), sv.ctypes.data,
+                                       _ptr(u), _stream(stream)), "rpy_tree_matvec_host")
+
+
 def rpy_laplace_far(tree, q, out, stream=None):
     _check(load().rpy_laplace_far(_h(tree), _dev_f64(q, "q"), _dev_f64(out, "out"), _stream(stream)),
            "rpy_laplace_far")
@@ -473,6 +489,14 @@ def rpy_tree_stage_times(tree) -> dict:
     ms = np.zeros(len(STAGES))
     _check(load().rpy_tree_stage_times(_h(tree), ms.ctypes.data, len(STAGES)), "rpy_tree_stage_times")
     return dict(zip(STAGES, ms.tolist()))
+
+
+def rpy_tree_work(tree) -> dict:
+    """Algorithmic FLOPs and DRAM bytes of one matvec per stage: {stage: (flops, bytes)}."""
+    fl = np.zeros(len(STAGES))
+    by = np.zeros(len(STAGES))
+    _check(load().rpy_tree_work(_h(tree), fl.ctypes.data, by.ctypes.data, len(STAGES)), "rpy_tree_work")
+    return {k: (float(a), float(b)) for k, a, b in zip(STAGES, fl, by)}
 
 
 def rpy_launch_count() -> int:

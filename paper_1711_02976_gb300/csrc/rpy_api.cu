@@ -110,10 +110,11 @@ static std::atomic<int64_t> g_launches{0};
 void note_launches(int n) { g_launches += n; }
 
 void prof_mark(Tree &t, int k, cudaStream_t st) {
-    if (!t.prof || k < 0 || k >= 16) return;
-    if (!t.ev[k]) cudaEventCreate(&t.ev[k]);
-    cudaEventRecord(t.ev[k], st);
-    t.ev_used[k] = true;
+    if (!t.prof || k < 0 || k > RPY_NUM_STAGES || t.n_marks >= Tree::kMaxMarks) return;
+    const int i = t.n_marks++;
+    if (!t.ev[i]) cudaEventCreate(&t.ev[i]);
+    cudaEventRecord(t.ev[i], st);
+    t.ev_stage[i] = k;
 }
 
 // ---------------------------------------------------------------- table cache
@@ -459,7 +460,7 @@ int run_matvec(Tree &t, const double *f_dev, const double *s_host, double *u_dev
     if (!t.built) return RPY_ERR_STATE;
     RPY_TRY(upload_s(t, s_host, st));
     SysConst sc{t.sys_cube, t.sys_a, t.sys_s, t.sys_pc};
-    for (int k = 0; k < 16; ++k) t.ev_used[k] = false;
+    t.n_marks = 0;
     prof_mark(t, RPY_STAGE_GATHER, st);
     k_gather_f<<<nb256(t.n), 256, 0, st>>>(f_dev, t.perm, t.n, t.fs, t.f32);
     RPY_LAUNCHED(1);
@@ -624,7 +625,7 @@ int rpy_tree_update_positions(rpy_tree h, const double *pos_dev, void *stream) {
     fresh.direct_w = t.direct_w;
     fresh.direct_x = t.direct_x;
     fresh.prof = t.prof;
-    for (int k = 0; k < 16; ++k) fresh.ev[k] = t.ev[k];
+    for (int k = 0; k < Tree::kMaxMarks; ++k) fresh.ev[k] = t.ev[k];
     fresh.done = t.done;
     fresh.cap_stream = t.cap_stream;
     fresh.side_stream = t.side_stream;
@@ -634,8 +635,37 @@ int rpy_tree_update_positions(rpy_tree h, const double *pos_dev, void *stream) {
     fresh.a_h = t.a_h;
     fresh.cache = std::move(t.cache);
     fresh.device_bytes = t.device_bytes;
+    fresh.host_io = t.host_io;
     t = std::move(fresh);
     return do_build(t, pos_dev, static_cast<cudaStream_t>(stream));
+}
+
+int rpy_tree_matvec_host(rpy_tree h, const double *pos_host, const double *f_host, const double *s_host,
+                         double *u_host, void *stream) {
+    if (!valid(h) || !f_host || !u_host || !s_host) return RPY_ERR_INVALID;
+    Tree &t = h->t;
+    for (int k = 0; k < t.nsys; ++k)
+        if (!std::isfinite(s_host[k])) return RPY_ERR_INVALID;
+    DeviceGuard g(t.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t n3 = 3 * size_t(t.n);
+    if (!t.host_io) {
+        cudaError_t e = cudaMalloc(&t.host_io, sizeof(double) * 3 * n3);
+        if (e != cudaSuccess) {
+            t.host_io = nullptr;
+            return check_cuda("cudaMalloc (host-buffer matvec)", e);
+        }
+    }
+    double *dp = t.host_io, *df = t.host_io + n3, *du = t.host_io + 2 * n3;
+    if (pos_host) {
+        RPY_CHECK(cudaMemcpyAsync(dp, pos_host, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
+        RPY_TRY(rpy_tree_update_positions(h, dp, stream));
+    }
+    RPY_CHECK(cudaMemcpyAsync(df, f_host, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
+    RPY_TRY(rpy_forest_matvec(h, df, s_host, du, stream));
+    RPY_CHECK(cudaMemcpyAsync(u_host, du, sizeof(double) * n3, cudaMemcpyDeviceToHost, st));
+    RPY_CHECK(cudaStreamSynchronize(st));
+    return RPY_OK;
 }
 
 int rpy_forest_matvec(rpy_tree h, const double *f_dev, const double *s_host, double *u_dev, void *stream) {
@@ -879,8 +909,9 @@ void rpy_tree_free(rpy_tree h) {
         DeviceGuard g(t.device);
         wait_done(t);
         tree_release(t);
-        for (int k = 0; k < 16; ++k)
+        for (int k = 0; k < Tree::kMaxMarks; ++k)
             if (t.ev[k]) cudaEventDestroy(t.ev[k]);
+        if (t.host_io) cudaFree(t.host_io);
         if (t.done) cudaEventDestroy(t.done);
         drop_graph(t);
         if (t.cap_stream) cudaStreamDestroy(t.cap_stream);
@@ -903,15 +934,14 @@ int rpy_tree_stage_times(rpy_tree h, double *ms, int n) {
     Tree &t = h->t;
     DeviceGuard g(t.device);
     RPY_CHECK(wait_done(t));
-    for (int k = 0; k < n; ++k) {
-        ms[k] = 0.0;
-        if (k >= RPY_NUM_STAGES || !t.ev_used[k]) continue;
-        int nx = k + 1;
-        while (nx <= RPY_NUM_STAGES && !t.ev_used[nx]) ++nx;
-        if (nx > RPY_NUM_STAGES) continue;
+    for (int k = 0; k < n; ++k) ms[k] = 0.0;
+    // each mark opens an interval of its stage that the next mark closes
+    for (int i = 0; i + 1 < t.n_marks; ++i) {
+        const int k = t.ev_stage[i];
+        if (k >= RPY_NUM_STAGES || k >= n) continue;
         float v = 0.f;
-        RPY_CHECK(cudaEventElapsedTime(&v, t.ev[k], t.ev[nx]));
-        ms[k] = v;
+        RPY_CHECK(cudaEventElapsedTime(&v, t.ev[i], t.ev[i + 1]));
+        ms[k] += v;
     }
     return RPY_OK;
 }

@@ -1636,8 +1636,8 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     RPY_CHECK(cudaGetLastError());
     // plane-wave M2L: all three frames in one pass, or (large trees, where the
     // plane-wave buffers of six directions would not fit) one frame per pass,
-    // each pass adding its frame's share into L.  With one frame per pass the
-    // stage times of frames 1 and 2 are counted under X2L.
+    // each pass adding its frame's share into L (with profiling on, every pass's
+    // M2X, X2X and X2L launches are timed under their own stages).
     const int nf = t.x_frames;
     size_t smx = smem_m2x<T>(p, D.s);
     RPY_TRY(set_smem(k_m2x<T>, smx));
@@ -1645,11 +1645,11 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     if constexpr (sizeof(T) == 4) RPY_TRY(set_smem(k_x2l4, sxl));
     else RPY_TRY(set_smem(k_x2l<T>, sxl));
     for (int f0 = 0; f0 < 3; f0 += nf) {
-        if (f0 == 0) prof_mark(t, RPY_STAGE_M2X, st);
+        prof_mark(t, RPY_STAGE_M2X, st);
         k_m2x<T><<<n2, even_threads(sizeof(T) == 8 ? D.NU : D.S), smx, st>>>(b2, n2, D, M, Xo, f0, nf);
         RPY_LAUNCHED(1);
         RPY_CHECK(cudaGetLastError());
-        if (f0 == 0) prof_mark(t, RPY_STAGE_X2X, st);
+        prof_mark(t, RPY_STAGE_X2X, st);
         if (t.n_x2x_par > 0) {
             dim3 g(t.n_x2x_par, 2 * nf);
             // FP32 (and the box-origin form): the four sets of a wave in one thread.  FP32 with
@@ -1677,7 +1677,7 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
             RPY_LAUNCHED(1);
             RPY_CHECK(cudaGetLastError());
         }
-        if (f0 == 0) prof_mark(t, RPY_STAGE_X2L, st);
+        prof_mark(t, RPY_STAGE_X2L, st);
         // FP32 X2L: blocks sized to the (node, m) items of its widest phase at low
         // order; at high order the shared memory already limits the blocks per SM
         // and 256 threads hide latency better

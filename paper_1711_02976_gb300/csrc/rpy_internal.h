@@ -247,6 +247,8 @@ struct Tree {
     float *p32 = nullptr;             // FP32 form: sorted positions as hi + lo floats, [6][n] (x,y,z hi; x,y,z lo)
     float *f32 = nullptr;             // FP32 form: sorted forces [3][n]
     double *u_near = nullptr, *u_far = nullptr, *u_dir = nullptr;   // sorted [n][3]
+    double *host_io = nullptr;        // rpy_tree_matvec_host: positions, forces, velocities [9][n] (caller order),
+                                      // allocated on its first call, kept across rebuilds
     double *lap_q = nullptr;          // [n][4] sorted charges for the Laplace debug path
     double *sys_s = nullptr;          // [nsys] kT/eta of the last matvec
     PairConst *sys_pc = nullptr;      // [nsys] constants derived from a, kT/eta and the root cube
@@ -281,8 +283,12 @@ struct Tree {
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int matvecs = 0;                  // matvecs since the last build
-    cudaEvent_t ev[16] = {};
-    bool ev_used[16] = {};
+    // stage marks of the last profiled matvec: event k opens an interval of stage
+    // ev_stage[k] that the next mark closes (a stage may recur, e.g. once per plane-wave frame)
+    static constexpr int kMaxMarks = 32;
+    cudaEvent_t ev[kMaxMarks] = {};
+    int ev_stage[kMaxMarks] = {};
+    int n_marks = 0;
 };
 
 // stage markers: record event k on st when profiling is on
