@@ -458,66 +458,141 @@ def precision_form(args, local, sysm_cfg):
     return res, sysm, u, stage_ms, work
 
 
-def serve(args, local):
-    """Serving form: Poisson requests from resident systems (sizes log-uniform
-    1e4..2e6, cube or sphere, jittered positions and fresh forces per request,
-    50/50 3-digit FP32 / 6-digit FP64), admitted by device-memory footprint."""
+class ServeClient:
+    """Client of the serving loop for the resident systems of the serving workload:
+    request data (jittered positions, fresh N(0,1) forces) drawn before any timing, a
+    few variants per system, so that the arrival process is not held up by random-number
+    generation; velocities land in page-locked buffers; a collector thread waits for the
+    requests in submission order and hands their velocity buffers back."""
+
+    def __init__(self, systems, srv, variants=2, seed=55):
+        import torch
+        rng = np.random.default_rng(seed)
+        # the server copies positions and forces into its own page-locked buffers at submit
+        self.systems, self.srv = systems, srv
+        self.data = [[(np.ascontiguousarray(synth_jitter(rng, sy.pos)), rng.standard_normal(sy.pos.shape))
+                      for _ in range(variants)] for sy in systems]
+        self.free_u = [[] for _ in systems]
+        self.lock = threading.Lock()
+
+    def _u(self, k):
+        import torch
+        with self.lock:
+            if self.free_u[k]:
+                return self.free_u[k].pop()
+        return torch.empty(self.systems[k].pos.shape, dtype=torch.float64).pin_memory().numpy()
+
+    def run(self, order, rate, rng):
+        """Submit one request per entry of `order` (system indices): back to back when
+        rate is 0, else at Poisson arrivals of `rate` per second.  Returns the wall time
+        from the first submit to the last completion and per-request records."""
+        import paper_1711_02976_gb300 as rp
+        import queue
+        q = queue.Queue()
+        recs = []
+
+        def collect():
+            while True:
+                item = q.get()
+                if item is None:
+                    return
+                rid, k, u = item
+                st, lat, tm = rp.rpy_server_wait_times(self.srv, rid)
+                recs.append((st, lat, k, tm))
+                with self.lock:
+                    self.free_u[k].append(u)
+
+        th = threading.Thread(target=collect, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        t_next = t0
+        for r, k in enumerate(order):
+            sy = self.systems[k]
+            pos, f = self.data[k][r % len(self.data[k])]
+            u = self._u(k)
+            if rate:
+                t_next += rng.exponential(1.0 / rate)
+                while time.perf_counter() < t_next:
+                    time.sleep(0.0002)
+            q.put((rp.rpy_server_submit(self.srv, k, pos, f, sy.s, u), k, u))
+        q.put(None)
+        th.join()
+        return time.perf_counter() - t0, recs
+
+
+def synth_jitter(rng, pos):
+    import synth
+    return synth.jitter(rng, pos)
+
+
+def serving(args, local, loads=(0.7,), n_req=None):
+    """Serving form: requests from the 64 resident systems of the serving workload
+    (sizes log-uniform 1e4..2e6 beads, cube or sphere, jittered positions and fresh
+    forces per request, 3-digit FP32 / 6-digit FP64 alternating by system), admitted by
+    device-memory footprint, four worker slots.  Measures (1) every system's request
+    alone (the serial bound: beads / sum of solo latencies, and the kernel-only bound
+    from the device time of each solo request's rebuild and matvec), (2) a closed loop
+    (all requests submitted at once) and (3) Poisson arrivals at a fraction of the
+    closed-loop capacity, with p50 / p99 latency and per-phase times."""
     import torch
     import paper_1711_02976_gb300 as rp
     import synth
     torch.cuda.set_device(local)
+    n_req = n_req or args.serve_requests
     systems = synth.config5(nsys=args.serve_systems)
-    rng = np.random.default_rng(55)
     srv = rp.rpy_server_create(slots=args.serve_slots)
-    kinds = []
     for k, sy in enumerate(systems):
         d, prec = (3, 1) if k % 2 == 0 else (6, 0)
-        kinds.append((d, prec))
         rp.rpy_server_add_system(srv, sy.pos, sy.a, d, precision=prec)
+    cl = ServeClient(systems, srv)
+    rng = np.random.default_rng(56)
+    nsys = len(systems)
+    # warm every system (its first admission builds its tree), then each request alone
+    cl.run(list(range(nsys)), 0, rng)
+    solo = {}
+    for k in range(nsys):
+        _, recs = cl.run([k], 0, rng)
+        st, lat, _, tm = recs[0]
+        solo[k] = (lat, tm["build_ms"] + tm["matvec_ms"], tm)
+    beads = np.array([sy.n for sy in systems], dtype=np.float64)
+    serial_bound = beads.sum() / sum(v[0] for v in solo.values()) / 1e3
+    kernel_bound = beads.sum() / sum(v[1] for v in solo.values()) / 1e3
 
-    def run(n_req, rate, order=None):
-        outs, t_next = [], time.perf_counter()
-        for r in range(n_req):
-            k = order[r] if order is not None else int(rng.integers(len(systems)))
-            sy = systems[k]
-            pos = synth.jitter(rng, sy.pos)
-            f = rng.standard_normal(sy.pos.shape)
-            u = np.zeros_like(f)
-            if rate:
-                t_next += rng.exponential(1.0 / rate)
-                while time.perf_counter() < t_next:
-                    time.sleep(0.0005)
-            outs.append((rp.rpy_server_submit(srv, k, pos, f, sy.s, u), sy.n, u))
-        t0 = time.perf_counter()
-        lat, beads = [], 0
-        for rid, nb, u in outs:
-            st, l = rp.rpy_server_wait(srv, rid)
-            if st == 0:
-                lat.append(l)
-                beads += nb
-        return lat, beads
+    def summarise(wall, recs):
+        ok = [r for r in recs if r[0] == 0]
+        lat = np.array([r[1] for r in ok])
+        nb = sum(systems[r[2]].n for r in ok)
+        ph = {key: round(float(np.mean([r[3][key] for r in ok])), 3) for key in
+              ("queue_ms", "run_ms", "h2d_ms", "build_ms", "matvec_ms", "d2h_ms")}
+        return {"requests": len(recs), "failed": len(recs) - len(ok), "req_s": round(len(recs) / wall, 3),
+                "Mbeads_s": round(nb / wall / 1e6, 3), "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                "p99_ms": round(float(np.percentile(lat, 99)), 2), "mean_phase_ms": ph}
 
-    # warm every system once (first admission builds its tree), then capacity from a closed loop
-    run(len(systems), 0, order=list(range(len(systems))))
-    t0 = time.perf_counter()
-    lat, beads = run(args.serve_requests, 0)
-    wall = time.perf_counter() - t0
-    cap_rps = args.serve_requests / wall
-    out = {"mode": "serve", "metric": "served RPY matvec Mbeads/s (mixed 3-digit FP32 / 6-digit FP64)",
-           "unit": "Mbeads/s", "systems": len(systems), "slots": args.serve_slots,
-           "total_beads": int(sum(sy.n for sy in systems)), "capacity_req_s": round(cap_rps, 3),
-           "closed_loop": {"Mbeads_s": round(beads / wall / 1e6, 3), "p50_ms": round(float(np.percentile(lat, 50)), 2),
-                           "p99_ms": round(float(np.percentile(lat, 99)), 2)}, "rates": []}
-    for frac in (0.3, 0.5, 0.7, 0.9):
-        t0 = time.perf_counter()
-        lat, beads = run(args.serve_requests, frac * cap_rps)
-        wall = time.perf_counter() - t0
-        out["rates"].append({"load": frac, "req_s": round(args.serve_requests / wall, 3),
-                             "Mbeads_s": round(beads / wall / 1e6, 3), "p50_ms": round(float(np.percentile(lat, 50)), 2),
-                             "p99_ms": round(float(np.percentile(lat, 99)), 2)})
+    order = [int(x) for x in rng.integers(nsys, size=max(256, n_req // 4))]
+    wall, recs = cl.run(order, 0, rng)
+    closed = summarise(wall, recs)
+    cap = closed["req_s"]
+    out = {"workload": f"{nsys} resident systems, log-uniform 1e4..2e6 beads (seed 5), half cube / half sphere, "
+                       "a = 0.5 N^(-1/3); per request jittered positions (sigma 1e-3) and fresh N(0,1) forces; "
+                       "3-digit FP32 and 6-digit FP64 systems alternating",
+           "unit": "Mbeads/s", "systems": nsys, "total_beads": int(beads.sum()), "slots": args.serve_slots,
+           "serial_bound_Mbeads_s": round(serial_bound, 3), "kernel_bound_Mbeads_s": round(kernel_bound, 3),
+           "closed_loop": closed,
+           "closed_loop_vs_serial_bound": round(closed["Mbeads_s"] / serial_bound, 3),
+           "closed_loop_vs_kernel_bound": round(closed["Mbeads_s"] / kernel_bound, 3), "loads": []}
+    for frac in loads:
+        order = [int(x) for x in rng.integers(nsys, size=n_req)]
+        wall, recs = cl.run(order, frac * cap, rng)
+        out["loads"].append(dict(load=frac, **summarise(wall, recs)))
     out["server"] = {k: v for k, v in rp.rpy_server_stats_get(srv).items() if k in
                      ("completed", "failed", "evictions", "rebuilds", "peak_resident_bytes", "resident_systems")}
     rp.rpy_server_destroy(srv)
+    return out
+
+
+def serve(args, local):
+    out = serving(args, local, loads=(0.3, 0.5, 0.7, 0.9))
+    out.update({"mode": "serve", "metric": "served RPY matvec Mbeads/s (mixed 3-digit FP32 / 6-digit FP64)"})
     return out
 
 
@@ -581,7 +656,8 @@ def main():
                          "e.g. to profile the autotuned configuration")
     ap.add_argument("--mode", default="bench", choices=["bench", "serve", "bd"])
     ap.add_argument("--serve-systems", type=int, default=64)
-    ap.add_argument("--serve-requests", type=int, default=64, help="requests per arrival rate")
+    ap.add_argument("--serve-requests", type=int, default=1000, help="requests per arrival rate")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement of the default run")
     ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     ws, rank, local = _dist()
@@ -653,6 +729,11 @@ def main():
                 "note": "same workload and digit setting: P2P in FP32 with compensated (Kahan) sums, translations "
                         "in FP32 with every expansion's fourth charge set about its own box centre; bounding "
                         "cube, Morton keys, r ~ 0 pairs and per-bead sums in FP64"}
+        if not args.no_serve and args.config == DEFAULT and ws == 1:
+            # the serving form (BASELINE metric: p50 / p99 latency served), after the timed steps
+            t0 = time.perf_counter()
+            result["serving"] = serving(args, local, loads=(0.7,))
+            result["serving"]["wall_s"] = round(time.perf_counter() - t0, 1)
         result["cpu_baseline"] = {"value": round(len(tg) / dt / 1e6, 6), "unit": "Mbeads/s", "cores": th,
                                   "kind": "oracle", "host": host_cpu(),
                                   "sample": (f"all {sysm.n} beads (full direct sum)" if len(tg) == sysm.n else

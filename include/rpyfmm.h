@@ -134,7 +134,10 @@ typedef struct {
 } rpy_stats;
 
 /*
- * Build an adaptive octree over N beads and all interaction lists.
+ * Build an adaptive octree over N beads and all interaction lists: the tree of
+ * the paper's evaluate(sources, targets, threshold, method, accuracy) call
+ * (Sec. 4.2), with `threshold` the refinement limit (leaf_cap: a box splits
+ * while it holds more beads) and `accuracy` the digit setting (Sec. 4.3).
  *   pos_dev   device, n x 3 FP64, caller order
  *   n         number of beads, >= 1
  *   a         bead radius, > 0 and finite
@@ -166,12 +169,17 @@ int rpy_forest_build(const double *pos_dev, const int64_t *sys_offsets, int nsys
 /*
  * Rebuild the tree of `t` for new positions of the same beads (same N, same
  * systems, same radii and parameters), reusing its device buffers where they
- * fit.  Used between Brownian-dynamics steps.  Synchronises `stream`.
+ * fit.  Used between Brownian-dynamics steps: the Ermak-McCammon update of
+ * Sec. 1 moves every bead, and D of the next step is the tensor at the new
+ * positions.  Synchronises `stream`.
  */
 int rpy_tree_update_positions(rpy_tree t, const double *pos_dev, void *stream);
 
 /*
- * u = D F for every bead of the tree (the hot path).  From the second call on
+ * u = D F for every bead of the tree (the hot path): D the RPY tensor of
+ * Sec. 1 (self term, r >= 2a far branch, r < 2a overlap branch), pairs of
+ * adjacent leaves summed directly and all others through the four Laplace
+ * potentials of Sec. 2 combined by Eq. 2.8.  From the second call on
  * the same build, the body of the matvec (everything after the force gather
  * and before the final combine) is replayed as a CUDA graph captured once on
  * a stream owned by the tree (unless RPY_FLAG_NO_GRAPH or profiling is on).
@@ -226,7 +234,9 @@ int rpy_tree_matvec_host(rpy_tree t, const double *pos_host, const double *f_hos
 
 /*
  * One-shot form with the paper's argument list (positions, radius, forces,
- * kT/eta, accuracy digits): builds a tree, applies it once, frees it.
+ * kT/eta, accuracy digits; the Bead / kparams interface of Sec. 4.2): u = D F
+ * with D the tensor of Sec. 1 split as in Sec. 2; builds a tree, applies it
+ * once, frees it.
  * All arrays are device arrays.  Synchronises `stream`.
  */
 int rpy_matvec_oneshot(const double *pos_dev, int64_t n, double a, const double *f_dev,
@@ -483,8 +493,12 @@ int rpy_alu_peak(int precision, double *flops_per_s, void *stream);
  *             rpy_tree_build uses (side NaN if a position is not finite)
  * Scratch is a fixed file-scope device array (about 230 KB) that every GPU
  * loading the library holds until exit.  The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress, no allocation); make
- * the first call before any stream capture.  All calls share the array:
+ * that array's device address (cudaGetSymbolAddress, no allocation) and keeps
+ * it for the life of the process; make the first call before any stream
+ * capture, and do not call this entry point after a cudaDeviceReset of that
+ * device in the same process (the kept address would be stale).  NULL
+ * pointers and n < 1 give RPY_ERR_INVALID with a message in
+ * rpy_last_cuda_error().  All calls share the array:
  * calls that overlap on the GPU (different streams, no ordering) race and
  * give wrong cubes.  Asynchronous on `stream`; allocates nothing.
  */
@@ -541,13 +555,29 @@ int rpy_server_create(const rpy_server_params *params, rpy_server *out);
 int rpy_server_add_system(rpy_server s, const double *pos_host, int64_t n, double a,
                           const rpy_build_params *params, int *system_id);
 /* Enqueue u = D(pos) f for a system.  pos_host may be NULL (keep the last positions).
- * Returns at once with a request id; the result lands in u_host. */
+ * pos_host and f_host are copied into page-locked buffers of the server before the
+ * call returns (the caller may reuse them at once); returns a request id; the result
+ * lands in u_host (page-locked memory there copies back fastest).  RPY_ERR_OOM when
+ * no page-locked host memory is left for the copies. */
 int rpy_server_submit(rpy_server s, int system_id, const double *pos_host, const double *f_host,
                       double kT_over_eta, double *u_host, int64_t *request_id);
 /* Wait for a request; timeout_ms < 0 waits forever.  Returns the request's own
  * status (RPY_OK, an error of its computation, RPY_ERR_STATE if cancelled) or
  * RPY_ERR_TIMEOUT if it is still pending.  latency_ms may be NULL. */
 int rpy_server_wait(rpy_server s, int64_t request_id, int timeout_ms, double *latency_ms);
+/* Per-request timing, filled by rpy_server_wait_times: host wall time in the queue and
+ * on a worker, and the device time of each phase on the worker's stream. */
+typedef struct {
+    double queue_ms;    /* submit -> start on a worker */
+    double run_ms;      /* start -> completion */
+    double h2d_ms;      /* host-to-device copies of positions (if new) and forces */
+    double build_ms;    /* tree build or rebuild for new positions (0 when they were kept) */
+    double matvec_ms;   /* the matvec */
+    double d2h_ms;      /* device-to-host copy of the velocities */
+} rpy_request_times;
+/* rpy_server_wait, also returning the request's phase times (times may be NULL). */
+int rpy_server_wait_times(rpy_server s, int64_t request_id, int timeout_ms, double *latency_ms,
+                          rpy_request_times *times);
 /* Cancel a request that has not started; RPY_ERR_STATE if it already started or finished. */
 int rpy_server_cancel(rpy_server s, int64_t request_id);
 /* Wait until every submitted request has finished. */

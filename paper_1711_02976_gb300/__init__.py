@@ -48,7 +48,7 @@ EXPORTED_SYMBOLS = [
     "rpy_last_cuda_error", "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times",
     "rpy_launch_count", "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_server_create", "rpy_server_add_system",
     "rpy_server_submit", "rpy_server_wait", "rpy_server_cancel", "rpy_server_drain", "rpy_server_stats_get",
-    "rpy_server_destroy", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt", "rpy_bd_step", "rpy_evaluate",
+    "rpy_server_destroy", "rpy_server_wait_times", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt", "rpy_bd_step", "rpy_evaluate",
     "rpy_matvec_batched", "rpy_tree_work", "rpy_tree_matvec_host",
 ]
 STAGES = ["gather", "p2p", "p2m", "m2m", "m2x", "x2x", "x2l", "p2l", "l2l", "eval", "combine"]
@@ -104,6 +104,11 @@ class AutotuneResult(ctypes.Structure):
 
 class ServerParams(ctypes.Structure):
     _fields_ = [("device_budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class RequestTimes(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("h2d_ms", ctypes.c_double),
+                ("build_ms", ctypes.c_double), ("matvec_ms", ctypes.c_double), ("d2h_ms", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
@@ -172,6 +177,7 @@ def load(build_if_missing: bool = True):
             "rpy_server_add_system": [vp, vp, i64, d, ctypes.POINTER(BuildParams), ctypes.POINTER(i)],
             "rpy_server_submit": [vp, i, vp, vp, d, vp, ctypes.POINTER(i64)],
             "rpy_server_wait": [vp, i64, i, ctypes.POINTER(d)],
+            "rpy_server_wait_times": [vp, i64, i, ctypes.POINTER(d), ctypes.POINTER(RequestTimes)],
             "rpy_server_cancel": [vp, i64],
             "rpy_server_drain": [vp],
             "rpy_server_stats_get": [vp, ctypes.POINTER(ServerStats)],
@@ -554,6 +560,15 @@ def rpy_server_wait(server, request_id, timeout_ms=-1):
     lat = ctypes.c_double()
     st = load().rpy_server_wait(ctypes.c_void_p(server), int(request_id), int(timeout_ms), ctypes.byref(lat))
     return st, lat.value
+
+
+def rpy_server_wait_times(server, request_id, timeout_ms=-1):
+    """Returns (status, latency_ms, {queue_ms, run_ms, h2d_ms, build_ms, matvec_ms, d2h_ms})."""
+    lat = ctypes.c_double()
+    tm = RequestTimes()
+    st = load().rpy_server_wait_times(ctypes.c_void_p(server), int(request_id), int(timeout_ms), ctypes.byref(lat),
+                                      ctypes.byref(tm))
+    return st, lat.value, {k: getattr(tm, k) for k, _ in RequestTimes._fields_}
 
 
 def rpy_server_cancel(server, request_id) -> int:

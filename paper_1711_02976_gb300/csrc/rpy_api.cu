@@ -949,7 +949,14 @@ int rpy_tree_stage_times(rpy_tree h, double *ms, int n) {
 int64_t rpy_launch_count(void) { return g_launches.load(); }
 
 int rpy_bounding_cube_noalloc(const double *pos_dev, int64_t n, double *cube_dev, void *stream) {
-    if (!pos_dev || !cube_dev || n < 1) return RPY_ERR_INVALID;
+    if (!pos_dev || !cube_dev) {
+        set_last_error("rpy_bounding_cube_noalloc: pos_dev and cube_dev must be device pointers, not NULL");
+        return RPY_ERR_INVALID;
+    }
+    if (n < 1) {
+        set_last_error("rpy_bounding_cube_noalloc: n must be at least 1");
+        return RPY_ERR_INVALID;
+    }
     RPY_TRY(have_device());
     return bounding_cube_noalloc(pos_dev, n, cube_dev, static_cast<cudaStream_t>(stream));
 }

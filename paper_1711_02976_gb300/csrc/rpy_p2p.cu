@@ -1,9 +1,10 @@
 // Near field: direct RPY tensor (Sec. 1) over the U list of every leaf, the
 // self term, and the final combine / unpermute of the matvec.
 //
-// One CTA per target leaf; its beads are the threads.  Source leaves of the U
-// list are staged through shared memory in chunks of blockDim beads
-// (coalesced SoA loads), and every thread sums its own target.
+// One CTA per work item: up to 256 target beads of one leaf (large leaves are
+// split into several items, launched in decreasing order of cost).  The beads of
+// the leaf's source boxes are staged through shared memory in chunks (coalesced
+// SoA loads) and every thread sums its own targets.
 //
 // Pair blocks (R = r_i - r_j, s = kT/eta):
 //   r >= 2a : s/(8 pi r) [ (1 + 2a^2/(3r^2)) F + (1 - 2a^2/r^2) (R.F)/r^2 R ]
@@ -15,11 +16,11 @@
 // one Newton-Raphson step for the reciprocal square root (y <- y (3 - r2 y^2)/2),
 // which brings the relative error from ~1e-7 to ~1e-14.
 // FP32 form (precision setting, k_p2p32): positions relative to the target
-// leaf centre in FP32; every thread carries two targets in the two lanes of the
-// paired FP32 instructions (one instruction evaluates the pair term for both);
-// accumulation is Kahan-compensated across blocks of kP32Block sources; pairs
-// closer than 1e-3 a (where the FP32 difference of coordinates loses the
-// direction) are recomputed in FP64 from the FP64 positions.
+// leaf centre in FP32; every thread carries two targets as two independent
+// scalar FP32 chains per staged source; both branches are evaluated without
+// divergence; accumulation is Kahan-compensated across blocks of kP32Block
+// sources; pairs closer than 1e-3 a (where the FP32 difference of coordinates
+// loses the direction) are recomputed in FP64 from the FP64 positions.
 #include <cmath>
 
 #include <mutex>

@@ -8,6 +8,12 @@
 // or fits the memory budget (idle resident systems are evicted, least
 // recently used first).  Requests of different systems therefore run at the
 // same time on the device; requests of one system keep their order.
+//
+// Host data lives in page-locked (pinned) buffers from a pool owned by the
+// server: a submit copies the caller's positions and forces into pinned
+// buffers, so the worker's host-to-device copies run at full bus speed and the
+// caller may reuse its arrays at once; a system's last good positions (needed
+// to rebuild it after an eviction or a failed request) stay in a pinned buffer.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -24,11 +30,45 @@ namespace rpy {
 
 using clk = std::chrono::steady_clock;
 
+// Page-locked host buffers, reused by size.
+struct PinnedPool {
+    std::mutex mu;
+    std::multimap<size_t, double *> free_;
+    std::vector<double *> all;
+    double *get(size_t count) {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto it = free_.find(count);
+            if (it != free_.end()) {
+                double *p = it->second;
+                free_.erase(it);
+                return p;
+            }
+        }
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, sizeof(double) * count, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        all.push_back(static_cast<double *>(p));
+        return static_cast<double *>(p);
+    }
+    void put(double *p, size_t count) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(mu);
+        free_.emplace(count, p);
+    }
+    ~PinnedPool() {
+        for (double *p : all) cudaFreeHost(p);
+    }
+};
+
 struct SrvSystem {
     int64_t n = 0;
     double a = 0;
     rpy_build_params params{};
-    std::vector<double> pos;           // last positions (host)
+    double *pos = nullptr;             // last good positions (pinned host, 3 n)
     rpy_tree tree = nullptr;           // resident when non-null
     double *d_buf = nullptr;           // positions, forces, velocities: 9 n doubles
     int64_t bytes = 0;                 // device bytes held (estimate until built)
@@ -41,17 +81,19 @@ struct SrvSystem {
 struct SrvRequest {
     int64_t id = 0;
     int sys = 0;
-    std::vector<double> pos;           // empty: keep the system's positions
-    std::vector<double> f;
+    double *pos = nullptr;             // pinned copy of new positions, or null: keep the system's
+    double *f = nullptr;               // pinned copy of the forces
     double s = 0;
     double *u_host = nullptr;
-    clk::time_point t_submit, t_done;
+    clk::time_point t_submit, t_start, t_done;
+    rpy_request_times times{};
     enum { QUEUED, RUNNING, DONE } state = QUEUED;
     int status = RPY_OK;
 };
 
 struct Server {
     rpy_server_params prm{};
+    PinnedPool pinned;                 // destroyed last: requests and systems return into it
     int device = 0;
     int64_t budget = 0;
     std::mutex mu;
@@ -71,6 +113,14 @@ struct Server {
     clk::time_point first_submit, last_done;
     bool any_submit = false;
 };
+
+// Return a finished request's pinned buffers (its positions only when not kept by the system).
+static void release_buffers(Server &S, SrvRequest &r, int64_t n) {
+    S.pinned.put(r.f, 3 * size_t(n));
+    r.f = nullptr;
+    S.pinned.put(r.pos, 3 * size_t(n));
+    r.pos = nullptr;
+}
 
 // Free a resident system's device state (caller holds no lock; the system is not busy).
 static void drop_device_state(SrvSystem &sy) {
@@ -122,13 +172,31 @@ static std::shared_ptr<SrvRequest> pick(Server &S, std::vector<SrvSystem *> &evi
         }
         sy.busy = true;
         r->state = SrvRequest::RUNNING;
+        r->t_start = clk::now();
         S.queue.erase(it);
         return r;
     }
     return nullptr;
 }
 
-static int run_request(Server &S, SrvSystem &sy, SrvRequest &r, cudaStream_t st) {
+// Events of one worker between the phases of a request (device time of each phase).
+struct PhaseEvents {
+    cudaEvent_t e[6] = {};
+    bool ok = true;
+    PhaseEvents() {
+        for (auto &x : e) ok = ok && cudaEventCreate(&x) == cudaSuccess;
+    }
+    ~PhaseEvents() {
+        for (auto &x : e)
+            if (x) cudaEventDestroy(x);
+    }
+    double ms(int a, int b) const {
+        float v = 0.f;
+        return ok && cudaEventElapsedTime(&v, e[a], e[b]) == cudaSuccess ? double(v) : 0.0;
+    }
+};
+
+static int run_request(Server &S, SrvSystem &sy, SrvRequest &r, cudaStream_t st, PhaseEvents &ev) {
     int64_t n = sy.n;
     bool fresh = false;
     if (!sy.d_buf) {
@@ -136,9 +204,12 @@ static int run_request(Server &S, SrvSystem &sy, SrvRequest &r, cudaStream_t st)
         fresh = true;
     }
     double *dp = sy.d_buf, *df = sy.d_buf + 3 * n, *du = sy.d_buf + 6 * n;
-    const double *pos = r.pos.empty() ? sy.pos.data() : r.pos.data();
-    if (!r.pos.empty() || fresh || sy.needs_build) {
-        RPY_CHECK(cudaMemcpyAsync(dp, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    const double *pos = r.pos ? r.pos : sy.pos;
+    const bool build = r.pos || fresh || sy.needs_build;
+    if (ev.ok) RPY_CHECK(cudaEventRecord(ev.e[0], st));
+    if (build) RPY_CHECK(cudaMemcpyAsync(dp, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    if (ev.ok) RPY_CHECK(cudaEventRecord(ev.e[1], st));
+    if (build) {
         if (sy.tree) {
             RPY_TRY(rpy_tree_update_positions(sy.tree, dp, st));
             S.st.rebuilds++;
@@ -148,15 +219,26 @@ static int run_request(Server &S, SrvSystem &sy, SrvRequest &r, cudaStream_t st)
         }
         sy.needs_build = false;
     }
-    RPY_CHECK(cudaMemcpyAsync(df, r.f.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    if (ev.ok) RPY_CHECK(cudaEventRecord(ev.e[2], st));
+    RPY_CHECK(cudaMemcpyAsync(df, r.f, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    if (ev.ok) RPY_CHECK(cudaEventRecord(ev.e[3], st));
     RPY_TRY(rpy_matvec(sy.tree, df, r.s, du, st));
+    if (ev.ok) RPY_CHECK(cudaEventRecord(ev.e[4], st));
     RPY_CHECK(cudaMemcpyAsync(r.u_host, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    if (ev.ok) RPY_CHECK(cudaEventRecord(ev.e[5], st));
     RPY_CHECK(cudaStreamSynchronize(st));
+    if (ev.ok) {
+        r.times.h2d_ms = ev.ms(0, 1) + ev.ms(2, 3);
+        r.times.build_ms = build ? ev.ms(1, 2) : 0.0;
+        r.times.matvec_ms = ev.ms(3, 4);
+        r.times.d2h_ms = ev.ms(4, 5);
+    }
     return RPY_OK;
 }
 
 static void worker(Server *S, cudaStream_t st) {
     cudaSetDevice(S->device);
+    PhaseEvents ev;
     for (;;) {
         std::shared_ptr<SrvRequest> r;
         std::vector<SrvSystem *> evict;
@@ -177,7 +259,7 @@ static void worker(Server *S, cudaStream_t st) {
             v->busy = false;
         }
         SrvSystem &sy = S->systems[r->sys];
-        int status = run_request(*S, sy, *r, st);
+        int status = run_request(*S, sy, *r, st, ev);
         int64_t real = 0;
         if (sy.tree) {
             rpy_stats s{};
@@ -193,11 +275,13 @@ static void worker(Server *S, cudaStream_t st) {
             S->resident += real - sy.bytes;
             sy.bytes = real;
             S->peak = std::max(S->peak, S->resident);
-            if (status == RPY_OK && !r->pos.empty()) sy.pos.swap(r->pos);
+            if (status == RPY_OK && r->pos) std::swap(sy.pos, r->pos);   // the new last good positions
             sy.busy = false;
             sy.last_use = ++S->tick;
             r->status = status;
             r->t_done = clk::now();
+            r->times.queue_ms = std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count();
+            r->times.run_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_start).count();
             r->state = SrvRequest::DONE;
             S->running--;
             if (status == RPY_OK) {
@@ -208,9 +292,8 @@ static void worker(Server *S, cudaStream_t st) {
                 S->st.failed++;
             }
             S->last_done = r->t_done;
-            r->f.clear();
-            r->f.shrink_to_fit();
         }
+        release_buffers(*S, *r, sy.n);
         S->cv_done.notify_all();
         S->cv_work.notify_all();
     }
@@ -278,12 +361,18 @@ int rpy_server_add_system(rpy_server h, const double *pos_host, int64_t n, doubl
     sy.n = n;
     sy.a = a;
     sy.params = *params;
-    sy.pos.assign(pos_host, pos_host + 3 * n);
     int64_t fp = 0;
     RPY_TRY(rpy_tree_footprint(n, params->digits, params->precision, params->leaf_cap, &fp));
     sy.est = fp + int64_t(sizeof(double)) * 9 * n;
+    {
+        std::lock_guard<std::mutex> lk(S.mu);
+        if (sy.est > S.budget) return RPY_ERR_OOM;
+    }
+    cudaSetDevice(S.device);
+    sy.pos = S.pinned.get(3 * size_t(n));
+    if (!sy.pos) return RPY_ERR_OOM;
+    std::memcpy(sy.pos, pos_host, sizeof(double) * 3 * size_t(n));
     std::lock_guard<std::mutex> lk(S.mu);
-    if (sy.est > S.budget) return RPY_ERR_OOM;
     S.systems.push_back(std::move(sy));
     *system_id = int(S.systems.size()) - 1;
     return RPY_OK;
@@ -301,8 +390,15 @@ int rpy_server_submit(rpy_server h, int system_id, const double *pos_host, const
     }
     int64_t n = S.systems[system_id].n;
     r->sys = system_id;
-    if (pos_host) r->pos.assign(pos_host, pos_host + 3 * n);
-    r->f.assign(f_host, f_host + 3 * n);
+    cudaSetDevice(S.device);
+    r->f = S.pinned.get(3 * size_t(n));
+    if (pos_host) r->pos = S.pinned.get(3 * size_t(n));
+    if (!r->f || (pos_host && !r->pos)) {
+        release_buffers(S, *r, n);
+        return RPY_ERR_OOM;
+    }
+    std::memcpy(r->f, f_host, sizeof(double) * 3 * size_t(n));
+    if (pos_host) std::memcpy(r->pos, pos_host, sizeof(double) * 3 * size_t(n));
     r->s = kT_over_eta;
     r->u_host = u_host;
     r->t_submit = clk::now();
@@ -322,7 +418,8 @@ int rpy_server_submit(rpy_server h, int system_id, const double *pos_host, const
     return RPY_OK;
 }
 
-int rpy_server_wait(rpy_server h, int64_t request_id, int timeout_ms, double *latency_ms) {
+int rpy_server_wait_times(rpy_server h, int64_t request_id, int timeout_ms, double *latency_ms,
+                          rpy_request_times *times) {
     if (!h) return RPY_ERR_INVALID;
     Server &S = h->S;
     std::unique_lock<std::mutex> lk(S.mu);
@@ -333,9 +430,14 @@ int rpy_server_wait(rpy_server h, int64_t request_id, int timeout_ms, double *la
     if (timeout_ms < 0) S.cv_done.wait(lk, done);
     else if (!S.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) return RPY_ERR_TIMEOUT;
     if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    if (times) *times = r->times;
     int status = r->status;
     S.reqs.erase(request_id);
     return status;
+}
+
+int rpy_server_wait(rpy_server h, int64_t request_id, int timeout_ms, double *latency_ms) {
+    return rpy_server_wait_times(h, request_id, timeout_ms, latency_ms, nullptr);
 }
 
 int rpy_server_cancel(rpy_server h, int64_t request_id) {
@@ -352,6 +454,7 @@ int rpy_server_cancel(rpy_server h, int64_t request_id) {
         r->status = RPY_ERR_STATE;
         r->t_done = clk::now();
         S.st.cancelled++;
+        release_buffers(S, *r, S.systems[r->sys].n);
     }
     S.cv_done.notify_all();
     S.cv_work.notify_all();
@@ -401,6 +504,7 @@ void rpy_server_destroy(rpy_server h) {
             r->state = SrvRequest::DONE;
             r->status = RPY_ERR_STATE;
             S.st.cancelled++;
+            release_buffers(S, *r, S.systems[r->sys].n);
         }
         S.queue.clear();
         S.stop = true;
@@ -411,7 +515,7 @@ void rpy_server_destroy(rpy_server h) {
     cudaSetDevice(S.device);
     for (auto &sy : S.systems) drop_device_state(sy);
     for (cudaStream_t q : S.streams) cudaStreamDestroy(q);
-    delete h;
+    delete h;   // the pinned pool (every system's positions and the requests' buffers) goes last
 }
 
 }  // extern "C"

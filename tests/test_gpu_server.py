@@ -42,8 +42,17 @@ def test_results_in_the_mix_equal_results_alone():
             rid = rp.rpy_server_submit(srv, ids[k], newpos, f, 6 * math.pi * a, u)
             jobs.append((rid, k, newpos, f, u))
         last_pos = [s[0] for s in systems]
-        for rid, k, newpos, f, u in jobs:
-            st, lat = rp.rpy_server_wait(srv, rid)
+        for i, (rid, k, newpos, f, u) in enumerate(jobs):
+            if i % 2:
+                st, lat = rp.rpy_server_wait(srv, rid)
+            else:
+                st, lat, tm = rp.rpy_server_wait_times(srv, rid)
+                # phase times: device time of each phase inside the worker's wall time
+                assert tm["matvec_ms"] > 0 and tm["h2d_ms"] > 0 and tm["d2h_ms"] > 0
+                if newpos is not None:
+                    assert tm["build_ms"] > 0   # new positions: the tree is rebuilt
+                assert tm["h2d_ms"] + tm["build_ms"] + tm["matvec_ms"] + tm["d2h_ms"] <= tm["run_ms"] + 1.0
+                assert tm["queue_ms"] + tm["run_ms"] <= lat + 1.0
             assert st == 0 and lat > 0
             pos, a, d, prec = systems[k]
             if newpos is not None:

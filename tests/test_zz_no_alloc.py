@@ -34,6 +34,30 @@ def test_bounding_cube_noalloc_limits():
     with pytest.raises(rp.RpyError) as e:
         rp.rpy_bounding_cube_noalloc(P, 33_554_433, cube)
     assert e.value.status == -1 and "33554432" in str(e.value)
+    with pytest.raises(rp.RpyError) as e:
+        rp.rpy_bounding_cube_noalloc(P, 0, cube)
+    assert e.value.status == -1 and "at least 1" in str(e.value)
+    with pytest.raises(rp.RpyError) as e:
+        rp.rpy_bounding_cube_noalloc(None, 4, cube)
+    assert e.value.status == -1 and "NULL" in str(e.value)
     P[2, 1] = float("nan")
     rp.rpy_bounding_cube_noalloc(P, 4, cube)
     assert np.isnan(cube.cpu().numpy()[3])
+
+
+def test_bounding_cube_noalloc_allocates_nothing():
+    """The entry point's promise: after its first call on the device (the one-time
+    lookup of the fixed array's address), a call leaves the device's free memory
+    exactly as it was."""
+    import torch
+    n = 1_000_003
+    P = torch.rand((n, 3), dtype=torch.float64, device="cuda")
+    cube = torch.empty(4, dtype=torch.float64, device="cuda")
+    rp.rpy_bounding_cube_noalloc(P, n, cube)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        rp.rpy_bounding_cube_noalloc(P, n, cube)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
