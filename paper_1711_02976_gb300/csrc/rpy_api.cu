@@ -201,6 +201,13 @@ static void pack_tables(const OpTables &h, std::vector<char> &blob, std::vector<
     putT(h.shz);      // 35
     putT(h.shx);      // 36
     putT(h.shy);      // 37
+    {                 // 38: shift rows padded to an even length
+        const int S = h.S, Sp = (S + 1) & ~1;
+        std::vector<double> v(size_t(216) * Sp * 2, 0.0);
+        for (int o = 0; o < 216; ++o)
+            for (int e = 0; e < 2 * S; ++e) v[size_t(o) * Sp * 2 + e] = h.shift[size_t(o) * S * 2 + e];
+        putT(v);
+    }
 }
 
 template <typename T>
@@ -251,6 +258,8 @@ static DevTables<T> bind_tables(const OpTables &h, char *base, const std::vector
     d.shz = reinterpret_cast<const T *>(base + o[35]);
     d.shx = reinterpret_cast<const cpx<T> *>(base + o[36]);
     d.shy = reinterpret_cast<const cpx<T> *>(base + o[37]);
+    d.shiftp = reinterpret_cast<const cpx<T> *>(base + o[38]);
+    d.Sp = (h.S + 1) & ~1;
     return d;
 }
 
@@ -793,6 +802,7 @@ int rpy_tree_sync(rpy_tree h) {
     unsigned status = 0;
     RPY_CHECK(cudaMemcpy(&status, t.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (status & DEVERR_NONFINITE) return RPY_ERR_NONFINITE;
+    if (status & DEVERR_TIMEOUT) return RPY_ERR_TIMEOUT;
     if (status) return RPY_ERR_INTERNAL;
     return RPY_OK;
 }

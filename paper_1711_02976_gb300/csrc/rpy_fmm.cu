@@ -265,8 +265,9 @@ __global__ void k_p2x(int b0, int nb, DevTables<T> D, const int *beg, const int 
     Rec<T> R = load_rec(D, smr);
     cpx<T> *ybuf = reinterpret_cast<cpx<T> *>(smr + ((rec_floats<T>(p) + 1) & ~1));
     cpx<T> *acc = ybuf + kChunkB * nc;
-    T *q = reinterpret_cast<T *>(acc + kSets * nc);
-    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) acc[i] = mk<T>(0, 0);
+    cpx<T> *cmp = acc + kSets * nc;   // FP32: compensation of the running sums
+    T *q = reinterpret_cast<T *>(cmp + kSets * nc);
+    for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) acc[i] = cmp[i] = mk<T>(0, 0);
     int sy = bsys[b];
     double cx = ctr[3 * b], cy = ctr[3 * b + 1], cz = ctr[3 * b + 2];
     const double c0x = rb ? cx : sc.cube[4 * sy], c0y = rb ? cy : sc.cube[4 * sy + 1],
@@ -304,14 +305,28 @@ __global__ void k_p2x(int b0, int nb, DevTables<T> D, const int *beg, const int 
             __syncthreads();
             for (int e = threadIdx.x; e < kSets * nc; e += blockDim.x) {
                 int k = e / nc, i = e - k * nc;
-                cpx<T> a = acc[e];
+                cpx<T> a = sizeof(T) == 4 ? mk<T>(0, 0) : acc[e];
                 for (int t = 0; t < cnt; ++t) {
                     cpx<T> yv = ybuf[t * nc + i];
                     T qq = q[4 * t + k];
                     a.x += qq * yv.x;
                     a.y -= qq * yv.y;   // conj
                 }
-                acc[e] = a;
+                if constexpr (sizeof(T) == 4) {
+                    // a leaf (or an X-list source) may hold hundreds to thousands of beads: the
+                    // chunk's plain sum enters the running sum by compensated (Kahan) addition
+                    cpx<T> sum = acc[e], c = cmp[e];
+                    const T yx = a.x - c.x, tx = sum.x + yx;
+                    c.x = (tx - sum.x) - yx;
+                    sum.x = tx;
+                    const T yy = a.y - c.y, ty = sum.y + yy;
+                    c.y = (ty - sum.y) - yy;
+                    sum.y = ty;
+                    acc[e] = sum;
+                    cmp[e] = c;
+                } else {
+                    acc[e] = a;
+                }
             }
             __syncthreads();
         }
@@ -561,11 +576,14 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int b = b0 + blockIdx.x;
     const int p = D.p, nc = ncoef(p), s = D.s, S = D.S, P1 = p + 1;
+    // A per node k: [P1][4 sets] at stride NS = 4 P1 + 1, so that the units of
+    // neighbouring nodes in one warp read different shared-memory banks
+    const int NS = kSets * P1 + 1;
     cpx<T> *Mw = reinterpret_cast<cpx<T> *>(smem_raw);
     cpx<T> *Mf = Mw + kSets * nc;
-    cpx<T> *AE = Mf + kSets * nc;       // [s][P1][4 sets]
-    cpx<T> *AO = AE + kSets * s * P1;
-    cpx<T> *Tm = AO + kSets * s * P1;   // rotation scratch
+    cpx<T> *AE = Mf + kSets * nc;       // [s][NS]
+    cpx<T> *AO = AE + s * NS;
+    cpx<T> *Tm = AO + s * NS;           // rotation scratch
     const cpx<T> *src = M + size_t(b) * kSets * nc;
     for (int i = threadIdx.x; i < kSets * nc; i += blockDim.x) Mw[i] = src[i];
     __syncthreads();
@@ -601,8 +619,8 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
                     ody = fma(cc[i], Ms[i].y, ody);
                 }
                 const T sg = m == 0 ? T(1) : (((m >> 1) & 1) ? T(-2) : T(2));   // 2 i^m up to i for odd m
-                AE[(k * P1 + m) * kSets + st] = mk(sg * evx, sg * evy);
-                AO[(k * P1 + m) * kSets + st] = mk(sg * odx, sg * ody);
+                AE[k * NS + m * kSets + st] = mk(sg * evx, sg * evy);
+                AO[k * NS + m * kSets + st] = mk(sg * odx, sg * ody);
             }
         }
         __syncthreads();
@@ -621,8 +639,8 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
                 const bool pair = t > 0 && 2 * t != H;
                 const int ja = j0 + t, jb = j0 + H - t;
                 const cpx<T> *rt = D.roots + 2 * j0;
-                const cpx<T> *ae = AE + k * P1 * kSets;
-                const cpx<T> *ao = AO + k * P1 * kSets;
+                const cpx<T> *ae = AE + k * NS;
+                const cpx<T> *ao = AO + k * NS;
                 const T wm = D.e_wm[ja];
                 T pe[kSets], qe[kSets], po[kSets], qo[kSets];
     #pragma unroll
@@ -700,8 +718,8 @@ __global__ void k_m2x(int b0, int nb, DevTables<T> D, const cpx<T> *M, cpx<T> *X
                 const int k = D.e_k[j];
                 const int j0 = D.k_start[k], jl = j - j0, Mk = 2 * (D.k_start[k + 1] - j0);
                 const cpx<T> *rt = D.roots + 2 * j0;
-                const cpx<T> *ae = AE + k * P1 * kSets;
-                const cpx<T> *ao = AO + k * P1 * kSets;
+                const cpx<T> *ae = AE + k * NS;
+                const cpx<T> *ao = AO + k * NS;
                 T er[kSets], orr[kSets], ei[kSets], oi[kSets];
     #pragma unroll
                 for (int st = 0; st < kSets; ++st) {
@@ -1016,6 +1034,238 @@ __global__ void k_x2x4(const int *parents, DevTables<T> D, const int *coll, cons
     }
 }
 
+// ---------------------------------------------------------------- bulk copies and mbarriers
+// One-dimensional bulk copies global -> shared (the TMA engine) completing on an
+// mbarrier: a thread announces the bytes to arrive (expect_tx), issues the copies,
+// and every thread waits for the barrier's phase.  Waits give up after about a
+// second (a copy that never lands), so that no kernel can hang the device.
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return unsigned(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(bar, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+// orders this thread's earlier generic-proxy accesses to shared memory before later bulk copies
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Bulk-copy pipeline of the FP32 X2X: kX2XStages buffers, each holding one source's
+// outgoing waves in one direction (4 S values) and its shift row (S values, rows
+// padded to an even length).
+constexpr int kX2XStages = 4;
+__host__ __device__ inline int x2x_tma_stage_elems(int S) { return 4 * S + ((S + 1) & ~1); }
+__host__ inline size_t x2x_tma_smem(int S) { return sizeof(cpx<float>) * size_t(kX2XStages) * x2x_tma_stage_elems(S); }
+
+// FP32 merge-and-shift, one consumer thread per plane wave (the four charge sets
+// and the box-origin move of set 4 as in k_x2x4), fed by a producer warp: the
+// present sources are staged through shared memory by bulk copies (TMA) into
+// kX2XStages buffers.  Buffer q is "full" when its copies have landed (an mbarrier
+// with the transaction count) and "empty" when every consumer warp has read it
+// (an mbarrier with one arrival per consumer warp); the producer refills a buffer
+// as soon as it is empty, so the consumers never wait on a global load and the
+// block needs no barrier per source.
+__global__ void __launch_bounds__(512, 1) k_x2x_tma(const int *parents, DevTables<float> D, const int *coll,
+                                                    const int *child, const int *leaf, const double *side,
+                                                    const cpx<float> *Xo, cpx<float> *Xi, int f0, int nf, int rb,
+                                                    unsigned *status) {
+    __shared__ int src[216];
+    __shared__ int vsrc[216], vsh[216], vpre[217], vend[216];
+    __shared__ float vd[3][216];
+    __shared__ __align__(8) uint64_t full[kX2XStages], empty[kX2XStages];
+    __shared__ int bad, issued;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = parents[blockIdx.x];
+    const int dl = blockIdx.y, d = 2 * f0 + dl;
+    const int S = D.S, Sp = D.Sp;
+    const int ncw = (S + 31) / 32;                 // consumer warps; the last warp produces
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double hc = 0.5 * side[P];
+    for (int sl = threadIdx.x; sl < 216; sl += blockDim.x) {
+        int q = sl >> 3, o = sl & 7;
+        int Q = coll[27 * P + q];
+        src[sl] = (Q >= 0 && !leaf[Q]) ? child[8 * Q + o] : -1;
+    }
+    if (threadIdx.x == 0) {
+        bad = 0;
+        issued = 0;
+        for (int q = 0; q < kX2XStages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], unsigned(ncw));
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const int ng = D.grp_n[d];
+    const int *goff = D.grp_off + d * (kGroupMax + 1);
+    const int *gmask = D.grp_mask + d * kGroupMax;
+    const int *slots = D.slot_list + d * 216;
+    if (warp == 0) {
+        const int nsl = goff[ng];
+        int carry = 0;
+        for (int z0 = 0; z0 < nsl; z0 += 32) {
+            const int z = z0 + lane;
+            int ent = 0, sb = -1;
+            if (z < nsl) {
+                ent = slots[z];
+                sb = src[ent & 255];
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, sb >= 0);
+            const int pos = carry + __popc(bal & ((1u << lane) - 1u));
+            if (z < nsl) vpre[z] = pos;
+            if (sb >= 0) {
+                vsrc[pos] = sb;
+                vsh[pos] = ent >> 8;
+                const int sl = ent & 255, q = sl >> 3, o = sl & 7;
+                vd[0][pos] = float(hc * (2 * (q % 3 - 1) + (o & 1) - 0.5));
+                vd[1][pos] = float(hc * (2 * ((q / 3) % 3 - 1) + ((o >> 1) & 1) - 0.5));
+                vd[2][pos] = float(hc * (2 * (q / 9 - 1) + ((o >> 2) & 1) - 0.5));
+            }
+            carry += __popc(bal);
+        }
+        if (lane == 0) vpre[nsl] = carry;
+    }
+    __syncthreads();
+    const int nz = vpre[goff[ng]];
+    for (int z = threadIdx.x; z < nz; z += blockDim.x) vend[z] = 0;
+    __syncthreads();
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        const int z1 = vpre[goff[g + 1]];
+        if (z1 > vpre[goff[g]]) vend[z1 - 1] = gmask[g];
+    }
+    __syncthreads();
+    const int stage_elems = x2x_tma_stage_elems(S);
+    cpx<float> *stage0 = reinterpret_cast<cpx<float> *>(smem_raw);
+    if (warp == ncw) {
+        // producer: one lane issues the copies, refilling each buffer once it is empty
+        if (lane == 0) {
+            const size_t dstride = size_t(2 * nf) * kSets * S;
+            const cpx<float> *Xd = Xo + size_t(dl) * kSets * S;
+            const unsigned src_bytes = 32u * unsigned(S), sh_bytes = 8u * unsigned(Sp);
+            for (int z = 0; z < nz; ++z) {
+                const int q = z % kX2XStages;
+                if (z >= kX2XStages && !mbar_wait(&empty[q], unsigned(z / kX2XStages - 1) & 1u)) {
+                    bad = 1;
+                    break;
+                }
+                if (*(volatile int *)&bad) break;
+                cpx<float> *buf = stage0 + size_t(q) * stage_elems;
+                mbar_expect(&full[q], src_bytes + sh_bytes);
+                bulk_load(buf, Xd + size_t(vsrc[z]) * dstride, src_bytes, &full[q]);
+                bulk_load(buf + 4 * S, D.shiftp + size_t(vsh[z]) * Sp, sh_bytes, &full[q]);
+                issued = z + 1;
+            }
+        }
+    } else {
+        int ch[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) ch[t] = child[8 * P + t];
+        const int j = threadIdx.x;
+        const bool act = j < S;
+        cpx<float> acc[8][kSets];
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+#pragma unroll
+            for (int k = 0; k < kSets; ++k) acc[t][k] = mk(0.f, 0.f);
+        cpx<float> ga[kSets];
+#pragma unroll
+        for (int k = 0; k < kSets; ++k) ga[k] = mk(0.f, 0.f);
+        for (int z = 0; z < nz; ++z) {
+            const int q = z % kX2XStages;
+            if (!mbar_wait(&full[q], unsigned(z / kX2XStages) & 1u) || *(volatile int *)&bad) {
+                bad = 1;
+                break;
+            }
+            if (act) {
+                const cpx<float> *buf = stage0 + size_t(q) * stage_elems;
+                cpx<float> x[kSets];
+#pragma unroll
+                for (int k = 0; k < kSets; ++k) x[k] = buf[k * S + j];
+                if (rb) {
+                    const float ex = vd[0][z], ey = vd[1][z], ez = vd[2][z];
+                    x[3].x = fmaf(ez, x[2].x, fmaf(ey, x[1].x, fmaf(ex, x[0].x, x[3].x)));
+                    x[3].y = fmaf(ez, x[2].y, fmaf(ey, x[1].y, fmaf(ex, x[0].y, x[3].y)));
+                }
+                const cpx<float> sh = buf[4 * S + j];
+#pragma unroll
+                for (int k = 0; k < kSets; ++k) {
+                    ga[k].x = fmaf(-x[k].y, sh.y, fmaf(x[k].x, sh.x, ga[k].x));
+                    ga[k].y = fmaf(x[k].y, sh.x, fmaf(x[k].x, sh.y, ga[k].y));
+                }
+                const int mask = vend[z];   // block-uniform
+                if (mask) {
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        if ((mask >> t) & 1)
+#pragma unroll
+                            for (int k = 0; k < kSets; ++k) acc[t][k] += ga[k];
+#pragma unroll
+                    for (int k = 0; k < kSets; ++k) ga[k] = mk(0.f, 0.f);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[q]);   // this warp is done with buffer q
+        }
+        if (!*(volatile int *)&bad && act) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                if (ch[t] < 0) continue;
+                if (rb) {   // P's centre - child t's centre = -(hc / 2) (2 bit - 1) per axis
+                    const float h = float(0.5 * hc);
+                    const float ex = (t & 1) ? -h : h, ey = (t & 2) ? -h : h, ez = (t & 4) ? -h : h;
+                    acc[t][3].x = fmaf(ez, acc[t][2].x, fmaf(ey, acc[t][1].x, fmaf(ex, acc[t][0].x, acc[t][3].x)));
+                    acc[t][3].y = fmaf(ez, acc[t][2].y, fmaf(ey, acc[t][1].y, fmaf(ex, acc[t][0].y, acc[t][3].y)));
+                }
+                const cpx<float> sh = D.shift[size_t(D.child_shift[d * 8 + t]) * S + j];
+                cpx<float> *dst = Xi + (size_t(ch[t]) * (2 * nf) + dl) * kSets * S + j;
+#pragma unroll
+                for (int k = 0; k < kSets; ++k) dst[size_t(k) * S] = acc[t][k] * sh;
+            }
+        }
+    }
+    __syncthreads();
+    if (bad && threadIdx.x == 0) {
+        // a wait gave up: let every copy issued land (bounded) before the block's shared
+        // memory is released, and flag the failure
+        for (int q = 0; q < min(issued, kX2XStages); ++q) {
+            const int zl = q + ((issued - 1 - q) / kX2XStages) * kX2XStages;   // last copy issued into buffer q
+            mbar_wait(&full[q], unsigned(zl / kX2XStages) & 1u);
+        }
+        atomicOr(status, DEVERR_TIMEOUT);
+    }
+}
+
 // ---------------------------------------------------------------- X2L
 template <typename T>
 __global__ void k_x2l(int b0, int nb, DevTables<T> D, const cpx<T> *Xi, cpx<T> *L, int f0, int nf) {
@@ -1181,19 +1431,27 @@ __global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi,
         for (int i = threadIdx.x; i < nc; i += blockDim.x) {
             const int n = deg_of(i), m = i - tri(n, 0);
             const cpx<float> *Bx = ((n + m) & 1) ? Bd : Bs;
+            // sum over the quadrature nodes with compensated (Kahan) addition: the terms
+            // (-lambda_k)^n b_k^m alternate in sign and cancel strongly at high degree
             float ax[kSets] = {0, 0, 0, 0}, ay[kSets] = {0, 0, 0, 0};
+            float cx[kSets] = {0, 0, 0, 0}, cy[kSets] = {0, 0, 0, 0};
+            auto kahan = [](float &sum, float &c, float v) {
+                const float y = v - c, t = sum + y;
+                c = (t - sum) - y;
+                sum = t;
+            };
             for (int k = 0; k < s; ++k) {
                 const float c = D.x2l_c[size_t(k) * nc + i];
                 const float4 *bb = reinterpret_cast<const float4 *>(Bx + (k * P1 + m) * kSets);
                 const float4 b01 = bb[0], b23 = bb[1];
-                ax[0] = fmaf(c, b01.x, ax[0]);
-                ay[0] = fmaf(c, b01.y, ay[0]);
-                ax[1] = fmaf(c, b01.z, ax[1]);
-                ay[1] = fmaf(c, b01.w, ay[1]);
-                ax[2] = fmaf(c, b23.x, ax[2]);
-                ay[2] = fmaf(c, b23.y, ay[2]);
-                ax[3] = fmaf(c, b23.z, ax[3]);
-                ay[3] = fmaf(c, b23.w, ay[3]);
+                kahan(ax[0], cx[0], c * b01.x);
+                kahan(ay[0], cy[0], c * b01.y);
+                kahan(ax[1], cx[1], c * b01.z);
+                kahan(ay[1], cy[1], c * b01.w);
+                kahan(ax[2], cx[2], c * b23.x);
+                kahan(ay[2], cy[2], c * b23.y);
+                kahan(ax[3], cx[3], c * b23.z);
+                kahan(ay[3], cy[3], c * b23.w);
             }
 #pragma unroll
             for (int st = 0; st < kSets; ++st) Lf[st * nc + i] = mul_ipow(mk(2 * ax[st], 2 * ay[st]), m + (m & 1));
@@ -1521,13 +1779,13 @@ __global__ void k_lap_eval(const int *leaves, DevTables<T> D, const int *beg, co
 template <typename T>
 static size_t smem_p2x(int p, int threads) {
     const int nc = ncoef(p), chunk = p2x_chunk(p, threads);
-    return sizeof(T) * ((rec_floats<T>(p) + 1) & ~1) + sizeof(cpx<T>) * (chunk * nc + kSets * nc) +
+    return sizeof(T) * ((rec_floats<T>(p) + 1) & ~1) + sizeof(cpx<T>) * (chunk * nc + 2 * kSets * nc) +
            sizeof(T) * 4 * chunk + 64;
 }
 template <typename T>
 static size_t smem_m2x(int p, int s) {
     int nc = ncoef(p);
-    return sizeof(cpx<T>) * (3 * kSets * nc + 2 * kSets * s * (p + 1));
+    return sizeof(cpx<T>) * (3 * kSets * nc + 2 * s * (kSets * (p + 1) + 1));
 }
 template <typename T>
 static size_t smem_x2l(int p, int s, int NU) {
@@ -1659,7 +1917,17 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
             if (sizeof(T) == 4 || rb) {
                 bool fac = false;
                 if constexpr (sizeof(T) == 4) {
-                    if (D.S <= 256) {
+                    if (D.S > 256 && D.S <= 480) {
+                        // a producer warp stages the sources through shared memory by bulk copies
+                        // (measured faster than per-thread loads from 323 stored waves up; at 3 digits,
+                        // 134 waves, the per-thread loads below keep two to three blocks per SM and win)
+                        const size_t sxx = x2x_tma_smem(D.S);
+                        RPY_TRY(set_smem(k_x2x_tma, sxx));
+                        k_x2x_tma<<<g, (D.S + 31) / 32 * 32 + 32, sxx, st>>>(t.x2x_par, D, t.b_coll, t.b_child,
+                                                                             t.b_leaf, t.b_side, Xo, Xi, f0, nf, rb,
+                                                                             t.dev_status);
+                        fac = true;
+                    } else if (D.S <= 256) {
                         const size_t sxx = sizeof(T) * ((6 * D.S + 3) & ~3) + 2 * sizeof(cpx<T>) * 6 * D.S;
                         k_x2x4<T, true><<<g, even_threads(D.S), sxx, st>>>(t.x2x_par, D, t.b_coll, t.b_child,
                                                                            t.b_leaf, t.b_side, Xo, Xi, f0, nf, rb);

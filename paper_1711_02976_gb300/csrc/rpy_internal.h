@@ -22,6 +22,7 @@ enum : unsigned {
     DEVERR_NONFINITE = 1u,     // a position was NaN/inf
     DEVERR_STACK = 2u,         // list-builder traversal stack overflow
     DEVERR_CAPACITY = 4u,      // a fixed-size device table overflowed
+    DEVERR_TIMEOUT = 8u,       // a bounded device wait (an mbarrier of a bulk-copy pipeline) gave up
 };
 
 struct CudaError {
@@ -169,6 +170,8 @@ struct DevTables {
     int NU;
     const T *e_cos, *e_sin, *e_wm;
     const cpx<T> *shift;
+    const cpx<T> *shiftp;   // the same rows with stride Sp (S rounded up to even: 16-byte rows for bulk copies)
+    int Sp;
     const T *shz;
     const cpx<T> *shx, *shy;
     const int *grp_off, *grp_n, *grp_mask, *slot_list, *child_shift;
