@@ -92,7 +92,15 @@ typedef struct {
                          grad L4 - sum_k x_k grad L_k of Eq. (2.8) to cancel terms of size
                          |x - o| |grad L|.  Default: box origin for RPY_FP32, cube origin for
                          RPY_FP64 (whose rounding does not need it); at most one of the two
-                         bits; other bits must be 0 */
+                         bits;
+                         bit 5 (RPY_FLAG_CARTESIAN): the polynomial far field that the paper's
+                         Sec. 5 proposes for low accuracy: Cartesian Taylor expansions of total
+                         degree order_p (default 8, at most 10) with a direct multipole-to-local
+                         step over the V lists instead of spherical harmonics and plane waves;
+                         every W- and X-list interaction is summed directly; 3 digits only
+                         (RPY_ERR_DIGITS otherwise); rpy_laplace_far is not available on such a
+                         tree (RPY_ERR_STATE);
+                         other bits must be 0 */
     int direct_w;     /* W-list boxes with at most this many beads are summed directly
                          instead of by multipole evaluation: 0 = automatic
                          (about 1.8 (p+3)(p+4)/2), -1 = never */
@@ -107,7 +115,7 @@ typedef struct {
 } rpy_build_params;
 
 enum { RPY_FLAG_NO_GRAPH = 1, RPY_FLAG_FRAME_PASSES = 2, RPY_FLAG_EVAL_PER_POTENTIAL = 4, RPY_FLAG_BOX_ORIGIN = 8,
-       RPY_FLAG_CUBE_ORIGIN = 16 };
+       RPY_FLAG_CUBE_ORIGIN = 16, RPY_FLAG_CARTESIAN = 32 };
 
 /* Statistics of a built tree (host struct filled by rpy_tree_stats). */
 typedef struct {

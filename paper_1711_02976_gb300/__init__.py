@@ -26,13 +26,14 @@ __all__ = [
     "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt",
     "rpy_bd_step", "rpy_evaluate", "rpy_matvec_batched", "rpy_tree_matvec_host", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
     "RPY_PART_ALL", "RPY_FLAG_NO_GRAPH", "RPY_FLAG_FRAME_PASSES",
-    "RPY_FLAG_EVAL_PER_POTENTIAL", "RPY_FLAG_BOX_ORIGIN", "RPY_FLAG_CUBE_ORIGIN", "EXPORTED_SYMBOLS",
+    "RPY_FLAG_EVAL_PER_POTENTIAL", "RPY_FLAG_BOX_ORIGIN", "RPY_FLAG_CUBE_ORIGIN", "RPY_FLAG_CARTESIAN",
+    "EXPORTED_SYMBOLS",
 ]
 
 RPY_FP64, RPY_FP32 = 0, 1
 RPY_PART_NEAR, RPY_PART_FAR, RPY_PART_ALL = 1, 2, 3
 RPY_FLAG_NO_GRAPH, RPY_FLAG_FRAME_PASSES, RPY_FLAG_EVAL_PER_POTENTIAL = 1, 2, 4
-RPY_FLAG_BOX_ORIGIN, RPY_FLAG_CUBE_ORIGIN = 8, 16
+RPY_FLAG_BOX_ORIGIN, RPY_FLAG_CUBE_ORIGIN, RPY_FLAG_CARTESIAN = 8, 16, 32
 FIELDS = {
     "perm": (1, np.int32), "keys": (2, np.uint64), "box_level": (3, np.int32), "box_range": (4, np.int32),
     "box_parent": (5, np.int32), "box_center": (6, np.float64), "box_leaf": (7, np.int32),

@@ -339,10 +339,27 @@ static int alloc_tree_arrays(Tree &t, cudaStream_t st) {
     return RPY_OK;
 }
 
-int tree_alloc_workspace(Tree &t, cudaStream_t) {
+int tree_alloc_workspace(Tree &t, cudaStream_t st) {
     const OpTables &h = t.tabs;
     size_t es = t.params.precision == RPY_FP32 ? sizeof(cpx<float>) : sizeof(cpx<double>);
     size_t nb = size_t(t.nbox);
+    if (t.params.flags & RPY_FLAG_CARTESIAN) {
+        // real coefficients: multipoles and locals of four sets, three velocity polynomials per leaf
+        const size_t rs = es / 2, N = size_t(cart_terms(t.p));
+        RPY_TRY(tree_build_vlists(t, st));
+        RPY_TRY(dev_alloc(t, &t.M, rs * nb * kSets * N));
+        RPY_TRY(dev_alloc(t, &t.L, rs * nb * kSets * N));
+        RPY_TRY(dev_alloc(t, &t.EVg, rs * size_t(t.nleaf) * 3 * N));
+        RPY_TRY(dev_alloc(t, (void **)&t.fs, sizeof(double) * 3 * t.n));
+        if (t.params.precision == RPY_FP32) {
+            RPY_TRY(dev_alloc(t, (void **)&t.p32, sizeof(float) * 6 * t.n));
+            RPY_TRY(dev_alloc(t, (void **)&t.f32, sizeof(float) * 3 * t.n));
+        }
+        RPY_TRY(dev_alloc(t, (void **)&t.u_near, sizeof(double) * 3 * t.n));
+        RPY_TRY(dev_alloc(t, (void **)&t.u_far, sizeof(double) * 3 * t.n));
+        RPY_TRY(dev_alloc(t, (void **)&t.u_dir, sizeof(double) * 3 * t.n));
+        return RPY_OK;
+    }
     RPY_TRY(dev_alloc(t, &t.M, es * nb * kSets * h.nc));
     RPY_TRY(dev_alloc(t, &t.L, es * nb * kSets * h.nc));
     t.x_frames = (t.params.flags & RPY_FLAG_FRAME_PASSES) ? 1 : plane_wave_frames(double(nb), double(es), h.S);
@@ -423,10 +440,14 @@ static int matvec_body(Tree &t, const SysConst &sc, int parts, cudaStream_t st, 
     }
     prof_mark(t, RPY_STAGE_P2M, st);
     if (parts & RPY_PART_FAR) {
-        if (t.params.precision == RPY_FP32)
+        if (t.params.flags & RPY_FLAG_CARTESIAN) {
+            if (t.params.precision == RPY_FP32) RPY_TRY(run_cart_t<float>(t, t.fs, t.u_far, sc, st));
+            else RPY_TRY(run_cart_t<double>(t, t.fs, t.u_far, sc, st));
+        } else if (t.params.precision == RPY_FP32) {
             RPY_TRY(run_far_t<float>(t, t.dt32, t.fs, nullptr, t.u_far, nullptr, sc, st));
-        else
+        } else {
             RPY_TRY(run_far_t<double>(t, t.dt64, t.fs, nullptr, t.u_far, nullptr, sc, st));
+        }
     }
     if (side) {
         RPY_CHECK(cudaEventRecord(t.join_ev, t.side_stream));
@@ -495,7 +516,7 @@ int run_matvec(Tree &t, const double *f_dev, const double *s_host, double *u_dev
 }
 
 int run_laplace_far(Tree &t, const double *q_dev, double *out_dev, cudaStream_t st) {
-    if (!t.built) return RPY_ERR_STATE;
+    if (!t.built || (t.params.flags & RPY_FLAG_CARTESIAN)) return RPY_ERR_STATE;
     if (!std::isfinite(t.sys_s_h[0])) {   // per-system constants (their geometric part) for a tree never applied
         std::vector<double> one(t.nsys, 1.0);
         RPY_TRY(upload_s(t, one.data(), st));
@@ -531,10 +552,14 @@ static int check_params(const rpy_build_params &p) {
     if (p.digits == 9 && p.precision != RPY_FP64) return RPY_ERR_DIGITS;   // beyond FP32 arithmetic
     if (p.leaf_cap < 0 || p.order_p < 0 || p.max_level < 0 || p.max_level > kMaxLevel ||
         (p.flags & ~(RPY_FLAG_NO_GRAPH | RPY_FLAG_FRAME_PASSES | RPY_FLAG_EVAL_PER_POTENTIAL |
-                     RPY_FLAG_BOX_ORIGIN | RPY_FLAG_CUBE_ORIGIN)) != 0 ||
+                     RPY_FLAG_BOX_ORIGIN | RPY_FLAG_CUBE_ORIGIN | RPY_FLAG_CARTESIAN)) != 0 ||
         ((p.flags & RPY_FLAG_BOX_ORIGIN) && (p.flags & RPY_FLAG_CUBE_ORIGIN)))
         return RPY_ERR_INVALID;
     if (p.order_p != 0 && (p.order_p < 2 || p.order_p > kMaxP)) return RPY_ERR_INVALID;
+    if (p.flags & RPY_FLAG_CARTESIAN) {
+        if (p.digits != 3) return RPY_ERR_DIGITS;
+        if (p.order_p > kCartMaxP) return RPY_ERR_INVALID;
+    }
     if (p.direct_w < -1 || p.direct_x < -1) return RPY_ERR_INVALID;
     if (p.quad != 0 && (p.quad < 3 || p.quad > 6) && p.quad != 9) return RPY_ERR_INVALID;
     return RPY_OK;
@@ -592,6 +617,12 @@ int rpy_forest_build(const double *pos_dev, const int64_t *sys_offsets, int nsys
     t.p = params->order_p ? params->order_p : default_order(params->digits);
     t.direct_w = params->direct_w < 0 ? 0 : (params->direct_w > 0 ? params->direct_w : int(1.8 * ncoef(t.p + 2)));
     t.direct_x = params->direct_x < 0 ? 0 : (params->direct_x > 0 ? params->direct_x : int(0.6 * ncoef(t.p)));
+    if (params->flags & RPY_FLAG_CARTESIAN) {
+        // polynomial far field: no multipole-to-target or source-to-local operators, so every
+        // W- and X-list interaction is summed directly
+        if (!params->order_p) t.p = kCartDefaultP;
+        t.direct_w = t.direct_x = 0x7fffffff;
+    }
     t.sys_off_h.assign(sys_offsets, sys_offsets + nsys + 1);
     t.a_h.assign(a_host, a_host + nsys);
     int s = do_build(t, pos_dev, static_cast<cudaStream_t>(stream));

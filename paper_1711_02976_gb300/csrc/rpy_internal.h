@@ -323,6 +323,11 @@ __device__ __forceinline__ double pow2i(int l) { return __hiloint2double((1023 +
 template <typename T>
 int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *lapq, double *ufar, double *lapout,
               const SysConst &sc, cudaStream_t st);
+// the polynomial (Cartesian Taylor) far field of RPY_FLAG_CARTESIAN trees (rpy_cart.cu)
+template <typename T>
+int run_cart_t(Tree &t, const double *fs, double *ufar, const SysConst &sc, cudaStream_t st);
+int cart_terms(int P);   // monomials of total degree <= P
+constexpr int kCartMaxP = 10, kCartDefaultP = 8;
 constexpr int kListU = 0, kListD = 1, kListM = 2;   // near list: U, direct substitutes, both
 int run_p2p(Tree &t, const double *fs, double *out, const SysConst &sc, cudaStream_t st, int list);
 int split_positions_f32(Tree &t, cudaStream_t st);

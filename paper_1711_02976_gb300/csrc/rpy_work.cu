@@ -35,6 +35,11 @@
 //         harmonics of degree p + 2 and 18 fields; bytes: L read, the derived
 //         expansions written and read once per leaf, positions read and
 //         velocities written.
+// Polynomial far field (RPY_FLAG_CARTESIAN, N monomials of degree <= P): P2M per
+// bead 2 multiplies and 4 FMA per monomial; M2M and L2L per child box and M2L per
+// V-list pair one FMA per set and operator term (the pair counts of the tables);
+// L2P per leaf the three velocity polynomials (about 10 FMA per coefficient) and
+// per bead 3 FMA and 1 multiply per monomial; its M2L is timed under X2L.
 #include <vector>
 
 #include "rpy_internal.h"
@@ -107,7 +112,42 @@ extern "C" int rpy_tree_work(rpy_tree h, double *flops, double *bytes, int n) {
     B[RPY_STAGE_GATHER] = double(N) * (3 * 8 + 4 + 3 * 8 + (f32 ? 3 * 4 : 0));   // forces, perm in; sorted out
     B[RPY_STAGE_COMBINE] = double(N) * (4 + 2 * 3 * 8 + 3 * 8);
 
-    if (t.nlevels > 2) {
+    if (t.nlevels > 2 && (t.params.flags & RPY_FLAG_CARTESIAN)) {
+        std::vector<int> lvl, beg, end, leaves;
+        const size_t nb = size_t(t.nbox);
+        RPY_TRY(fetch(lvl, t.b_level, nb));
+        RPY_TRY(fetch(beg, t.b_begin, nb));
+        RPY_TRY(fetch(end, t.b_end, nb));
+        RPY_TRY(fetch(leaves, t.leaves, size_t(t.nleaf)));
+        const int P = t.p, Nm = cart_terms(P);
+        double pairs_l = 0, pairs_m = 0;   // M2L pairs (|a + b| <= P); M2M / L2L pairs (b <= a)
+        for (int a0 = 0; a0 <= P; ++a0)
+            for (int a1 = 0; a0 + a1 <= P; ++a1)
+                for (int a2 = 0; a0 + a1 + a2 <= P; ++a2) {
+                    pairs_l += cart_terms(P - a0 - a1 - a2);
+                    pairs_m += double(a0 + 1) * (a1 + 1) * (a2 + 1);
+                }
+        double bead2 = 0, leaf2 = 0;
+        for (int li = 0; li < t.nleaf; ++li) {
+            const int b = leaves[li];
+            if (lvl[b] < 2) continue;
+            leaf2 += 1;
+            bead2 += end[b] - beg[b];
+        }
+        const double n2 = double(nb - t.level_off[2]);
+        const double nch = t.nlevels > 3 ? double(nb - t.level_off[3]) : 0.0;
+        const double rw = w;   // real coefficients
+        F[RPY_STAGE_P2M] = bead2 * Nm * (2 + 4 * 2);
+        B[RPY_STAGE_P2M] = bead2 * 48 + leaf2 * 4 * Nm * rw;
+        F[RPY_STAGE_M2M] = nch * pairs_m * 4 * 2;
+        B[RPY_STAGE_M2M] = (nch + n2) * 4 * Nm * rw;
+        F[RPY_STAGE_X2L] = double(t.n_v) * pairs_l * 4 * 2;
+        B[RPY_STAGE_X2L] = n2 * 4 * Nm * rw * 2;   // every multipole read, every local written
+        F[RPY_STAGE_L2L] = nch * pairs_m * 4 * 2;
+        B[RPY_STAGE_L2L] = nch * 3 * 4 * Nm * rw;
+        F[RPY_STAGE_EVAL] = leaf2 * 3 * Nm * 20.0 + bead2 * Nm * 7.0;
+        B[RPY_STAGE_EVAL] = leaf2 * (4 + 2 * 3) * Nm * rw + bead2 * 48;
+    } else if (t.nlevels > 2) {
         std::vector<int> lvl, beg, end, leaf, leaves, xoff, xidx, woff, coll, child, par;
         const size_t nb = size_t(t.nbox);
         RPY_TRY(fetch(lvl, t.b_level, nb));

@@ -695,3 +695,62 @@ def test_full_matvec_equals_near_plus_far_parts(precision, tol):
         out[name] = U.cpu().numpy()
     assert oracle.rel_l2(out["near"] + out["far"], out["all"]) < tol
     assert oracle.rel_l2(out["far"], out["all"]) > 1e-3   # the far part is not negligible
+
+
+# ---------------------------------------------------------------- polynomial (Cartesian) far field
+
+def test_cartesian_far_field_meets_3digits_and_converges_in_order():
+    """RPY_FLAG_CARTESIAN (the polynomial expansions Sec. 5 proposes for low accuracy):
+    at its default total degree the full velocity meets rel-L2 <= 1e-3 against the oracle
+    in FP64 and FP32; the error falls geometrically with the degree (each +2 at least 2x);
+    FP32 and FP64 differ only by rounding."""
+    sysm = synth.config1()
+    ref = oracle.rpy_direct(sysm.pos, sysm.f, sysm.a, sysm.s)
+    errs = {}
+    for P in (4, 6, 8, 10):
+        u, t = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, 3, leaf_cap=40, order_p=P, flags=rp.RPY_FLAG_CARTESIAN)
+        errs[P] = oracle.rel_l2(u, ref)
+        assert rp.rpy_tree_stats(t)["n_vpairs"] > 0
+    assert all(errs[P + 2] < 0.5 * errs[P] for P in (4, 6, 8)), errs
+    u64, t64 = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, 3, leaf_cap=40, flags=rp.RPY_FLAG_CARTESIAN)
+    u32, t32 = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, 3, leaf_cap=40, flags=rp.RPY_FLAG_CARTESIAN,
+                      precision=rp.RPY_FP32)
+    assert rp.rpy_tree_stats(t64)["order_p"] == 8
+    assert oracle.rel_l2(u64, ref) < 1e-3 and oracle.rel_l2(u32, ref) < 1e-3
+    assert oracle.rel_l2(u32, u64) < 1e-6
+
+
+def test_cartesian_adaptive_sphere_and_dipole_regime():
+    """The polynomial far field on an adaptive sphere-plus-cube tree (W and X lists summed
+    directly) on sampled targets, and with a comparable to the box size (the a^2/r^2 term
+    of Eq. (2.8) large), both at 3 digits against the oracle."""
+    sysm = synth.sphere_plus_cube(200000, 71, 1e-4)
+    tg = synth.sample_targets(sysm.n, 600)
+    e, e_far, t = _check(sysm.pos, sysm.f, sysm.a, sysm.s, 3, 1e-3, targets=tg, precision=rp.RPY_FP32,
+                         flags=rp.RPY_FLAG_CARTESIAN)
+    st = rp.rpy_tree_stats(t)
+    assert st["n_wlist"] == 0 and st["n_dlist"] > 0 and st["depth"] >= 5
+    rng = np.random.default_rng(6)
+    pos = rng.random((512, 3))
+    f = rng.standard_normal((512, 3))
+    a = 0.02
+    _check(pos, f, a, 6 * math.pi * a, 3, 1e-3, leaf_cap=8, order_p=10, flags=rp.RPY_FLAG_CARTESIAN)
+
+
+def test_cartesian_refusals():
+    import torch
+    sysm = synth.config1()
+    P = cuda_tensor(sysm.pos)
+    with pytest.raises(rp.RpyError) as e:
+        rp.rpy_forest_build(P, [0, sysm.n], [sysm.a], 6, flags=rp.RPY_FLAG_CARTESIAN)
+    assert e.value.status == -2
+    with pytest.raises(rp.RpyError) as e:
+        rp.rpy_forest_build(P, [0, sysm.n], [sysm.a], 3, order_p=11, flags=rp.RPY_FLAG_CARTESIAN)
+    assert e.value.status == -1
+    t = rp.rpy_forest_build(P, [0, sysm.n], [sysm.a], 3, leaf_cap=40, flags=rp.RPY_FLAG_CARTESIAN)
+    q = torch.zeros((sysm.n, 4), dtype=torch.float64, device="cuda")
+    out = torch.zeros((sysm.n, 52), dtype=torch.float64, device="cuda")
+    with pytest.raises(rp.RpyError) as e:
+        rp.rpy_laplace_far(t, q, out)
+    assert e.value.status == -7
+    t.close()
