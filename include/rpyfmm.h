@@ -90,9 +90,9 @@ typedef struct {
                          the size of the box's own moments; cube origin: one origin per system
                          (the bounding-cube centre), which leaves the far-field combination
                          grad L4 - sum_k x_k grad L_k of Eq. (2.8) to cancel terms of size
-                         |x - o| |grad L|.  Default: box origin for RPY_FP32, cube origin for
-                         RPY_FP64 (whose rounding does not need it); at most one of the two
-                         bits;
+                         |x - o| |grad L|.  Default: box origin for RPY_FP32 at 6 digits, cube
+                         origin for RPY_FP64 and at 3 digits (whose rounding stays far below
+                         the setting there); at most one of the two bits;
                          bit 5 (RPY_FLAG_CARTESIAN): the polynomial far field that the paper's
                          Sec. 5 proposes for low accuracy: Cartesian Taylor expansions of total
                          degree order_p (default 8, at most 10) with a direct multipole-to-local
@@ -525,6 +525,17 @@ int rpy_bounding_cube_noalloc(const double *pos_dev, int64_t n, double *cube_dev
  * synchronises t's last stream.
  */
 int rpy_tree_work(rpy_tree t, double *flops_host, double *bytes_host, int n);
+
+/*
+ * Self-test of the bounded device waits of the bulk-copy pipelines (the paper
+ * has no counterpart): one thread waits on an mbarrier phase that nothing will
+ * complete, gives up after limit_ms (0 < limit_ms <= 2000) and reports it in a
+ * status word, as the pipelined kernels do when a copy never lands.  Returns
+ * RPY_ERR_TIMEOUT when the wait gave up (the expected outcome), RPY_OK if it
+ * did not.  No copy is issued, so nothing is left in flight; the context stays
+ * usable.  Allocates and frees one word of device memory; synchronises `stream`.
+ */
+int rpy_debug_wait_timeout(double limit_ms, void *stream);
 
 /* Number of kernels this library has launched in this process (all devices). */
 int64_t rpy_launch_count(void);

@@ -24,7 +24,7 @@ __all__ = [
     "rpy_tree_sync", "rpy_tree_footprint", "rpy_tree_free", "rpy_strerror", "rpy_last_cuda_error", "rpy_tree_work",
     "rpy_version", "rpy_debug_table", "rpy_tree_set_profiling", "rpy_tree_stage_times", "rpy_launch_count",
     "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt",
-    "rpy_bd_step", "rpy_evaluate", "rpy_matvec_batched", "rpy_tree_matvec_host", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
+    "rpy_bd_step", "rpy_evaluate", "rpy_matvec_batched", "rpy_tree_matvec_host", "rpy_debug_wait_timeout", "STAGES", "FIELDS", "RPY_FP64", "RPY_FP32", "RPY_PART_NEAR", "RPY_PART_FAR",
     "RPY_PART_ALL", "RPY_FLAG_NO_GRAPH", "RPY_FLAG_FRAME_PASSES",
     "RPY_FLAG_EVAL_PER_POTENTIAL", "RPY_FLAG_BOX_ORIGIN", "RPY_FLAG_CUBE_ORIGIN", "RPY_FLAG_CARTESIAN",
     "EXPORTED_SYMBOLS",
@@ -50,7 +50,7 @@ EXPORTED_SYMBOLS = [
     "rpy_launch_count", "rpy_alu_peak", "rpy_bounding_cube_noalloc", "rpy_server_create", "rpy_server_add_system",
     "rpy_server_submit", "rpy_server_wait", "rpy_server_cancel", "rpy_server_drain", "rpy_server_stats_get",
     "rpy_server_destroy", "rpy_server_wait_times", "rpy_direct_sampled", "rpy_autotune", "rpy_lanczos_sqrt", "rpy_bd_step", "rpy_evaluate",
-    "rpy_matvec_batched", "rpy_tree_work", "rpy_tree_matvec_host",
+    "rpy_matvec_batched", "rpy_tree_work", "rpy_tree_matvec_host", "rpy_debug_wait_timeout",
 ]
 STAGES = ["gather", "p2p", "p2m", "m2m", "m2x", "x2x", "x2l", "p2l", "l2l", "eval", "combine"]
 
@@ -163,6 +163,7 @@ def load(build_if_missing: bool = True):
             "rpy_tree_set_profiling": [vp, i],
             "rpy_tree_stage_times": [vp, vp, i],
             "rpy_tree_work": [vp, vp, vp, i],
+            "rpy_debug_wait_timeout": [d, vp],
             "rpy_tree_matvec_host": [vp, vp, vp, vp, vp, vp],
             "rpy_launch_count": [],
             "rpy_alu_peak": [i, ctypes.POINTER(d), vp],
@@ -504,6 +505,11 @@ def rpy_tree_work(tree) -> dict:
     by = np.zeros(len(STAGES))
     _check(load().rpy_tree_work(_h(tree), fl.ctypes.data, by.ctypes.data, len(STAGES)), "rpy_tree_work")
     return {k: (float(a), float(b)) for k, a, b in zip(STAGES, fl, by)}
+
+
+def rpy_debug_wait_timeout(limit_ms, stream=None) -> int:
+    """Bounded-wait self-test: returns the status (RPY_ERR_TIMEOUT, -5, is the expected one)."""
+    return load().rpy_debug_wait_timeout(float(limit_ms), _stream(stream))
 
 
 def rpy_launch_count() -> int:

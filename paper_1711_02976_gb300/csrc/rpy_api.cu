@@ -989,6 +989,12 @@ int rpy_tree_stage_times(rpy_tree h, double *ms, int n) {
 
 int64_t rpy_launch_count(void) { return g_launches.load(); }
 
+int rpy_debug_wait_timeout(double limit_ms, void *stream) {
+    if (!(limit_ms > 0.0) || limit_ms > 2000.0) return RPY_ERR_INVALID;
+    RPY_TRY(have_device());
+    return wait_selftest(limit_ms, static_cast<cudaStream_t>(stream));
+}
+
 int rpy_bounding_cube_noalloc(const double *pos_dev, int64_t n, double *cube_dev, void *stream) {
     if (!pos_dev || !cube_dev) {
         set_last_error("rpy_bounding_cube_noalloc: pos_dev and cube_dev must be device pointers, not NULL");

@@ -1067,12 +1067,40 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, uint64_t limit_ns = 1000000000ull) {
     if (mbar_test(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (!mbar_test(bar, parity))
-        if (global_ns() - t0 > 1000000000ull) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
+}
+
+// Self-test of the bounded wait: one thread waits for an mbarrier phase that no
+// arrival will ever complete (no copy is issued), gives up after limit_ns and
+// reports the timeout through the status word, as the pipelined kernels do.
+__global__ void k_wait_selftest(uint64_t limit_ns, unsigned *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+    if (!mbar_wait(&bar, 0, limit_ns)) atomicOr(status, DEVERR_TIMEOUT);
+}
+
+int wait_selftest(double limit_ms, cudaStream_t st) {
+    unsigned *d = nullptr;
+    RPY_CHECK(cudaMalloc(&d, sizeof(unsigned)));
+    unsigned h = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32, 0, st>>>(uint64_t(limit_ms * 1e6), d);
+        RPY_LAUNCHED(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return check_cuda("wait self-test", e);
+    return (h & DEVERR_TIMEOUT) ? RPY_ERR_TIMEOUT : RPY_OK;
 }
 // orders this thread's earlier generic-proxy accesses to shared memory before later bulk copies
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -1849,10 +1877,13 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
     int b2 = t.level_off[2];
     int n2 = nbx - b2;
     // origin of q4 (RPY charges only; the Laplace diagnostic takes its charges as given):
-    // each expansion's own box centre by default in FP32, the cube centre in FP64
+    // each expansion's own box centre by default in the FP32 form at 6 digits, the cube
+    // centre otherwise (in FP64, and at 3 digits, its rounding stays far below the setting)
     const int fl = t.params.flags;
     const int rb = lapq ? 0
-                        : (sizeof(T) == 4 ? !(fl & RPY_FLAG_CUBE_ORIGIN) : (fl & RPY_FLAG_BOX_ORIGIN) != 0);
+                        : (fl & RPY_FLAG_BOX_ORIGIN) ? 1
+                        : (fl & RPY_FLAG_CUBE_ORIGIN) ? 0
+                        : (sizeof(T) == 4 && t.params.digits >= 6);
     // upward pass
     size_t sp = smem_p2x<T>(p, 128);
     RPY_TRY(set_smem(k_p2x<T, 0>, sp));
@@ -1914,7 +1945,12 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
             // up to 256 stored waves: shifts from per-axis factors in shared memory (measured
             // faster there; at more waves the shared memory costs occupancy and the table is
             // faster)
-            if (sizeof(T) == 4 || rb) {
+            if (sizeof(T) == 4 && !rb && D.S <= 256) {
+                // cube origin, few plane waves: one set per thread, shifts from per-axis factors
+                const size_t sxx = sizeof(T) * ((6 * D.S + 3) & ~3) + 2 * sizeof(cpx<T>) * 6 * D.S;
+                k_x2x<T, true><<<g, x2x_threads(D.S), sxx, st>>>(t.x2x_par, D, t.b_coll, t.b_child, t.b_leaf, Xo,
+                                                                 Xi, f0, nf);
+            } else if (sizeof(T) == 4 || rb) {
                 bool fac = false;
                 if constexpr (sizeof(T) == 4) {
                     if (D.S > 256 && D.S <= 480) {

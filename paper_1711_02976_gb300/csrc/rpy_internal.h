@@ -327,6 +327,7 @@ int run_far_t(Tree &t, const DevTables<T> &D, const double *fs, const double *la
 template <typename T>
 int run_cart_t(Tree &t, const double *fs, double *ufar, const SysConst &sc, cudaStream_t st);
 int cart_terms(int P);   // monomials of total degree <= P
+int wait_selftest(double limit_ms, cudaStream_t st);   // bounded mbarrier wait that must time out
 constexpr int kCartMaxP = 10, kCartDefaultP = 8;
 constexpr int kListU = 0, kListD = 1, kListM = 2;   // near list: U, direct substitutes, both
 int run_p2p(Tree &t, const double *fs, double *out, const SysConst &sc, cudaStream_t st, int list);

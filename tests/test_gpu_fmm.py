@@ -623,7 +623,8 @@ def test_fp32_box_origin_rounding_against_fp64(digits, order):
     sysm = synth.sphere_plus_cube(400000, 41, 2e-5)
     kw = dict(order_p=order, leaf_cap=20)
     u64, t64 = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, digits, **kw)
-    ub, tb = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, digits, precision=rp.RPY_FP32, **kw)
+    ub, tb = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, digits, precision=rp.RPY_FP32, flags=rp.RPY_FLAG_BOX_ORIGIN,
+                    **kw)
     uc, tc = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, digits, precision=rp.RPY_FP32, flags=rp.RPY_FLAG_CUBE_ORIGIN,
                     **kw)
     assert rp.rpy_tree_stats(tb)["depth"] >= 7
@@ -754,3 +755,15 @@ def test_cartesian_refusals():
         rp.rpy_laplace_far(t, q, out)
     assert e.value.status == -7
     t.close()
+
+
+def test_bounded_device_wait_times_out_and_context_stays_usable():
+    """The pipelined kernels' mbarrier waits are bounded: a wait that nothing completes gives up
+    after its limit and reports RPY_ERR_TIMEOUT through the status word; the next matvec runs."""
+    import time
+    t0 = time.perf_counter()
+    assert rp.rpy_debug_wait_timeout(50.0) == -5
+    assert time.perf_counter() - t0 < 5.0
+    sysm = synth.config1()
+    u, t = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, 3, leaf_cap=40)
+    assert oracle.rel_l2(u, oracle.rpy_direct(sysm.pos, sysm.f, sysm.a, sysm.s)) < 1e-3
