@@ -113,3 +113,34 @@ def test_poisoned_request_fails_alone_and_cancel():
         assert st_c == (-7 if cancelled else 0)
     finally:
         rp.rpy_server_destroy(srv)
+
+
+def test_served_results_match_the_oracle_at_serving_sizes():
+    """Requests of the serving mix at realistic sizes (a 300k-bead cube in the 3-digit FP32
+    form and a 200k-bead sphere at 6 digits in FP64, jittered positions and fresh forces each
+    request, both resident, requests interleaved on three slots) meet their digit settings
+    against the oracle on sampled targets."""
+    import oracle
+    rng = np.random.default_rng(9)
+    n1, n2 = 300000, 200000
+    cube = rng.random((n1, 3))
+    sph = synth._sphere_surface(rng, n2, 0.5, (0.5, 0.5, 0.5))
+    a1, a2 = 0.5 / n1 ** (1 / 3), 0.5 / n2 ** (1 / 3)
+    srv = rp.rpy_server_create(slots=3)
+    try:
+        s1 = rp.rpy_server_add_system(srv, cube, a1, 3, precision=rp.RPY_FP32)
+        s2 = rp.rpy_server_add_system(srv, sph, a2, 6, precision=rp.RPY_FP64)
+        jobs = []
+        for r in range(6):
+            sid, base, a, tol = (s1, cube, a1, 1e-3) if r % 2 == 0 else (s2, sph, a2, 1e-6)
+            pos = base + 1e-3 * rng.standard_normal(base.shape)
+            f = rng.standard_normal(base.shape)
+            u = np.zeros_like(f)
+            jobs.append((rp.rpy_server_submit(srv, sid, pos, f, 6 * math.pi * a, u), pos, f, a, tol, u))
+        for rid, pos, f, a, tol, u in jobs:
+            assert rp.rpy_server_wait(srv, rid)[0] == 0
+            tg = synth.sample_targets(len(pos), 200, seed=rid)
+            ref = oracle.rpy_direct(pos, f, a, 6 * math.pi * a, targets=tg)
+            assert oracle.rel_l2(u[tg], ref) <= tol
+    finally:
+        rp.rpy_server_destroy(srv)
