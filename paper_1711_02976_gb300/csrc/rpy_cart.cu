@@ -23,6 +23,11 @@
 //         eta-derivative of L_k) and Q = sum_k P_kk,
 //         U_d[a] = C1 L_d[a] - C1 sum_k P_kd[a - e_k] + (C1/h) P_4d[a] - (C2/h^2) (a_d + 1) Q[a + e_d],
 //         u_d(x) = sum_a U_d[a] eta^a: three polynomials per leaf, evaluated per bead.
+// Multipoles are stored [box][monomial][4 sets] (one 16-byte load per monomial in FP32),
+// locals [box][4 sets][monomial].  The M2L terms of each a form a prefix of the graded
+// monomials b (those with |b| <= P - |a|), and each V-list offset's operator values
+// c_ab t_{a+b}(R) are tabulated per offset, so a term costs one table load, one multipole
+// load and four FMAs.
 // W- and X-list interactions are all summed directly (the tree's direct
 // substitutes), so M2P and P2L are not needed.  The Taylor coefficients of 1/|R + y|
 // follow the recurrence |g| |R|^2 t_g = -(2|g| - 1) sum_i R_i t_{g - e_i} - (|g| - 1) sum_i t_{g - 2 e_i}.
@@ -55,6 +60,7 @@ struct CartHost {
     // [it_of[a], it_of[a + 1])
     std::vector<int> it_a, it_k0, it_of;
     std::vector<double> dtab;             // [343][N] t_g(R), R = (i - 3, j - 3, k - 3), index 49 i + 7 j + k
+    std::vector<double> ktab;             // [343][pairs] c_ab t_{a+b}(R): the M2L operator per offset
     std::vector<int> mm_off, mm_b, mm_odd;    // M2M pairs (a, b <= a), odd-exponent mask of a - b
     std::vector<double> mm_c;             // prod C(a_i, b_i) 2^-b_i 4^-(a_i - b_i)
     std::vector<int> ll_off, ll_b, ll_odd;    // L2L pairs (a, b >= a)
@@ -133,6 +139,11 @@ void build_cart(int P, CartHost &h) {
             t[g] = s / (n * r2);
         }
     }
+    const size_t npair = h.m2l_b.size();
+    h.ktab.assign(size_t(343) * npair, 0.0);
+    for (int oi = 0; oi < 343; ++oi)
+        for (size_t k = 0; k < npair; ++k)
+            h.ktab[oi * npair + k] = h.m2l_c[k] * h.dtab[size_t(oi) * N + h.m2l_g[k]];
     // M2M and L2L pairs (octant signs applied on the device through the odd masks)
     h.mm_off.push_back(0);
     h.ll_off.push_back(0);
@@ -175,7 +186,8 @@ struct CartDev {
     const int *m2l_off, *m2l_b, *m2l_g;
     const T *m2l_c, *dtab;
     const int *it_a, *it_k0, *it_of;
-    int n_items;
+    int n_items, n_pairs;
+    const T *ktab;
     const int *mm_off, *mm_b, *mm_odd;
     const T *mm_c;
     const int *ll_off, *ll_b, *ll_odd;
@@ -222,6 +234,7 @@ void pack(const CartHost &h, std::vector<char> &blob, std::vector<size_t> &o) {
     putI(h.it_a);      // 15
     putI(h.it_k0);     // 16
     putI(h.it_of);     // 17
+    putT(h.ktab);      // 18
 }
 
 template <typename T>
@@ -248,6 +261,8 @@ CartDev<T> bind(const CartHost &h, const char *base, const std::vector<size_t> &
     d.it_k0 = reinterpret_cast<const int *>(base + o[16]);
     d.it_of = reinterpret_cast<const int *>(base + o[17]);
     d.n_items = int(h.it_a.size());
+    d.n_pairs = int(h.m2l_b.size());
+    d.ktab = reinterpret_cast<const T *>(base + o[18]);
     return d;
 }
 
@@ -290,6 +305,22 @@ int cart_terms(int P) { return (P + 1) * (P + 2) * (P + 3) / 6; }
 namespace {
 
 constexpr int kCartChunk = 64;   // beads staged per P2M round
+
+// the four sets of one monomial from a 16-byte aligned [monomial][4 sets] array
+__device__ __forceinline__ void load4(const float *p, float (&m)[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    m[0] = v.x;
+    m[1] = v.y;
+    m[2] = v.z;
+    m[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double *p, double (&m)[4]) {
+    const double2 v = reinterpret_cast<const double2 *>(p)[0], w = reinterpret_cast<const double2 *>(p)[1];
+    m[0] = v.x;
+    m[1] = v.y;
+    m[2] = w.x;
+    m[3] = w.y;
+}
 
 // P2M: one block per leaf at level >= 2; thread = monomial a (four sets); beads
 // staged with their powers of eta per axis; chunk sums enter the running sums by
@@ -354,7 +385,7 @@ __global__ void k_cart_p2m(int b0, int nb, CartDev<T> D, const int *beg, const i
         }
     }
     if (a < N)
-        for (int k = 0; k < kSets; ++k) M[(size_t(b) * kSets + k) * N + a] = acc[k];
+        for (int k = 0; k < kSets; ++k) M[(size_t(b) * N + a) * kSets + k] = acc[k];
 }
 
 // M2M: one block per parent (levels >= 2 with children); thread = monomial a.
@@ -382,7 +413,7 @@ __global__ void k_cart_m2m(int b0, int nb, CartDev<T> D, const int *leaf, const 
                 const int bi = D.mm_b[k];
                 const T cf = (__popc(D.mm_odd[k] & neg) & 1) ? -D.mm_c[k] : D.mm_c[k];
 #pragma unroll
-                for (int q = 0; q < kSets; ++q) s[q] = fma(cf, Mc[q * N + bi], s[q]);
+                for (int q = 0; q < kSets; ++q) s[q] = fma(cf, Mc[bi * kSets + q], s[q]);
             }
             // the fourth set about the parent's centre: + (c_C - c_P) . M_F
             const T dx = T((o & 1) ? hq : -hq), dy = T((o & 2) ? hq : -hq), dz = T((o & 4) ? hq : -hq);
@@ -393,15 +424,16 @@ __global__ void k_cart_m2m(int b0, int nb, CartDev<T> D, const int *leaf, const 
         }
     }
     if (a < N)
-        for (int q = 0; q < kSets; ++q) M[(size_t(b) * kSets + q) * N + a] = acc[q];
+        for (int q = 0; q < kSets; ++q) M[(size_t(b) * N + a) * kSets + q] = acc[q];
 }
 
-// M2L over the V list: one block per target box at level >= 2.  The pairs (a, b)
-// are split into work items of at most kCartRun pairs; each thread keeps the
-// partial sums of its items (up to kCartItems) over all sources in registers, and
-// the items of each a are added in a fixed order at the end (deterministic).  Each
-// source's multipole (set 4 moved to the target's centre) and its row of Taylor
-// coefficients are staged in shared memory.
+// M2L over the V list: one block per target box at level >= 2.  The terms of each
+// monomial a (b = 0 .. N_{P-|a|} - 1 in graded order) are split into work items of at
+// most kCartRun terms; each thread keeps the partial sums of its items (up to
+// kCartItems) over all sources in registers, and the items of each a are added in a
+// fixed order at the end (deterministic).  Each source's multipole ([monomial][4 sets],
+// set 4 moved to the target's centre) is staged in shared memory; the operator values
+// c_ab t_{a+b}(R) of its offset come from the per-offset table.
 template <typename T>
 __global__ void k_cart_m2l(int b0, int nb, CartDev<T> D, const int *voff, const int *vidx, const int *cell,
                            const double *side, const int *lvl, T *M, T *L) {
@@ -410,11 +442,24 @@ __global__ void k_cart_m2l(int b0, int nb, CartDev<T> D, const int *voff, const 
     if (lvl[b] < 2) return;
     const int nv = voff[b + 1] - voff[b];
     if (nv == 0) return;
-    const int N = D.N, NI = D.n_items;
-    T *Ms = reinterpret_cast<T *>(smem_raw);   // [4][N]
-    T *tr = Ms + kSets * N;                     // [N]
-    T *part = tr + N;                           // [NI][4]
+    const int N = D.N, NI = D.n_items, NP = D.n_pairs;
+    T *Ms = reinterpret_cast<T *>(smem_raw);   // [N][4]
+    T *part = Ms + kSets * N;                   // [NI][4]
     const double h = side[b];
+    // this thread's items: first term, term count, first b
+    int k0[kCartItems], kn[kCartItems], bb[kCartItems];
+#pragma unroll
+    for (int r = 0; r < kCartItems; ++r) {
+        const int it = threadIdx.x + r * blockDim.x;
+        k0[r] = 0;
+        kn[r] = 0;
+        bb[r] = 0;
+        if (it < NI) {
+            k0[r] = D.it_k0[it];
+            kn[r] = D.it_k0[it + 1] - k0[r];
+            bb[r] = k0[r] - D.m2l_off[D.it_a[it]];
+        }
+    }
     T acc[kCartItems][kSets];
 #pragma unroll
     for (int r = 0; r < kCartItems; ++r)
@@ -425,30 +470,27 @@ __global__ void k_cart_m2l(int b0, int nb, CartDev<T> D, const int *voff, const 
         // R = (c_T - c_S) / h from the integer cells (same level)
         const int rx = cell[3 * b] - cell[3 * S], ry = cell[3 * b + 1] - cell[3 * S + 1],
                   rz = cell[3 * b + 2] - cell[3 * S + 2];
-        const int oi = (rx + 3) * 49 + (ry + 3) * 7 + (rz + 3);
+        const T *kt = D.ktab + size_t((rx + 3) * 49 + (ry + 3) * 7 + (rz + 3)) * NP;
         // the fourth set about the target's centre: + (c_S - c_T) . M_F = -h R . M_F
         const T dx = T(-h * rx), dy = T(-h * ry), dz = T(-h * rz);
         __syncthreads();
         for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            const T *src = M + size_t(S) * kSets * N;
-            const T m0 = src[i], m1 = src[N + i], m2 = src[2 * N + i];
-            Ms[i] = m0;
-            Ms[N + i] = m1;
-            Ms[2 * N + i] = m2;
-            Ms[3 * N + i] = fma(dz, m2, fma(dy, m1, fma(dx, m0, src[3 * N + i])));
-            tr[i] = D.dtab[size_t(oi) * N + i];
+            const T *src = M + (size_t(S) * N + i) * kSets;
+            const T m0 = src[0], m1 = src[1], m2 = src[2];
+            Ms[kSets * i] = m0;
+            Ms[kSets * i + 1] = m1;
+            Ms[kSets * i + 2] = m2;
+            Ms[kSets * i + 3] = fma(dz, m2, fma(dy, m1, fma(dx, m0, src[3])));
         }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < kCartItems; ++r) {
-            const int it = threadIdx.x + r * blockDim.x;
-            if (it < NI) {
-                for (int k = D.it_k0[it]; k < D.it_k0[it + 1]; ++k) {
-                    const int bi = D.m2l_b[k];
-                    const T cf = D.m2l_c[k] * tr[D.m2l_g[k]];
+            for (int i = 0; i < kn[r]; ++i) {
+                const T cf = kt[k0[r] + i];
+                T m[kSets];
+                load4(Ms + kSets * (bb[r] + i), m);
 #pragma unroll
-                    for (int q = 0; q < kSets; ++q) acc[r][q] = fma(cf, Ms[q * N + bi], acc[r][q]);
-                }
+                for (int q = 0; q < kSets; ++q) acc[r][q] = fma(cf, m[q], acc[r][q]);
             }
         }
     }
@@ -627,7 +669,7 @@ int run_cart_t(Tree &t, const double *fs, double *ufar, const SysConst &sc, cuda
     {
         const int mt = std::max(64, ((D.n_items + kCartItems - 1) / kCartItems + 31) / 32 * 32);
         if (mt > 1024) return RPY_ERR_INTERNAL;
-        const size_t sm = s4 + sizeof(T) * (N + size_t(kSets) * D.n_items);
+        const size_t sm = s4 + sizeof(T) * size_t(kSets) * D.n_items;
         RPY_TRY(set_cart_smem(k_cart_m2l<T>, sm));
         k_cart_m2l<T><<<n2, mt, sm, st>>>(b2, n2, D, t.v_off, t.v_idx, t.b_cell, t.b_side, t.b_level, M, L);
     }
