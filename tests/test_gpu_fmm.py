@@ -767,3 +767,27 @@ def test_bounded_device_wait_times_out_and_context_stays_usable():
     sysm = synth.config1()
     u, t = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, 3, leaf_cap=40)
     assert oracle.rel_l2(u, oracle.rpy_direct(sysm.pos, sysm.f, sysm.a, sysm.s)) < 1e-3
+
+
+def test_tree_work_counts_match_the_tree():
+    """rpy_tree_work's per-stage numerators follow the tree: the near field counts 38 FLOP
+    (FP64) or 33 (FP32) per near-list pair and 72 / 60 B per bead; every far-field stage of an
+    FMM tree has work; the Cartesian form counts its multipole-to-local step under X2L from the
+    V-list pairs, with nothing under M2X, X2X and P2L."""
+    sysm = synth.sphere_plus_cube(50000, 81, 1e-4)
+    for prec, per_pair, per_bead in ((rp.RPY_FP64, 38.0, 72.0), (rp.RPY_FP32, 33.0, 60.0)):
+        u, t = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, 6, leaf_cap=40, precision=prec)
+        st = rp.rpy_tree_stats(t)
+        w = rp.rpy_tree_work(t)
+        assert w["p2p"][0] == per_pair * (st["u_pairs"] + st["d_pairs"])
+        assert w["p2p"][1] == per_bead * sysm.n
+        for k in ("p2m", "m2m", "m2x", "x2x", "x2l", "l2l", "eval"):
+            assert w[k][0] > 0 and w[k][1] > 0, k
+    u, t = matvec(sysm.pos, sysm.f, sysm.a, sysm.s, 3, leaf_cap=40, flags=rp.RPY_FLAG_CARTESIAN)
+    st = rp.rpy_tree_stats(t)
+    w = rp.rpy_tree_work(t)
+    P = st["order_p"]
+    terms = sum(math.comb(P - d + 3, 3) * (d + 1) * (d + 2) // 2 for d in range(P + 1))   # |a| + |b| <= P
+    assert terms == math.comb(P + 6, 6)
+    assert w["x2l"][0] == st["n_vpairs"] * terms * 4 * 2
+    assert w["m2x"] == (0.0, 0.0) and w["x2x"] == (0.0, 0.0) and w["p2l"] == (0.0, 0.0)
