@@ -17,8 +17,9 @@
 // which brings the relative error from ~1e-7 to ~1e-14.
 // FP32 form (precision setting, k_p2p32): positions relative to the target
 // leaf centre in FP32; every thread carries two targets as two independent
-// scalar FP32 chains per staged source; both branches are evaluated without
-// divergence; accumulation is Kahan-compensated across blocks of kP32Block
+// scalar FP32 chains per staged source; an iteration whose pairs are all far
+// (across the warp) evaluates the far branch alone, any other evaluates both
+// branches without divergence; accumulation is Kahan-compensated across blocks of kP32Block
 // sources; pairs closer than 1e-3 a (where the FP32 difference of coordinates
 // loses the direction) are recomputed in FP64 from the FP64 positions.
 #include <cmath>
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p(const int2 *items, const in
 
 // ---------------------------------------------------------------- FP32 form
 constexpr int kP32Threads = 256;
-constexpr int kP32Chunk = 1024;    // sources staged per pass
+constexpr int kP32Chunk = 512;     // sources staged per pass
 constexpr int kP32List = 256;      // list boxes per prefix segment
 constexpr int kP32Block = 32;      // sources per plain FP32 block between Kahan merges
 
@@ -266,6 +267,33 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, f
     pz = fmaf(t2, dz, fmaf(t1, fz, pz));
 }
 
+// Packed forms over the two targets of a thread (lane .x target a, lane .y
+// target b) and one staged source.  x - x_j is formed as x + (-x_j), which
+// rounds as the difference does.
+__device__ __forceinline__ float2 packed_d(float2 X, float nx0, float nx1) {
+    return __fadd2_rn(X, make_float2(nx0, nx1));
+}
+
+__device__ __forceinline__ float2 packed_r2(float2 DX, float2 DY, float2 DZ) {
+    return __ffma2_rn(DZ, DZ, __ffma2_rn(DY, DY, __fmul2_rn(DX, DX)));
+}
+
+// The r >= 2a branch of pair32 on both lanes, for pairs known to be far (the
+// clamp and the selects of pair32 are then the identity): the same operations
+// in the same order, hence the same rounding lane by lane.
+__device__ __forceinline__ void far_packed(float2 DX, float2 DY, float2 DZ, float2 R2, float2 FX, float2 FY,
+                                           float2 FZ, float2 K23, float2 NK2, float2 &AX, float2 &AY, float2 &AZ) {
+    const float2 RI = make_float2(rsqrt_ftz(R2.x), rsqrt_ftz(R2.y));
+    const float2 RI2 = __fmul2_rn(RI, RI);
+    const float2 B = __fmul2_rn(RI, RI2);
+    const float2 T1 = __ffma2_rn(K23, B, RI);
+    const float2 C = __fmul2_rn(B, __ffma2_rn(NK2, RI2, make_float2(1.f, 1.f)));
+    const float2 T2 = __fmul2_rn(C, __ffma2_rn(DZ, FZ, __ffma2_rn(DY, FY, __fmul2_rn(DX, FX))));
+    AX = __ffma2_rn(T2, DX, __ffma2_rn(T1, FX, AX));
+    AY = __ffma2_rn(T2, DY, __ffma2_rn(T1, FY, AY));
+    AZ = __ffma2_rn(T2, DZ, __ffma2_rn(T1, FZ, AZ));
+}
+
 __device__ __forceinline__ void kahan_merge(float &s, float &c, float v) {
     float y = v - c;
     float t = s + y;
@@ -279,7 +307,7 @@ __device__ __forceinline__ void kahan_merge(float &s, float &c, float v) {
 // prefix-summed in shared memory and each staged bead finds its box by
 // binary search.
 constexpr int kP32Queue = 256;   // FP64 pairs of one staged chunk handled after its FP32 loop
-constexpr size_t kP32Smem = sizeof(float4) * kP32Chunk + sizeof(float2) * kP32Chunk + sizeof(int) * kP32Chunk +
+constexpr size_t kP32Smem = sizeof(float4) * 3 * kP32Chunk + sizeof(int) * kP32Chunk +
                             sizeof(float2) * 6 * kP32Threads + sizeof(double) * 6 * kP32Threads +
                             sizeof(int) * (2 * kP32List + 2) + sizeof(float) * 6 + sizeof(int) * (kP32Queue + 2);
 
@@ -290,9 +318,10 @@ __global__ void __launch_bounds__(kP32Threads, 4) k_p2p32(const int2 *items, con
                                                          const double *pos, const double *fs, int64_t n, SysConst sc,
                                                          int add_self, double *out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4 *sP = reinterpret_cast<float4 *>(smem_raw);       // (x, y, z) relative to the target leaf centre, fx
-    float2 *sQ2 = reinterpret_cast<float2 *>(sP + kP32Chunk);  // fy, fz
-    float2 *sK = sQ2 + kP32Chunk;                              // [6][kP32Threads] Kahan states (S, C)
+    // staged source e, relative to the target leaf centre, each value twice (both lanes of a
+    // packed pair): sS[3e] = (-x, -x, -y, -y), sS[3e+1] = (-z, -z, fx, fx), sS[3e+2] = (fy, fy, fz, fz)
+    float4 *sS = reinterpret_cast<float4 *>(smem_raw);
+    float2 *sK = reinterpret_cast<float2 *>(sS + 3 * kP32Chunk);   // [6][kP32Threads] Kahan states (S, C)
     double *sD = reinterpret_cast<double *>(sK + 6 * kP32Threads);   // [kP32Threads][6] FP64 pairs
     int *sJ = reinterpret_cast<int *>(sD + 6 * kP32Threads);
     int *lb = sJ + kP32Chunk, *lpre = lb + kP32List;
@@ -321,6 +350,7 @@ __global__ void __launch_bounds__(kP32Threads, 4) k_p2p32(const int2 *items, con
     __syncthreads();
     const float chx = sCtr[0], chy = sCtr[1], chz = sCtr[2], clx = sCtr[3], cly = sCtr[4], clz = sCtr[5];
     const float *xh = p32, *yh = p32 + n, *zh = p32 + 2 * n, *xl = p32 + 3 * n, *yl = p32 + 4 * n, *zl = p32 + 5 * n;
+    const float2 K23 = make_float2(k.k23, k.k23), NK2 = make_float2(k.nk2, k.nk2);
     const int u0 = uoff[li], u1 = uoff[li + 1];
     const int tb = item.y, te = min(end[b], item.y + kItemTargets), nt = te - tb;
     const int half = (nt + 1) / 2;
@@ -339,6 +369,7 @@ __global__ void __launch_bounds__(kP32Threads, 4) k_p2p32(const int2 *items, con
         const float xb = actb ? (xh[ib] - chx) + (xl[ib] - clx) : 1e15f;
         const float yb = actb ? (yh[ib] - chy) + (yl[ib] - cly) : 1e15f;
         const float zb = actb ? (zh[ib] - chz) + (zl[ib] - clz) : 1e15f;
+        const float2 X = make_float2(xa, xb), Y = make_float2(ya, yb), Z = make_float2(za, zb);
         for (int c = 0; c < 6; ++c) {
             sK[c * kP32Threads + threadIdx.x] = make_float2(0.f, 0.f);
             sD[6 * threadIdx.x + c] = 0.0;
@@ -373,7 +404,7 @@ __global__ void __launch_bounds__(kP32Threads, 4) k_p2p32(const int2 *items, con
                 const int nS = min(kP32Chunk, Ns - c0);
                 // no barrier here: the one after the prefix (first chunk) or after the
                 // previous chunk's compute (and its FP64 queue pass) already orders
-                // every read of sP, sQ2 and sJ before this chunk's writes
+                // every read of sS and sJ before this chunk's writes
                 for (int e = threadIdx.x; e < nS; e += kP32Threads) {
                     int q = c0 + e, lo = 0, hi = L;   // box: lpre[lo] <= q < lpre[lo + 1]
                     while (hi - lo > 1) {
@@ -382,40 +413,77 @@ __global__ void __launch_bounds__(kP32Threads, 4) k_p2p32(const int2 *items, con
                         else hi = mid;
                     }
                     int j = lb[lo] + (q - lpre[lo]);
-                    sP[e] = make_float4((xh[j] - chx) + (xl[j] - clx), (yh[j] - chy) + (yl[j] - cly),
-                                        (zh[j] - chz) + (zl[j] - clz), f32[j]);
-                    sQ2[e] = make_float2(f32[n + j], f32[2 * n + j]);
+                    const float px = (xh[j] - chx) + (xl[j] - clx), py = (yh[j] - chy) + (yl[j] - cly),
+                                pz = (zh[j] - chz) + (zl[j] - clz);
+                    const float fx = f32[j], fy = f32[n + j], fz = f32[2 * n + j];
+                    sS[3 * e] = make_float4(-px, -px, -py, -py);
+                    sS[3 * e + 1] = make_float4(-pz, -pz, fx, fx);
+                    sS[3 * e + 2] = make_float4(fy, fy, fz, fz);
                     sJ[e] = j;
                 }
                 __syncthreads();
                 if (act) {
                     for (int jb = g; jb < nS; jb += kP32Block * G) {
                         const int je = min(nS, jb + kP32Block * G);
-                        float Pax = 0, Pay = 0, Paz = 0, Pbx = 0, Pby = 0, Pbz = 0;
-#pragma unroll 1
-                        for (int jj = jb; jj < je; jj += G) {
-                            const float4 P = sP[jj];
-                            const float2 Q = sQ2[jj];
-                            const float dxa = xa - P.x, dya = ya - P.y, dza = za - P.z;
-                            const float dxb = xb - P.x, dyb = yb - P.y, dzb = zb - P.z;
-                            const float r2a = fmaf(dza, dza, fmaf(dya, dya, dxa * dxa));
-                            const float r2b = fmaf(dzb, dzb, fmaf(dyb, dyb, dxb * dxb));
-                            pair32(dxa, dya, dza, r2a, P.w, Q.x, Q.y, k, Pax, Pay, Paz);
-                            pair32(dxb, dyb, dzb, r2b, P.w, Q.x, Q.y, k, Pbx, Pby, Pbz);
-                            if (!(r2a > k.tiny2) || !(r2b > k.tiny2)) {
+                        // accumulators: lane .x for target a, lane .y for target b
+                        float2 AX = make_float2(0.f, 0.f), AY = AX, AZ = AX;
+                        // both branches with selects per target, and the close-pair queue
+                        auto slow = [&](int jj, float2 DX, float2 DY, float2 DZ, float2 R2, float2 FX, float2 FY,
+                                        float2 FZ) {
+                            pair32(DX.x, DY.x, DZ.x, R2.x, FX.x, FY.x, FZ.x, k, AX.x, AY.x, AZ.x);
+                            pair32(DX.y, DY.y, DZ.y, R2.y, FX.x, FY.x, FZ.x, k, AX.y, AY.y, AZ.y);
+                            if (!(R2.x > k.tiny2) || !(R2.y > k.tiny2)) {
                                 // the self pair, or beads within 1e-3 a: queue all but the self pair
                                 const int jg = sJ[jj];
-                                if (!(r2a > k.tiny2) && jg != ia) {
+                                if (!(R2.x > k.tiny2) && jg != ia) {
                                     int q = atomicAdd(&sQn[0], 1);
                                     if (q < kP32Queue) sQ[q] = (threadIdx.x << 11) | (jj << 1);
                                 }
-                                if (actb && !(r2b > k.tiny2) && jg != ib) {
+                                if (actb && !(R2.y > k.tiny2) && jg != ib) {
                                     int q = atomicAdd(&sQn[0], 1);
                                     if (q < kP32Queue) sQ[q] = (threadIdx.x << 11) | (jj << 1) | 1;
                                 }
                             }
+                        };
+                        // Two staged sources per iteration: two independent packed chains.  When
+                        // every pair of the lanes running the iteration is far (a warp-uniform
+                        // vote), the far branch alone on packed pairs, the same operations as
+                        // pair32's far branch lane by lane; otherwise the slow form above.
+                        int jj = jb;
+                        for (; jj + G < je; jj += 2 * G) {
+                            const int j1 = jj + G;
+                            const float4 S0 = sS[3 * jj], S1 = sS[3 * jj + 1], S2 = sS[3 * jj + 2];
+                            const float4 U0 = sS[3 * j1], U1 = sS[3 * j1 + 1], U2 = sS[3 * j1 + 2];
+                            const float2 DX = packed_d(X, S0.x, S0.y), DY = packed_d(Y, S0.z, S0.w),
+                                         DZ = packed_d(Z, S1.x, S1.y);
+                            const float2 EX = packed_d(X, U0.x, U0.y), EY = packed_d(Y, U0.z, U0.w),
+                                         EZ = packed_d(Z, U1.x, U1.y);
+                            const float2 R2 = packed_r2(DX, DY, DZ), Q2 = packed_r2(EX, EY, EZ);
+                            const float2 FX = make_float2(S1.z, S1.w), FY = make_float2(S2.x, S2.y),
+                                         FZ = make_float2(S2.z, S2.w);
+                            const float2 GX = make_float2(U1.z, U1.w), GY = make_float2(U2.x, U2.y),
+                                         GZ = make_float2(U2.z, U2.w);
+                            if (__all_sync(__activemask(), fminf(fminf(R2.x, R2.y), fminf(Q2.x, Q2.y)) >= k.a2x4)) {
+                                far_packed(DX, DY, DZ, R2, FX, FY, FZ, K23, NK2, AX, AY, AZ);
+                                far_packed(EX, EY, EZ, Q2, GX, GY, GZ, K23, NK2, AX, AY, AZ);
+                                continue;
+                            }
+                            slow(jj, DX, DY, DZ, R2, FX, FY, FZ);
+                            slow(j1, EX, EY, EZ, Q2, GX, GY, GZ);
                         }
-                        const float Pv[6] = {Pax, Pay, Paz, Pbx, Pby, Pbz};
+                        if (jj < je) {
+                            const float4 S0 = sS[3 * jj], S1 = sS[3 * jj + 1], S2 = sS[3 * jj + 2];
+                            const float2 DX = packed_d(X, S0.x, S0.y), DY = packed_d(Y, S0.z, S0.w),
+                                         DZ = packed_d(Z, S1.x, S1.y);
+                            const float2 R2 = packed_r2(DX, DY, DZ);
+                            const float2 FX = make_float2(S1.z, S1.w), FY = make_float2(S2.x, S2.y),
+                                         FZ = make_float2(S2.z, S2.w);
+                            if (__all_sync(__activemask(), fminf(R2.x, R2.y) >= k.a2x4))
+                                far_packed(DX, DY, DZ, R2, FX, FY, FZ, K23, NK2, AX, AY, AZ);
+                            else
+                                slow(jj, DX, DY, DZ, R2, FX, FY, FZ);
+                        }
+                        const float Pv[6] = {AX.x, AY.x, AZ.x, AX.y, AY.y, AZ.y};
 #pragma unroll
                         for (int c = 0; c < 6; ++c) {
                             float2 kc = sK[c * kP32Threads + threadIdx.x];
@@ -439,10 +507,10 @@ __global__ void __launch_bounds__(kP32Threads, 4) k_p2p32(const int2 *items, con
                         }
                     } else if (act) {
                         for (int jj = g; jj < nS; jj += G) {
-                            const float4 P = sP[jj];
+                            const float4 S0 = sS[3 * jj], S1 = sS[3 * jj + 1];
                             const int jg = sJ[jj];
                             for (int h = 0; h < 2; ++h) {
-                                const float dx = (h ? xb : xa) - P.x, dy = (h ? yb : ya) - P.y, dz = (h ? zb : za) - P.z;
+                                const float dx = (h ? xb : xa) + S0.x, dy = (h ? yb : ya) + S0.z, dz = (h ? zb : za) + S1.x;
                                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                                 const int i = h ? ib : ia;
                                 if (!(r2 > k.tiny2) && jg != i && (h == 0 || actb))
