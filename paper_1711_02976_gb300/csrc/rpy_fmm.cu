@@ -32,8 +32,6 @@
 
 namespace rpy {
 
-constexpr double kPi = 3.14159265358979323846;
-
 __device__ __forceinline__ int deg_of(int idx) {
     int n = int((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
     while (tri(n + 1, 0) <= idx) ++n;

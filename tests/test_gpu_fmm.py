@@ -164,6 +164,28 @@ def test_fp32_near_part_matches_oracle_on_u_lists(a):
     assert np.abs(u - ref).max() < 2e-6 * np.abs(ref).max()
 
 
+def test_fp32_close_pairs_beyond_the_queue():
+    """A cluster of 48 beads within 1e-4 a of one point (a quarter of them coincident) sits in
+    one leaf (the 2a rule stops refinement there): 2,256 ordered pairs closer than 1e-3 a meet
+    in one staged chunk, more than the near-field kernel's shared-memory queue holds, so every
+    thread re-scans its sources for them in FP64.  The FP32 near part still matches the oracle."""
+    rng = np.random.default_rng(17)
+    n, a = 3000, 0.002
+    pos = rng.random((n, 3)) * 0.9 + 0.05
+    c0 = pos[0].copy()
+    for k in range(1, 48):
+        d = rng.standard_normal(3)
+        pos[k] = c0 if k % 4 == 0 else c0 + 1e-4 * a * rng.random() * d / np.linalg.norm(d)
+    f = rng.standard_normal((n, 3))
+    s = 6 * math.pi * a
+    u, t = matvec(pos, f, a, s, 3, leaf_cap=40, precision=rp.RPY_FP32, parts=rp.RPY_PART_NEAR)
+    assert rp.rpy_tree_stats(t)["max_leaf_count"] >= 48
+    ref = _near_oracle(t, pos, f, a, s)
+    assert np.abs(u - ref).max() < 2e-6 * np.abs(ref).max()
+    # the cluster's beads themselves (their sums are dominated by the close pairs)
+    np.testing.assert_allclose(u[:48], ref[:48], rtol=0, atol=2e-6 * np.abs(ref[:48]).max())
+
+
 # ---------------------------------------------------------------- far field operators
 
 @pytest.mark.parametrize("digits,tol", [(3, 1e-3), (6, 1e-6), (9, 1e-9)])
