@@ -538,7 +538,7 @@ def serving(args, local, loads=(0.7,), n_req=None):
     import paper_1711_02976_gb300 as rp
     import synth
     torch.cuda.set_device(local)
-    n_req = n_req or args.serve_requests
+    n_req = n_req or args.serve_requests or 1000
     systems = synth.config5(nsys=args.serve_systems)
     srv = rp.rpy_server_create(slots=args.serve_slots)
     for k, sy in enumerate(systems):
@@ -591,7 +591,7 @@ def serving(args, local, loads=(0.7,), n_req=None):
 
 
 def serve(args, local):
-    out = serving(args, local, loads=(0.3, 0.5, 0.7, 0.9))
+    out = serving(args, local, loads=(0.3, 0.5, 0.7, 0.9), n_req=args.serve_requests or 2000)
     out.update({"mode": "serve", "metric": "served RPY matvec Mbeads/s (mixed 3-digit FP32 / 6-digit FP64)"})
     return out
 
@@ -656,7 +656,9 @@ def main():
                          "e.g. to profile the autotuned configuration")
     ap.add_argument("--mode", default="bench", choices=["bench", "serve", "bd"])
     ap.add_argument("--serve-systems", type=int, default=64)
-    ap.add_argument("--serve-requests", type=int, default=1000, help="requests per arrival rate")
+    ap.add_argument("--serve-requests", type=int, default=None,
+                    help="requests per arrival rate (default: 1,000 in the default run's serving object, "
+                         "2,000 per rate with --mode serve)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement of the default run")
     ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
