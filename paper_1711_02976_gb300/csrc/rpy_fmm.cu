@@ -1401,9 +1401,12 @@ __global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi,
     float4 *PIm = PRe + S;
     float4 *MRe = PIm + S;                                  // - direction
     float4 *MIm = MRe + S;
-    cpx<float> *Bs = reinterpret_cast<cpx<float> *>(MIm + S);   // [s][P1][4] b+ + b-
-    cpx<float> *Bd = Bs + kSets * s * P1;                         // [s][P1][4] b+ - b-
-    cpx<float> *Lf = Bd + kSets * s * P1;                         // [4][nc]
+    // b+ + b- (Bs) and b+ - b- (Bd) per (node, m), as planes of set pairs: (re, im) of sets
+    // 0 and 1, then of sets 2 and 3, so that each thread's 16-byte stores are contiguous
+    // across lanes (one [s][P1][4] array took four 8-byte stores 32 bytes apart)
+    const int SP = s * P1;
+    float4 *Bs01 = MIm + S, *Bs23 = Bs01 + SP, *Bd01 = Bs23 + SP, *Bd23 = Bd01 + SP;
+    cpx<float> *Lf = reinterpret_cast<cpx<float> *>(Bd23 + SP);                  // [4][nc]
     cpx<float> *Lw = Lf + kSets * nc;
     cpx<float> *Lr = Lw + kSets * nc;
     cpx<float> *Tm = Lr + kSets * nc;                             // rotation scratch
@@ -1446,17 +1449,17 @@ __global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi,
                 idx += mm;
                 if (idx >= Mk) idx -= Mk;
             }
-#pragma unroll
-            for (int st = 0; st < kSets; ++st) {
-                Bs[e * kSets + st] = mk(bpx[st] + bmx[st], bpy[st] + bmy[st]);
-                Bd[e * kSets + st] = mk(bpx[st] - bmx[st], bpy[st] - bmy[st]);
-            }
+            Bs01[e] = make_float4(bpx[0] + bmx[0], bpy[0] + bmy[0], bpx[1] + bmx[1], bpy[1] + bmy[1]);
+            Bs23[e] = make_float4(bpx[2] + bmx[2], bpy[2] + bmy[2], bpx[3] + bmx[3], bpy[3] + bmy[3]);
+            Bd01[e] = make_float4(bpx[0] - bmx[0], bpy[0] - bmy[0], bpx[1] - bmx[1], bpy[1] - bmy[1]);
+            Bd23[e] = make_float4(bpx[2] - bmx[2], bpy[2] - bmy[2], bpx[3] - bmx[3], bpy[3] - bmy[3]);
         }
         __syncthreads();
         // L_n^m = i^m sum_k (-lambda_k)^n / sqrt((n-m)!(n+m)!) b_k^m, the - direction reflected
         for (int i = threadIdx.x; i < nc; i += blockDim.x) {
             const int n = deg_of(i), m = i - tri(n, 0);
-            const cpx<float> *Bx = ((n + m) & 1) ? Bd : Bs;
+            const bool odd = (n + m) & 1;
+            const float4 *B01 = odd ? Bd01 : Bs01, *B23 = odd ? Bd23 : Bs23;
             // sum over the quadrature nodes with compensated (Kahan) addition: the terms
             // (-lambda_k)^n b_k^m alternate in sign and cancel strongly at high degree
             float ax[kSets] = {0, 0, 0, 0}, ay[kSets] = {0, 0, 0, 0};
@@ -1468,8 +1471,7 @@ __global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi,
             };
             for (int k = 0; k < s; ++k) {
                 const float c = D.x2l_c[size_t(k) * nc + i];
-                const float4 *bb = reinterpret_cast<const float4 *>(Bx + (k * P1 + m) * kSets);
-                const float4 b01 = bb[0], b23 = bb[1];
+                const float4 b01 = B01[k * P1 + m], b23 = B23[k * P1 + m];
                 kahan(ax[0], cx[0], c * b01.x);
                 kahan(ay[0], cy[0], c * b01.y);
                 kahan(ax[1], cx[1], c * b01.z);
