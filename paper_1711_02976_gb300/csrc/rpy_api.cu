@@ -340,7 +340,7 @@ static int alloc_tree_arrays(Tree &t, cudaStream_t st) {
 }
 
 int tree_alloc_workspace(Tree &t, cudaStream_t st) {
-    const OpTables &h = t.tabs;
+    const OpTables &h = *t.tabs;
     size_t es = t.params.precision == RPY_FP32 ? sizeof(cpx<float>) : sizeof(cpx<double>);
     size_t nb = size_t(t.nbox);
     if (t.params.flags & RPY_FLAG_CARTESIAN) {
@@ -390,7 +390,7 @@ static int do_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     RPY_TRY(tree_build(t, pos_dev, st));
     OpTables *h = nullptr;
     RPY_TRY(host_tables(t.p, t.params.quad, &h));
-    t.tabs = *h;   // small copy of the host description (sizes used by workspace / stats)
+    t.tabs = h;   // the host description (sizes used by workspace / stats), cached for the process
     DevTableSet *ds = nullptr;
     RPY_TRY(device_tables(t.device, t.p, t.params.quad, &ds));
     t.dt64 = ds->d64;
@@ -903,8 +903,8 @@ int rpy_tree_stats(rpy_tree h, rpy_stats *o) {
     o->n_leaves = t.nleaf;
     o->depth = t.nlevels - 1;
     o->order_p = t.p;
-    o->exp_nodes = t.tabs.s;
-    o->exp_terms = 2 * t.tabs.S;
+    o->exp_nodes = t.tabs ? t.tabs->s : 0;
+    o->exp_terms = t.tabs ? 2 * t.tabs->S : 0;
     o->leaf_cap = t.params.leaf_cap;
     o->digits = t.params.digits;
     o->precision = t.params.precision;

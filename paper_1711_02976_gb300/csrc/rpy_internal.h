@@ -263,7 +263,7 @@ struct Tree {
     int *v_off = nullptr, *v_idx = nullptr;
     int64_t n_v = 0;
     // tables
-    OpTables tabs;
+    const OpTables *tabs = nullptr;   // the cached host tables of (p, quadrature rule); never freed
     void *dtabs_mem = nullptr;        // one device block holding all tables
     DevTables<double> dt64{};
     DevTables<float> dt32{};

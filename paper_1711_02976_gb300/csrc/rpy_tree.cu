@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <set>
 
 #include "rpy_internal.h"
 
@@ -189,6 +190,12 @@ static void scan_rec(const int *in, int *out, int n, char *tmp, cudaStream_t st)
     RPY_LAUNCHED(1);
 }
 
+// *dst = sum of in[0 .. n) after an exclusive scan of it into out (in != out), on the
+// device, so that several scans' totals come back in one copy and one synchronisation.
+__global__ void k_scan_total(const int *in, const int *out, int n, int *dst) {
+    if (threadIdx.x == 0) *dst = n > 0 ? out[n - 1] + in[n - 1] : 0;
+}
+
 // out[i] = sum_{j<i} in[j]; if total_host, *total_host = sum of all (synchronises st).
 int exclusive_scan_i32(const int *in, int *out, int n, int *total_host, void *tmp, size_t tmp_bytes,
                        cudaStream_t st) {
@@ -228,10 +235,22 @@ __global__ void k_radix_hist(const uint64_t *keys, int n, int shift, int *counts
 }
 
 // Stable scatter: ranks inside the tile follow the input order (warp by warp,
-// 32-item rounds in order), tiles are laid out in input order by the scan.
-__global__ void k_radix_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout, int n,
-                                int shift, const int *offs, int ntiles) {
+// 32-item rounds in order), tiles are laid out in input order by the scan.  The
+// tile is first reordered by digit in shared memory, then written out slot by
+// slot, so that consecutive threads store consecutive elements of one digit's run
+// (a direct store from the ranking registers sends a warp's 32 stores to up to
+// 32 different runs).
+constexpr size_t kSortScatterSmem = (sizeof(uint64_t) + sizeof(uint32_t)) * kSortTile;
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t *kin, const uint32_t *vin,
+                                                                uint64_t *kout, uint32_t *vout, int n, int shift,
+                                                                const int *offs, int ntiles) {
     __shared__ int wh[kSortWarps][257];
+    __shared__ int wb[kSortWarps][256];
+    __shared__ int tstart[257];   // first slot of each digit in the reordered tile; [256] = valid items
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sk + kSortTile);
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < kSortWarps * 257; i += blockDim.x) (&wh[0][0])[i] = 0;
     __syncthreads();
@@ -261,28 +280,61 @@ __global__ void k_radix_scatter(const uint64_t *kin, const uint32_t *vin, uint64
         rk[r] = b + pre;
     }
     __syncthreads();
-    __shared__ int wb[kSortWarps][256];
     for (int d = threadIdx.x; d < 256; d += blockDim.x) {
         int s = 0;
         for (int w = 0; w < kSortWarps; ++w) {
             wb[w][d] = s;
             s += wh[w][d];
         }
+        tstart[d] = s;   // this tile's count of digit d, scanned below
+    }
+    __syncthreads();
+    {
+        const int c = threadIdx.x < 256 ? tstart[threadIdx.x] : 0;
+        int total;
+        const int ex = block_exclusive_scan(c, &total);
+        if (threadIdx.x < 256) tstart[threadIdx.x] = ex;
+        if (threadIdx.x == 0) tstart[256] = total;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         if (dg[r] < 256) {
-            int pos = offs[dg[r] * ntiles + blockIdx.x] + wb[warp][dg[r]] + rk[r];
-            kout[pos] = k[r];
-            vout[pos] = v[r];
+            const int lp = tstart[dg[r]] + wb[warp][dg[r]] + rk[r];
+            sk[lp] = k[r];
+            sv[lp] = v[r];
         }
     }
+    __syncthreads();
+    const int nt = tstart[256];
+    for (int q = threadIdx.x; q < nt; q += blockDim.x) {
+        const uint64_t key = sk[q];
+        const int d = int((key >> shift) & 255);
+        const int pos = offs[d * ntiles + blockIdx.x] + (q - tstart[d]);
+        kout[pos] = key;
+        vout[pos] = sv[q];
+    }
+}
+
+// The scatter's dynamic shared memory (the reordered tile) exceeds the default
+// 48 KB together with its static arrays: raise the limit once per device.
+static cudaError_t set_scatter_smem() {
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(dev)) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSortScatterSmem));
+    if (e == cudaSuccess) done.insert(dev);
+    return e;
 }
 
 // Sort (keys, vals) by bits [0, bits) stably.  Result ends in (k0, v0).
 static int radix_sort(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int n, int bits, int *counts,
                       void *scan_tmp, size_t scan_bytes, cudaStream_t st) {
+    RPY_CHECK(set_scatter_smem());
     int ntiles = (n + kSortTile - 1) / kSortTile;
     int passes = (bits + 7) / 8;
     for (int pss = 0; pss < passes; ++pss) {
@@ -290,7 +342,7 @@ static int radix_sort(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, in
         k_radix_hist<<<ntiles, kSortThreads, 0, st>>>(k0, n, shift, counts, ntiles);
         RPY_LAUNCHED(1);
         RPY_TRY(exclusive_scan_i32(counts, counts, 256 * ntiles, nullptr, scan_tmp, scan_bytes, st));
-        k_radix_scatter<<<ntiles, kSortThreads, 0, st>>>(k0, v0, k1, v1, n, shift, counts, ntiles);
+        k_radix_scatter<<<ntiles, kSortThreads, kSortScatterSmem, st>>>(k0, v0, k1, v1, n, shift, counts, ntiles);
         RPY_LAUNCHED(1);
         RPY_CHECK(cudaGetLastError());
         std::swap(k0, k1);
@@ -337,20 +389,45 @@ __global__ void k_bbox_partial(const double *pos, const int64_t *cb, const int64
     if (threadIdx.x < 6) part[6 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// cube of system s: centre = (lo+hi)/2, side = max extent (exact IEEE ops, no contraction)
-__global__ void k_bbox_final(const double *part, const int *sys_chunk_off, int nsys, double *cube) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nsys) return;
+// cube of system s (one block per system): the chunk partials folded by min / max
+// (exact, so the order does not matter), then centre = (lo+hi)/2, side = max extent
+// (exact IEEE ops, no contraction).  kq[s] = the key grid's origin per axis,
+// origin = centre - side/2, and RN(1/side) * 2^21 (= RN(2^21/side): the power of two
+// scales exactly), for k_morton.
+constexpr int kBoxFinalThreads = 128;
+__global__ void k_bbox_final(const double *part, const int *sys_chunk_off, double *cube, double *kq) {
+    __shared__ double red[6][kBoxFinalThreads];
+    const int s = blockIdx.x;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int c = sys_chunk_off[s]; c < sys_chunk_off[s + 1]; ++c)
+    for (int c = sys_chunk_off[s] + threadIdx.x; c < sys_chunk_off[s + 1]; c += blockDim.x)
         for (int a = 0; a < 3; ++a) {
             lo[a] = fmin(lo[a], part[6 * c + a]);
             hi[a] = fmax(hi[a], part[6 * c + 3 + a]);
         }
-    double side = 0.0;
-    for (int a = 0; a < 3; ++a) side = fmax(side, __dsub_rn(hi[a], lo[a]));
-    for (int a = 0; a < 3; ++a) cube[4 * s + a] = __dmul_rn(0.5, __dadd_rn(lo[a], hi[a]));
-    cube[4 * s + 3] = side;
+    for (int a = 0; a < 3; ++a) {
+        red[a][threadIdx.x] = lo[a];
+        red[3 + a][threadIdx.x] = hi[a];
+    }
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int a = 0; a < 3; ++a) {
+                red[a][threadIdx.x] = fmin(red[a][threadIdx.x], red[a][threadIdx.x + h]);
+                red[3 + a][threadIdx.x] = fmax(red[3 + a][threadIdx.x], red[3 + a][threadIdx.x + h]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double side = 0.0;
+        for (int a = 0; a < 3; ++a) side = fmax(side, __dsub_rn(red[3 + a][0], red[a][0]));
+        for (int a = 0; a < 3; ++a) {
+            const double c = __dmul_rn(0.5, __dadd_rn(red[a][0], red[3 + a][0]));
+            cube[4 * s + a] = c;
+            kq[4 * s + a] = __dsub_rn(c, __dmul_rn(0.5, side));
+        }
+        cube[4 * s + 3] = side;
+        kq[4 * s + 3] = side == 0.0 ? 0.0 : __dmul_rn(__drcp_rn(side), 2097152.0);
+    }
 }
 
 __device__ __forceinline__ int sys_of(const int64_t *off, int nsys, int64_t i) {
@@ -374,22 +451,34 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v) {
 
 // q = min(2^21-1, floor((x - origin)/side * 2^21)), origin = centre - side/2,
 // every step a single correctly rounded operation (no FMA contraction).
+// The scaled quotient is formed as d * RN(2^21/side): two roundings instead of
+// one put it within 3.5e-16 (relative, for |d| <= side) of RN(d / side) * 2^21,
+// i.e. within 7.3e-10 of it, so its floor is that of the defined value unless
+// it lies within 1e-9 of an integer; there the correctly rounded division is
+// taken.  The band test compares the bit patterns of the fraction (non-negative
+// doubles order as integers), and the integer is read from the mantissa after
+// adding 2^52 (exact for integers below 2^52): no FP64 conversions.
 __global__ void k_morton(const double *pos, int64_t n, const int64_t *off, int nsys, const double *cube,
-                         uint64_t *keys, uint64_t *keys_copy, uint32_t *idx, uint64_t *sysk) {
+                         const double *kq, uint64_t *keys, uint64_t *keys_copy, uint32_t *idx, uint64_t *sysk) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int s = sys_of(off, nsys, i);
-    double side = cube[4 * s + 3];
+    const double inv21 = kq[4 * s + 3];
+    const long long lo_band = __double_as_longlong(1e-9), hi_band = __double_as_longlong(1.0 - 1e-9);
     uint64_t q[3];
     for (int a = 0; a < 3; ++a) {
-        if (side == 0.0) { q[a] = 0; continue; }
-        double origin = __dsub_rn(cube[4 * s + a], __dmul_rn(0.5, side));
-        double t = __ddiv_rn(__dsub_rn(pos[3 * i + a], origin), side);
-        t = __dmul_rn(t, 2097152.0);
-        double fl = floor(t);
+        if (inv21 == 0.0) {   // side 0: every bead at the centre
+            q[a] = 0;
+            continue;
+        }
+        const double d = __dsub_rn(pos[3 * i + a], kq[4 * s + a]);
+        const double t2 = __dmul_rn(d, inv21);
+        double fl = floor(t2);
+        const long long fr = __double_as_longlong(__dsub_rn(t2, fl));   // fraction in [0, 1), exact
+        if (fr < lo_band || fr > hi_band) fl = floor(__dmul_rn(__ddiv_rn(d, cube[4 * s + 3]), 2097152.0));
         fl = fl < 0.0 ? 0.0 : fl;
         fl = fl > 2097151.0 ? 2097151.0 : fl;
-        q[a] = uint64_t(fl);
+        q[a] = uint64_t(__double_as_longlong(__dadd_rn(fl, 4503599627370496.0))) & 0x1fffffull;
     }
     uint64_t key = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
     keys[i] = key;
@@ -712,16 +801,32 @@ __global__ void k_leaf_stats(int nleaf, const int *leaves, const int *beg, const
                              const int *uidx, const int *doff, const int *didx, int cap, unsigned long long *pairs,
                              int *maxcnt, int *over) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nleaf) return;
-    int b = leaves[i];
-    int nb = end[b] - beg[b];
-    unsigned long long s = 0, sd = 0;
-    for (int k = uoff[i]; k < uoff[i + 1]; ++k) s += unsigned(end[uidx[k]] - beg[uidx[k]]);
-    for (int k = doff[i]; k < doff[i + 1]; ++k) sd += unsigned(end[didx[k]] - beg[didx[k]]);
-    atomicAdd(pairs, s * unsigned(nb));
-    atomicAdd(pairs + 1, sd * unsigned(nb));
-    atomicMax(maxcnt, nb);
-    if (nb > cap) atomicAdd(over, 1);
+    unsigned long long ps = 0, pd = 0;   // this leaf's U-list and direct pairs
+    int nb = 0, ov = 0;
+    if (i < nleaf) {
+        int b = leaves[i];
+        nb = end[b] - beg[b];
+        unsigned long long s = 0, sd = 0;
+        for (int k = uoff[i]; k < uoff[i + 1]; ++k) s += unsigned(end[uidx[k]] - beg[uidx[k]]);
+        for (int k = doff[i]; k < doff[i + 1]; ++k) sd += unsigned(end[didx[k]] - beg[didx[k]]);
+        ps = s * unsigned(nb);
+        pd = sd * unsigned(nb);
+        ov = nb > cap;
+    }
+    // integer sums and maximum over the warp, then one atomic of each per warp (one per
+    // leaf on a single word serialised on the hundreds of thousands of leaves of a forest)
+    for (int o = 16; o > 0; o >>= 1) {
+        ps += __shfl_down_sync(0xffffffffu, ps, o);
+        pd += __shfl_down_sync(0xffffffffu, pd, o);
+        nb = max(nb, __shfl_down_sync(0xffffffffu, nb, o));
+        ov += __shfl_down_sync(0xffffffffu, ov, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (ps) atomicAdd(pairs, ps);
+        if (pd) atomicAdd(pairs + 1, pd);
+        atomicMax(maxcnt, nb);
+        if (ov) atomicAdd(over, ov);
+    }
 }
 
 // ---------------------------------------------------------------- near-field work items
@@ -852,7 +957,9 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     RPY_CHECK(cudaMemsetAsync(t.dev_status, 0, sizeof(unsigned), st));
     k_bbox_partial<<<nch, 256, 0, st>>>(pos_dev, d_cb, d_ce, d_part, t.dev_status);
     RPY_LAUNCHED(1);
-    k_bbox_final<<<nblk(nsys, 128), 128, 0, st>>>(d_part, d_sco, nsys, t.sys_cube);
+    double *d_kq;
+    RPY_TRY(dev_alloc(scratch, (void **)&d_kq, sizeof(double) * 4 * nsys));
+    k_bbox_final<<<nsys, kBoxFinalThreads, 0, st>>>(d_part, d_sco, t.sys_cube, d_kq);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     unsigned status = 0;
@@ -877,7 +984,7 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     void *stmp;
     RPY_TRY(dev_alloc(scratch, &stmp, sbytes));
     if (nsys > 1) RPY_TRY(dev_alloc(scratch, (void **)&sysk, sizeof(uint64_t) * n));
-    k_morton<<<nblk(n, 256), 256, 0, st>>>(pos_dev, n, t.sys_off, nsys, t.sys_cube, k0, kcaller, v0, nullptr);
+    k_morton<<<nblk(n, 256), 256, 0, st>>>(pos_dev, n, t.sys_off, nsys, t.sys_cube, d_kq, k0, kcaller, v0, nullptr);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     RPY_TRY(radix_sort(k0, v0, k1, v1, int(n), 63, counts, stmp, sbytes, st));
@@ -1001,12 +1108,24 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
     RPY_TRY(dev_alloc(t, (void **)&t.u_off, sizeof(int) * (nleaf + 1)));
     RPY_TRY(dev_alloc(t, (void **)&t.w_off, sizeof(int) * (nleaf + 1)));
     RPY_TRY(dev_alloc(t, (void **)&t.x_off, sizeof(int) * (nbx + 1)));
-    int nu = 0, nw = 0, nx = 0, nwd = 0, nxd = 0;
-    RPY_TRY(exclusive_scan_i32(ucnt, t.u_off, nleaf + 1, &nu, stmp, sbytes, st));
-    RPY_TRY(exclusive_scan_i32(wcnt, t.w_off, nleaf + 1, &nw, stmp, sbytes, st));
-    RPY_TRY(exclusive_scan_i32(xcnt, t.x_off, nbx + 1, &nx, stmp, sbytes, st));
-    RPY_TRY(exclusive_scan_i32(wdcnt, wdoff, nleaf + 1, &nwd, stmp, sbytes, st));
-    RPY_TRY(exclusive_scan_i32(xdcnt, xdoff, nbx + 1, &nxd, stmp, sbytes, st));
+    // the five list offsets: scans in stream order, their totals read back together
+    int tot[5] = {0, 0, 0, 0, 0};
+    {
+        int *dtot;
+        RPY_TRY(dev_alloc(scratch, (void **)&dtot, sizeof(tot)));
+        const int *sin[5] = {ucnt, wcnt, xcnt, wdcnt, xdcnt};
+        int *sout[5] = {t.u_off, t.w_off, t.x_off, wdoff, xdoff};
+        const int sn[5] = {nleaf + 1, nleaf + 1, nbx + 1, nleaf + 1, nbx + 1};
+        for (int j = 0; j < 5; ++j) {
+            RPY_TRY(exclusive_scan_i32(sin[j], sout[j], sn[j], nullptr, stmp, sbytes, st));
+            k_scan_total<<<1, 32, 0, st>>>(sin[j], sout[j], sn[j], dtot + j);
+            RPY_LAUNCHED(1);
+        }
+        RPY_CHECK(cudaGetLastError());
+        RPY_CHECK(cudaMemcpyAsync(tot, dtot, sizeof(tot), cudaMemcpyDeviceToHost, st));
+        RPY_CHECK(cudaStreamSynchronize(st));
+    }
+    const int nu = tot[0], nw = tot[1], nx = tot[2], nwd = tot[3], nxd = tot[4];
     t.n_u = nu; t.n_w = nw; t.n_x = nx;
     RPY_TRY(dev_alloc(t, (void **)&t.u_idx, sizeof(int) * std::max(nu, 1)));
     RPY_TRY(dev_alloc(t, (void **)&t.w_idx, sizeof(int) * std::max(nw, 1)));

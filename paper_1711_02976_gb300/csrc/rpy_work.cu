@@ -102,7 +102,7 @@ extern "C" int rpy_tree_work(rpy_tree h, double *flops, double *bytes, int n) {
     double F[RPY_NUM_STAGES] = {}, B[RPY_NUM_STAGES] = {};
     const bool f32 = t.params.precision == RPY_FP32;
     const double w = f32 ? 4.0 : 8.0;                  // bytes of one real expansion value
-    const int p = t.p, nc = ncoef(p), s = t.tabs.s, S = t.tabs.S;
+    const int p = t.p, nc = ncoef(p), s = t.tabs->s, S = t.tabs->S;
     const double ce = 2 * w;                           // one complex value
     const int64_t N = t.n;
 
@@ -202,7 +202,7 @@ extern "C" int rpy_tree_work(rpy_tree h, double *flops, double *bytes, int n) {
         B[RPY_STAGE_M2X] = n2 * (4 * nc + 6.0 * 4 * S) * ce;
         B[RPY_STAGE_X2L] = n2 * (6.0 * 4 * S + 2 * 4 * nc) * ce;
         double units = 0;
-        const OpTables &tb = t.tabs;
+        const OpTables &tb = *t.tabs;
         for (int P : par)
             for (int d = 0; d < kDirs; ++d) {
                 const int ng = tb.grp_n[d];

@@ -48,6 +48,28 @@ def test_permutation_and_keys_bit_exact():
     np.testing.assert_array_equal(rp.rpy_tree_export(t, "cube")[0], cube)
 
 
+def test_morton_keys_exact_on_and_near_grid_points():
+    """Coordinates whose scaled value (x - origin) / side * 2^21 is an integer (a cube of side 1
+    and coordinates on a 2^-12 grid), or lies within rounding of one (a cube of side 3, offsets of
+    0, 1e-12 and 3e-10 key cells): the key kernel's multiply-by-reciprocal path must defer to the
+    correctly rounded division there.  Keys and order bit-exact against the oracle."""
+    rng = np.random.default_rng(12)
+    n = 20000
+    on_grid = rng.integers(0, 4097, size=(n, 3)) / 4096.0
+    on_grid[0], on_grid[1] = 0.0, 1.0
+    k = rng.integers(0, 2 ** 21, size=(n, 3)).astype(np.float64)
+    delta = rng.choice([-3e-10, -1e-12, 0.0, 1e-12, 3e-10], size=(n, 3))
+    near_grid = 3.0 * (k + delta) / 2 ** 21
+    near_grid[0], near_grid[1] = 0.0, 3.0
+    for pos in (on_grid, near_grid):
+        t = rp.rpy_tree_build(cuda_tensor(pos), n, 1e-6, 3, leaf_cap=40)
+        keys, cube = oracle.morton_keys(pos)
+        perm = oracle.stable_sort(keys)
+        np.testing.assert_array_equal(rp.rpy_tree_export(t, "keys"), keys[perm])
+        np.testing.assert_array_equal(rp.rpy_tree_export(t, "perm"), perm)
+        np.testing.assert_array_equal(rp.rpy_tree_export(t, "cube")[0], cube)
+
+
 def test_forest_permutation_bit_exact():
     rng = np.random.default_rng(5)
     sizes = [1, 700, 33, 2000]
