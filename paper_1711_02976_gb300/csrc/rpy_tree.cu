@@ -487,16 +487,18 @@ __global__ void k_morton(const double *pos, int64_t n, const int64_t *off, int n
     if (sysk) sysk[i] = uint64_t(s);
 }
 
+// keys_sorted: the keys already in sorted order (one system: the sort's own output),
+// read in place of the gather from keys_caller
 __global__ void k_gather_sorted(const double *pos, int64_t n, const uint32_t *perm, const uint64_t *keys_caller,
-                                const int64_t *off, int nsys, double *pos_s, uint64_t *keys_s, int *perm_i,
-                                int *bead_sys) {
+                                const uint64_t *keys_sorted, const int64_t *off, int nsys, double *pos_s,
+                                uint64_t *keys_s, int *perm_i, int *bead_sys) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t j = perm[i];
     pos_s[i] = pos[3 * int64_t(j)];
     pos_s[n + i] = pos[3 * int64_t(j) + 1];
     pos_s[2 * n + i] = pos[3 * int64_t(j) + 2];
-    keys_s[i] = keys_caller[j];
+    keys_s[i] = keys_sorted ? keys_sorted[i] : keys_caller[j];
     perm_i[i] = int(j);
     bead_sys[i] = sys_of(off, nsys, int64_t(j));
 }
@@ -995,8 +997,8 @@ int tree_build(Tree &t, const double *pos_dev, cudaStream_t st) {
         while ((1 << bits) < nsys) ++bits;
         RPY_TRY(radix_sort(sysk, v0, k1, v1, int(n), bits, counts, stmp, sbytes, st));
     }
-    k_gather_sorted<<<nblk(n, 256), 256, 0, st>>>(pos_dev, n, v0, kcaller, t.sys_off, nsys, t.pos, t.keys, t.perm,
-                                                  t.bead_sys);
+    k_gather_sorted<<<nblk(n, 256), 256, 0, st>>>(pos_dev, n, v0, kcaller, nsys == 1 ? k0 : nullptr, t.sys_off, nsys,
+                                                  t.pos, t.keys, t.perm, t.bead_sys);
     RPY_LAUNCHED(1);
     RPY_CHECK(cudaGetLastError());
     // -- octree, level by level
