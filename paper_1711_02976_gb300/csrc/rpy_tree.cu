@@ -219,7 +219,7 @@ int exclusive_scan_i32(const int *in, int *out, int n, int *total_host, void *tm
 // ---------------------------------------------------------------- radix sort
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;   // 4096
 constexpr int kSortWarps = kSortThreads / 32;
 
@@ -258,12 +258,18 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t *
     uint32_t v[kSortItems];
     int rk[kSortItems], dg[kSortItems];
     int base = blockIdx.x * kSortTile + warp * (kSortItems * 32);
+    // all of the thread's loads first (independent, so all in flight at once), then the ranking
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int i = base + r * 32 + lane;
+        k[r] = i < n ? kin[i] : 0ull;
+        v[r] = i < n ? vin[i] : 0u;
+    }
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         int i = base + r * 32 + lane;
         bool valid = i < n;
-        uint64_t key = valid ? kin[i] : 0ull;
-        int d = valid ? int((key >> shift) & 255) : 256;
+        int d = valid ? int((k[r] >> shift) & 255) : 256;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int leader = __ffs(peers) - 1;
         int pre = __popc(peers & ((1u << lane) - 1u));
@@ -274,8 +280,6 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t *
         }
         b = __shfl_sync(0xffffffffu, b, leader);
         __syncwarp();
-        k[r] = key;
-        v[r] = valid ? vin[i] : 0u;
         dg[r] = d;
         rk[r] = b + pre;
     }
@@ -316,8 +320,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t *
     }
 }
 
-// The scatter's dynamic shared memory (the reordered tile) exceeds the default
-// 48 KB together with its static arrays: raise the limit once per device.
+// The scatter's dynamic shared memory (the reordered tile): the limit is raised
+// once per device, so that a larger tile may pass the default 48 KB together
+// with the static arrays (2,048 items per tile take 24 KB).
 static cudaError_t set_scatter_smem() {
     static std::mutex mu;
     static std::set<int> done;
