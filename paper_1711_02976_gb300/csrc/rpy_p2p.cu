@@ -16,12 +16,13 @@
 // one Newton-Raphson step for the reciprocal square root (y <- y (3 - r2 y^2)/2),
 // which brings the relative error from ~1e-7 to ~1e-14.
 // FP32 form (precision setting, k_p2p32): positions relative to the target
-// leaf centre in FP32; every thread carries two targets as two independent
-// scalar FP32 chains per staged source; an iteration whose pairs are all far
-// (across the warp) evaluates the far branch alone, any other evaluates both
-// branches without divergence; accumulation is Kahan-compensated across blocks of kP32Block
-// sources; pairs closer than 1e-3 a (where the FP32 difference of coordinates
-// loses the direction) are recomputed in FP64 from the FP64 positions.
+// leaf centre in FP32; every thread carries two targets as the two lanes of
+// packed FP32x2 operations and takes two staged sources per iteration; an
+// iteration whose pairs are all far (across the warp) evaluates the far branch
+// alone on the packed pairs, any other evaluates both branches per target with
+// selects; accumulation is Kahan-compensated across blocks of kP32Block sources;
+// pairs closer than 1e-3 a (where the FP32 difference of coordinates loses the
+// direction) are recomputed in FP64 from the FP64 positions.
 #include <cmath>
 
 #include <mutex>
@@ -302,7 +303,7 @@ __device__ __forceinline__ void kahan_merge(float &s, float &c, float v) {
 }
 
 // A leaf of T beads: R = min(ceil(T/2), blockDim) threads per pass carry
-// targets i0 + t and i0 + R + t (two independent chains per staged source);
+// targets i0 + t and i0 + R + t (the two lanes of each packed chain);
 // G = blockDim / R groups split every staged chunk.  The U list's boxes are
 // prefix-summed in shared memory and each staged bead finds its box by
 // binary search.
