@@ -406,6 +406,40 @@ def test_forest_results_equal_individual_systems():
         np.testing.assert_array_equal(got[off[k]:off[k + 1]], uk)
 
 
+@pytest.mark.parametrize("precision,digits,tol", [(rp.RPY_FP64, 6, 1e-6), (rp.RPY_FP32, 3, 1e-3)])
+def test_forest_with_degenerate_systems(precision, digits, tol):
+    """One forest of degenerate systems beside ordinary ones: a single bead (a cube of side 0),
+    two coincident beads, two beads far apart, three beads within 2a of each other, a system whose
+    beads all sit on one plane (a cube flat on one axis), and a 6,000-bead cube deep enough for a
+    far field.  Every system against the oracle on its own, in both precision forms."""
+    import torch
+    rng = np.random.default_rng(21)
+    plane = rng.random((400, 3))
+    plane[:, 2] = 0.25
+    systems = [
+        (np.array([[0.3, 0.4, 0.5]]), 0.01),
+        (np.array([[0.2, 0.2, 0.2], [0.2, 0.2, 0.2]]), 0.01),
+        (np.array([[0.0, 0.0, 0.0], [10.0, -3.0, 2.0]]), 0.01),
+        (np.array([[0.5, 0.5, 0.5], [0.505, 0.5, 0.5], [0.5, 0.508, 0.5]]), 0.01),
+        (plane, 0.004),
+        (rng.random((6000, 3)), 0.002),
+    ]
+    pos = [sy[0] for sy in systems]
+    a = [sy[1] for sy in systems]
+    s = [6 * math.pi * ak for ak in a]
+    f = [rng.standard_normal(p_.shape) for p_ in pos]
+    off = np.concatenate([[0], np.cumsum([len(p_) for p_ in pos])]).astype(np.int64)
+    t = rp.rpy_forest_build(cuda_tensor(np.concatenate(pos)), off, a, digits, leaf_cap=20, precision=precision)
+    U = torch.empty((int(off[-1]), 3), dtype=torch.float64, device="cuda")
+    rp.rpy_forest_matvec(t, cuda_tensor(np.concatenate(f)), s, U)
+    rp.rpy_tree_sync(t)
+    u = U.cpu().numpy()
+    assert rp.rpy_tree_stats(t)["depth"] >= 3
+    for k in range(len(systems)):
+        ref = oracle.rpy_direct(pos[k], f[k], a[k], s[k])
+        assert oracle.rel_l2(u[off[k]:off[k + 1]], ref) <= tol, k
+
+
 def test_host_entry_point():
     sysm = synth.config1()
     u = np.zeros_like(sysm.f)
