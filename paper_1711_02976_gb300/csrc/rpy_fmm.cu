@@ -1425,8 +1425,13 @@ __global__ void k_x2l4(int b0, int nb, DevTables<float> D, const cpx<float> *Xi,
         }
         __syncthreads();
         // b_k^m = 2 sum_j Re(I_j) e^{-i m a_j} (m even), 2i sum_j Im(I_j) e^{-i m a_j} (m odd)
-        for (int e = threadIdx.x; e < s * P1; e += blockDim.x) {
-            const int k = e / P1, m = e - k * P1;
+        // (node, m) items at a stride of PA = 8 per node when p + 1 <= 8, so that a
+        // quarter-warp never straddles two nodes (its wave loads are then broadcasts)
+        const int PA = P1 <= 8 ? 8 : P1;
+        for (int ea = threadIdx.x; ea < s * PA; ea += blockDim.x) {
+            const int k = ea / PA, m = ea - k * PA;
+            if (m >= P1) continue;
+            const int e = k * P1 + m;
             const int j0 = D.k_start[k], j1 = D.k_start[k + 1];
             const int Mk = 2 * (j1 - j0), mm = m % Mk;
             const cpx<float> *rt = D.roots + 2 * j0;
