@@ -671,6 +671,7 @@ int rpy_tree_update_positions(rpy_tree h, const double *pos_dev, void *stream) {
     fresh.side_stream = t.side_stream;
     fresh.fork_ev = t.fork_ev;
     fresh.join_ev = t.join_ev;
+    fresh.h2d_ev = t.h2d_ev;
     fresh.sys_off_h = t.sys_off_h;
     fresh.a_h = t.a_h;
     fresh.cache = std::move(t.cache);
@@ -698,10 +699,18 @@ int rpy_tree_matvec_host(rpy_tree h, const double *pos_host, const double *f_hos
     }
     double *dp = t.host_io, *df = t.host_io + n3, *du = t.host_io + 2 * n3;
     if (pos_host) {
+        // the forces' copy on the side stream, beside the rebuild (the previous call of this
+        // entry synchronised st, so nothing still reads df); st waits for it before the matvec
+        if (!t.side_stream) RPY_CHECK(cudaStreamCreateWithFlags(&t.side_stream, cudaStreamNonBlocking));
+        if (!t.h2d_ev) RPY_CHECK(cudaEventCreateWithFlags(&t.h2d_ev, cudaEventDisableTiming));
         RPY_CHECK(cudaMemcpyAsync(dp, pos_host, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
+        RPY_CHECK(cudaMemcpyAsync(df, f_host, sizeof(double) * n3, cudaMemcpyHostToDevice, t.side_stream));
+        RPY_CHECK(cudaEventRecord(t.h2d_ev, t.side_stream));
         RPY_TRY(rpy_tree_update_positions(h, dp, stream));
+        RPY_CHECK(cudaStreamWaitEvent(st, t.h2d_ev, 0));
+    } else {
+        RPY_CHECK(cudaMemcpyAsync(df, f_host, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
     }
-    RPY_CHECK(cudaMemcpyAsync(df, f_host, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
     RPY_TRY(rpy_forest_matvec(h, df, s_host, du, stream));
     RPY_CHECK(cudaMemcpyAsync(u_host, du, sizeof(double) * n3, cudaMemcpyDeviceToHost, st));
     RPY_CHECK(cudaStreamSynchronize(st));
@@ -959,6 +968,7 @@ void rpy_tree_free(rpy_tree h) {
         if (t.side_stream) cudaStreamDestroy(t.side_stream);
         if (t.fork_ev) cudaEventDestroy(t.fork_ev);
         if (t.join_ev) cudaEventDestroy(t.join_ev);
+        if (t.h2d_ev) cudaEventDestroy(t.h2d_ev);
     }
     h->magic = 0;
     delete h;

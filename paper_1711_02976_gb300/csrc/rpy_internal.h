@@ -284,6 +284,7 @@ struct Tree {
     // (fork_ev / join_ev order the two branches inside the graph)
     cudaStream_t side_stream = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaEvent_t h2d_ev = nullptr;     // host-buffer step: the forces' copy (on side_stream) has landed
     cudaGraphExec_t gexec = nullptr;
     int matvecs = 0;                  // matvecs since the last build
     // stage marks of the last profiled matvec: event k opens an interval of stage
