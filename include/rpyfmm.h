@@ -226,9 +226,10 @@ int rpy_matvec_parts(rpy_tree t, const double *f_dev, double kT_over_eta, double
  * The matvec of a resident tree with HOST buffers: the step of a Brownian-
  * dynamics loop or a serving request (Sec. 1: D F at the current positions).
  * When pos_host is non-NULL it is copied to the device and the tree is rebuilt
- * for it (as rpy_tree_update_positions); then f_host is copied, u = D F is
- * applied (as rpy_forest_matvec) and u is copied back to u_host.  All on
- * `stream`, synchronised before return.  Page-locked host buffers
+ * for it (as rpy_tree_update_positions), while f_host is copied on a stream of
+ * the tree's own; then u = D F is applied (as rpy_forest_matvec, after both
+ * copies) and u is copied back to u_host.  The work is ordered on `stream` and
+ * synchronised before return.  Page-locked host buffers
  * (cudaHostAlloc, cudaHostRegister) copy at full bus speed; pageable ones work
  * and copy slower.  The tree allocates 9 N doubles of device buffers for the
  * copies on the first call and keeps them until rpy_tree_free.
