@@ -465,6 +465,15 @@ def test_resident_tree_host_buffer_matvec():
     u2 = torch.zeros(f.shape, dtype=torch.float64).pin_memory().numpy()
     rp.rpy_tree_matvec_host(t, None, f2, sysm.s, u2)
     np.testing.assert_array_equal(u2, -2.0 * ref)   # the matvec is linear, and -2x is exact
+    # new positions and forces from page-locked buffers (the forces' copy then runs
+    # asynchronously beside the rebuild), twice in a row
+    pos3 = torch.from_numpy(np.ascontiguousarray(sysm.pos[::-1] * 0.9 + 0.05)).pin_memory().numpy()
+    f3 = torch.from_numpy(np.ascontiguousarray(f[::-1])).pin_memory().numpy()
+    for _ in range(2):
+        u3 = torch.zeros(f.shape, dtype=torch.float64).pin_memory().numpy()
+        rp.rpy_tree_matvec_host(t, pos3, f3, sysm.s, u3)
+        ref3, _ = matvec(pos3, f3, sysm.a, sysm.s, 6)
+        np.testing.assert_array_equal(u3, ref3)
     tg = synth.sample_targets(sysm.n, 500)
     assert oracle.rel_l2(u[tg], oracle.rpy_direct(pos2, f, sysm.a, sysm.s, targets=tg)) < 1e-6
     t.close()
