@@ -440,6 +440,47 @@ def test_forest_with_degenerate_systems(precision, digits, tol):
         assert oracle.rel_l2(u[off[k]:off[k + 1]], ref) <= tol, k
 
 
+def _forest_parity(systems, digits, tol, **kw):
+    import torch
+    pos = [sy[0] for sy in systems]
+    a = [sy[1] for sy in systems]
+    s = [6 * math.pi * ak for ak in a]
+    rng = np.random.default_rng(33)
+    f = [rng.standard_normal(p_.shape) for p_ in pos]
+    off = np.concatenate([[0], np.cumsum([len(p_) for p_ in pos])]).astype(np.int64)
+    t = rp.rpy_forest_build(cuda_tensor(np.concatenate(pos)), off, a, digits, **kw)
+    U = torch.empty((int(off[-1]), 3), dtype=torch.float64, device="cuda")
+    rp.rpy_forest_matvec(t, cuda_tensor(np.concatenate(f)), s, U)
+    rp.rpy_tree_sync(t)
+    u = U.cpu().numpy()
+    for k in range(len(systems)):
+        tg = synth.sample_targets(len(pos[k]), 300, seed=40 + k)
+        ref = oracle.rpy_direct(pos[k], f[k], a[k], s[k], targets=tg)
+        assert oracle.rel_l2(u[off[k] + tg], ref) <= tol, k
+    return t
+
+
+@pytest.mark.parametrize("precision", [rp.RPY_FP64, rp.RPY_FP32])
+def test_cartesian_far_field_on_a_forest(precision):
+    """The polynomial far field with several systems in one tree (each its own cube, its own
+    boxes and V lists): a uniform cube, a sphere surface and a clustered system of different
+    sizes and radii, every one against the oracle at 3 digits."""
+    rng = np.random.default_rng(34)
+    systems = [(rng.random((12000, 3)), 0.002),
+               (synth._sphere_surface(rng, 8000, 0.5, (0.5, 0.5, 0.5)), 0.001),
+               (_clustered(6000, 35) * 3.0, 0.003)]
+    t = _forest_parity(systems, 3, 1e-3, leaf_cap=40, precision=precision, flags=rp.RPY_FLAG_CARTESIAN)
+    assert rp.rpy_tree_stats(t)["depth"] >= 3
+
+
+def test_9digit_forest():
+    """Nine digits (FP64) with two systems of different scales in one tree."""
+    rng = np.random.default_rng(36)
+    systems = [(rng.random((8000, 3)), 0.002),
+               (synth._sphere_surface(rng, 6000, 2.0, (1.0, -1.0, 0.5)), 0.004)]
+    _forest_parity(systems, 9, 1e-9, leaf_cap=60)
+
+
 def test_host_entry_point():
     sysm = synth.config1()
     u = np.zeros_like(sysm.f)
