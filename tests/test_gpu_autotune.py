@@ -95,6 +95,23 @@ def test_evaluate_sources_at_targets():
     assert np.max(np.abs(u[:10] - ref[:10])) <= 1e-6 * np.max(np.abs(ref))
 
 
+def test_evaluate_sources_at_targets_fp32():
+    """rpy_evaluate in the FP32 precision form at 3 digits, targets on and near sources."""
+    rng = np.random.default_rng(43)
+    src = synth.uniform_cube(20000, seed=44, a=0.002)
+    tgt = rng.random((2000, 3))
+    tgt[:5] = src.pos[:5]
+    tgt[5:10] = src.pos[5:10] + 0.0007
+    import torch
+    U = torch.empty((len(tgt), 3), dtype=torch.float64, device="cuda")
+    rp.rpy_evaluate(cuda_tensor(src.pos), cuda_tensor(src.f), cuda_tensor(tgt), src.a, src.s, 3, U,
+                    precision=rp.RPY_FP32)
+    pos = np.concatenate([src.pos, tgt])
+    f = np.concatenate([src.f, np.zeros_like(tgt)])
+    ref = oracle.rpy_direct(pos, f, src.a, src.s, targets=np.arange(src.n, src.n + len(tgt)))
+    assert oracle.rel_l2(U.cpu().numpy(), ref) <= 1e-3
+
+
 def test_autotune_verifies_its_choice_on_a_fresh_deep_sample():
     """With the loosest search margin (accept a sampled error up to the bound itself on
     64 targets), the tuner's choice must still pass its verification: an independent

@@ -534,6 +534,33 @@ def test_update_positions_matches_fresh_build():
     np.testing.assert_array_equal(U.cpu().numpy(), u2)
 
 
+@pytest.mark.parametrize("precision", [rp.RPY_FP64, rp.RPY_FP32])
+def test_forest_update_positions_matches_fresh_build(precision):
+    """A forest rebuilt in place for new positions (as each Brownian-dynamics step does) gives
+    bitwise the velocities of a forest built fresh at those positions, graph replay included."""
+    import torch
+    rng = np.random.default_rng(37)
+    sizes = [3000, 500, 9000]
+    pos = [rng.random((n, 3)) * (k + 1) for k, n in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    a, s = [0.004, 0.01, 0.003], [1.0, 2.0, 0.5]
+    P = np.concatenate(pos)
+    F = cuda_tensor(rng.standard_normal(P.shape))
+    t = rp.rpy_forest_build(cuda_tensor(P), off, a, 3, leaf_cap=30, precision=precision)
+    U = torch.empty_like(F)
+    for _ in range(2):
+        rp.rpy_forest_matvec(t, F, s, U)   # the second replays the captured graph
+    P2 = P + 1e-3 * rng.standard_normal(P.shape)
+    rp.rpy_tree_update_positions(t, cuda_tensor(P2))
+    for _ in range(2):
+        rp.rpy_forest_matvec(t, F, s, U)
+    t2 = rp.rpy_forest_build(cuda_tensor(P2), off, a, 3, leaf_cap=30, precision=precision)
+    U2 = torch.empty_like(F)
+    rp.rpy_forest_matvec(t2, F, s, U2)
+    rp.rpy_tree_sync(t2)
+    np.testing.assert_array_equal(U.cpu().numpy(), U2.cpu().numpy())
+
+
 def test_graph_replay_matches_plain_launches():
     """From the second matvec on a build, the body runs as a captured CUDA graph;
     results stay bitwise equal to plain launches, also after a rebuild."""
