@@ -66,11 +66,12 @@ def test_lanczos_forest_is_block_diagonal():
     assert np.linalg.norm(y.ravel() - ref) <= 1e-9 * np.linalg.norm(ref)
 
 
-def test_lanczos_invariants_at_fmm_size():
+@pytest.mark.parametrize("precision", [rp.RPY_FP64, rp.RPY_FP32])
+def test_lanczos_invariants_at_fmm_size(precision):
     rng = np.random.default_rng(12)
     sysm = synth.sphere_plus_cube(20000, seed=13, a=5e-4)
     z = rng.standard_normal((sysm.n, 3))
-    t = rp.rpy_forest_build(cuda_tensor(sysm.pos), [0, sysm.n], [sysm.a], 6)
+    t = rp.rpy_forest_build(cuda_tensor(sysm.pos), [0, sysm.n], [sysm.a], 6, precision=precision)
     import torch
     Y = torch.empty((sysm.n, 3), dtype=torch.float64, device="cuda")
     Y2 = torch.empty_like(Y)
